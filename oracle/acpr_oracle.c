@@ -1,0 +1,489 @@
+/*
+ * acpr_oracle.c -- plain, slow, float64 CPU oracle for the Parareal / Allen-Cahn
+ * hot path.  TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the CPU
+ * baseline leg of the benchmark call it; the library never does.  It shares no
+ * code with the CUDA path.
+ *
+ * Every routine follows the paper's definitions in their stated order, with no
+ * blocking or fusion:
+ *   - Allen-Cahn models and double-well nonlinearity f(u) = u - u^3: Sec. 2,
+ *     Eq. (class_AC_eq) and Eq. (mass_AC_eq).
+ *   - Energy E(u) = int eps^2/2 |grad u|^2 + F(u): Sec. 2, Eq. (energy).
+ *   - Grid: N unknowns per side, h = L/N, x_i = -L/2 + i h (Sec. 3.1, periodic
+ *     identification U^0 = U^N).
+ *   - Fine step: stabilised linear semi-implicit scheme with the periodic
+ *     5-point Laplacian, solved by the 2D DFT (the scheme family the paper cites
+ *     in Sec. 1; the spatial options are in Sec. 3.1).
+ *   - Coarse propagator: 3x3 circular-padded conv stack (Sec. 3.2).
+ *   - Parareal: Algorithm 2 / Sec. 3.3.
+ *
+ * Parity status: every function here is pinned by the not-gpu tests (naive DFT,
+ * dense linear solve, closed forms, invariants, finite differences, brute force)
+ * except the bf16-emulating conv mode, whose values are pinned only through the
+ * float64 mode it reduces to when rounding is off.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+typedef struct {
+    int n;          /* grid points per side */
+    double length;  /* side of the periodic square */
+    double eps;     /* interface width epsilon */
+    double S;       /* stabilisation constant */
+    double dt;      /* fine time step */
+    int variant;    /* 0 classic, 1 mass-conserving */
+} or_params;
+
+typedef struct {
+    int layers;     /* number of 3x3 convolutions */
+    int channels;   /* hidden width C */
+    int act;        /* 0 tanh, 1 gelu (erf form) */
+    int residual;   /* 1: output = input + stack(input) */
+    int mass_fix;   /* 1: add mean(input) - mean(output) to every entry */
+    int limiter;    /* 1: clamp to [lo, hi] */
+    int bf16;       /* 1: round weights, conv input and hidden activations to bf16 */
+    double lo, hi;
+    const double* w; /* concat over layers of W_l[cout][cin][3][3] */
+    const double* b; /* concat over layers of b_l[cout] */
+} or_cnn;
+
+static const double PI = 3.14159265358979323846264338327950288;
+
+/* ------------------------------------------------------------------ FFT -- */
+/* Recursive radix-2 decimation-in-time Cooley-Tukey transform,
+ * y_k = sum_j x_j exp(sign * 2 pi i j k / n), unnormalised. */
+static void fft_rec(const cplx* in, cplx* out, int n, int stride, int sign) {
+    if (n == 1) { out[0] = in[0]; return; }
+    int h = n / 2;
+    fft_rec(in, out, h, 2 * stride, sign);
+    fft_rec(in + stride, out + h, h, 2 * stride, sign);
+    for (int k = 0; k < h; k++) {
+        double ang = sign * 2.0 * PI * (double)k / (double)n;
+        cplx w = cos(ang) + I * sin(ang);
+        cplx e = out[k], o = w * out[k + h];
+        out[k] = e + o;
+        out[k + h] = e - o;
+    }
+}
+
+void or_fft1d(cplx* x, int n, int sign) {
+    cplx* in = malloc(sizeof(cplx) * n);
+    memcpy(in, x, sizeof(cplx) * n);
+    fft_rec(in, x, n, 1, sign);
+    free(in);
+}
+
+/* 2D transform of a row-major n x n array: every row, then every column. */
+void or_fft2d(cplx* x, int n, int sign) {
+    cplx* col = malloc(sizeof(cplx) * n);
+    for (int i = 0; i < n; i++) or_fft1d(x + (size_t)i * n, n, sign);
+    for (int j = 0; j < n; j++) {
+        for (int i = 0; i < n; i++) col[i] = x[(size_t)i * n + j];
+        or_fft1d(col, n, sign);
+        for (int i = 0; i < n; i++) x[(size_t)i * n + j] = col[i];
+    }
+    free(col);
+}
+
+/* Direct O(n^4) 2D DFT, the definition itself. */
+void or_dft2d_naive(const cplx* x, cplx* y, int n, int sign) {
+    for (int k = 0; k < n; k++)
+        for (int l = 0; l < n; l++) {
+            cplx acc = 0;
+            for (int i = 0; i < n; i++)
+                for (int j = 0; j < n; j++) {
+                    double ang = sign * 2.0 * PI * (double)(((long)i * k + (long)j * l) % n) / n;
+                    acc += x[(size_t)i * n + j] * (cos(ang) + I * sin(ang));
+                }
+            y[(size_t)k * n + l] = acc;
+        }
+}
+
+/* Interleaved (re, im) wrappers for callers without C99 complex. */
+void or_fft2d_ri(double* xri, int n, int sign) { or_fft2d((cplx*)xri, n, sign); }
+void or_dft2d_naive_ri(const double* xri, double* yri, int n, int sign) {
+    or_dft2d_naive((const cplx*)xri, (cplx*)yri, n, sign);
+}
+
+/* ------------------------------------------------------------- model ---- */
+static double f_dw(double u) { return u - u * u * u; }          /* f = -F' */
+static double fprime_dw(double u) { return 1.0 - 3.0 * u * u; }
+static double F_dw(double u) { double t = u * u - 1.0; return 0.25 * t * t; }
+
+/* Eigenvalue of the periodic 5-point Laplacian for mode (k, l):
+ * -(4/h^2) (sin^2(pi k/N) + sin^2(pi l/N)). */
+static double lap_symbol(int k, int l, int n, double h) {
+    double sk = sin(PI * k / n), sl = sin(PI * l / n);
+    return -(4.0 / (h * h)) * (sk * sk + sl * sl);
+}
+
+/* Solve ((1 + S dt) I - dt eps^2 Lap_h) v = r by the 2D DFT. */
+static void solve_A(const or_params* p, const double* r, double* v) {
+    int n = p->n;
+    double h = p->length / n;
+    cplx* z = malloc(sizeof(cplx) * n * n);
+    for (int i = 0; i < n * n; i++) z[i] = r[i];
+    or_fft2d(z, n, -1);
+    for (int k = 0; k < n; k++)
+        for (int l = 0; l < n; l++) {
+            double D = 1.0 + p->S * p->dt - p->dt * p->eps * p->eps * lap_symbol(k, l, n, h);
+            z[(size_t)k * n + l] /= D;
+        }
+    or_fft2d(z, n, +1);
+    for (int i = 0; i < n * n; i++) v[i] = creal(z[i]) / ((double)n * n);
+    free(z);
+}
+
+void or_solve_A(const or_params* p, const double* r, double* v) { solve_A(p, r, v); }
+
+/* One stabilised semi-implicit step:
+ *   (1 + S dt) u' - dt eps^2 Lap_h u' = (1 + S dt) u + dt (f(u) - beta),
+ * beta = 0 (classic) or beta = mean_x f(u) (mass-conserving Lagrange multiplier,
+ * Eq. (mass_AC_eq) evaluated explicitly at u^n). */
+void or_fine_step(const or_params* p, const double* u, double* out) {
+    int n = p->n, m = n * n;
+    double beta = 0.0;
+    if (p->variant == 1) {
+        for (int i = 0; i < m; i++) beta += f_dw(u[i]);
+        beta /= m;
+    }
+    double* r = malloc(sizeof(double) * m);
+    for (int i = 0; i < m; i++) r[i] = (1.0 + p->S * p->dt) * u[i] + p->dt * (f_dw(u[i]) - beta);
+    solve_A(p, r, out);
+    free(r);
+}
+
+/* Fine propagator over one slice: `steps` fine steps. */
+void or_fine_propagate(const or_params* p, int steps, const double* u, double* out) {
+    int m = p->n * p->n;
+    double* a = malloc(sizeof(double) * m);
+    memcpy(a, u, sizeof(double) * m);
+    for (int s = 0; s < steps; s++) {
+        or_fine_step(p, a, out);
+        memcpy(a, out, sizeof(double) * m);
+    }
+    if (steps == 0) memcpy(out, u, sizeof(double) * m);
+    free(a);
+}
+
+/* Discrete energy E_h(u) = h^2 sum eps^2/2 (|D+x u|^2 + |D+y u|^2) + F(u). */
+double or_energy(const or_params* p, const double* u) {
+    int n = p->n;
+    double h = p->length / n, e = 0.0;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) {
+            double c = u[i * n + j];
+            double dx = (u[((i + 1) % n) * n + j] - c) / h;
+            double dy = (u[i * n + (j + 1) % n] - c) / h;
+            e += 0.5 * p->eps * p->eps * (dx * dx + dy * dy) + F_dw(c);
+        }
+    return h * h * e;
+}
+
+/* Mass M = h^2 sum u. */
+double or_mass(const or_params* p, const double* u) {
+    double h = p->length / p->n, s = 0.0;
+    for (int i = 0; i < p->n * p->n; i++) s += u[i];
+    return h * h * s;
+}
+
+/* 5-point periodic Laplacian applied directly (used by the energy gradient). */
+static void apply_lap(int n, double h, const double* u, double* out) {
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++)
+            out[i * n + j] = (u[((i + 1) % n) * n + j] + u[((i + n - 1) % n) * n + j] +
+                              u[i * n + (j + 1) % n] + u[i * n + (j + n - 1) % n] -
+                              4.0 * u[i * n + j]) / (h * h);
+}
+
+/* dE_h/du = h^2 (-eps^2 Lap_h u - f(u)). */
+void or_energy_grad(const or_params* p, const double* u, double* g) {
+    int n = p->n, m = n * n;
+    double h = p->length / n;
+    double* lu = malloc(sizeof(double) * m);
+    apply_lap(n, h, u, lu);
+    for (int i = 0; i < m; i++) g[i] = h * h * (-p->eps * p->eps * lu[i] - f_dw(u[i]));
+    free(lu);
+}
+
+/* Transposed Jacobian of one fine step at u^n applied to lam (the adjoint step):
+ * u' = A^{-1} ((1+S dt) u + dt (f(u) - beta(u))), A symmetric, so with
+ * mu = A^{-1} lam:  lam_n = (1+S dt) mu + dt f'(u) * (mu - [mass] mean(mu)). */
+void or_fine_adjoint_step(const or_params* p, const double* u, const double* lam, double* out) {
+    int m = p->n * p->n;
+    double* mu = malloc(sizeof(double) * m);
+    solve_A(p, lam, mu);
+    double mbar = 0.0;
+    if (p->variant == 1) {
+        for (int i = 0; i < m; i++) mbar += mu[i];
+        mbar /= m;
+    }
+    for (int i = 0; i < m; i++)
+        out[i] = (1.0 + p->S * p->dt) * mu[i] + p->dt * fprime_dw(u[i]) * (mu[i] - mbar);
+    free(mu);
+}
+
+/* Gradient of E_h(u^steps) with respect to u^0 by storing every state and
+ * running the adjoint steps backwards (no checkpointing: the plain form). */
+void or_energy_gradient_through_solve(const or_params* p, int steps, const double* u0, double* grad) {
+    int m = p->n * p->n;
+    double* traj = malloc(sizeof(double) * (size_t)m * (steps + 1));
+    memcpy(traj, u0, sizeof(double) * m);
+    for (int s = 0; s < steps; s++) or_fine_step(p, traj + (size_t)s * m, traj + (size_t)(s + 1) * m);
+    double* lam = malloc(sizeof(double) * m);
+    double* tmp = malloc(sizeof(double) * m);
+    or_energy_grad(p, traj + (size_t)steps * m, lam);
+    for (int s = steps - 1; s >= 0; s--) {
+        or_fine_adjoint_step(p, traj + (size_t)s * m, lam, tmp);
+        memcpy(lam, tmp, sizeof(double) * m);
+    }
+    memcpy(grad, lam, sizeof(double) * m);
+    free(traj); free(lam); free(tmp);
+}
+
+/* --------------------------------------------------------------- CNN ---- */
+/* Round a double to the nearest bfloat16 value (ties to even). */
+double or_round_bf16(double x) {
+    if (!isfinite(x) || x == 0.0) return x;
+    int e;
+    double mant = frexp(fabs(x), &e);         /* |x| = mant * 2^e, mant in [0.5,1) */
+    /* bf16 keeps 8 significant bits: scale so that the kept bits are integral */
+    double scaled = ldexp(mant, 8);            /* in [128, 256) */
+    double r = nearbyint(scaled);              /* ties to even under the default mode */
+    double y = ldexp(r, e - 8);
+    return x < 0 ? -y : y;
+}
+
+static double act_fn(int act, double x) {
+    if (act == 0) return tanh(x);
+    return 0.5 * x * (1.0 + erf(x / sqrt(2.0)));
+}
+
+static double act_grad(int act, double x) {
+    if (act == 0) { double t = tanh(x); return 1.0 - t * t; }
+    return 0.5 * (1.0 + erf(x / sqrt(2.0))) + x * exp(-0.5 * x * x) / sqrt(2.0 * PI);
+}
+
+/* One 3x3 cross-correlation with circular padding 1:
+ * out[o][i][j] = b[o] + sum_{c,a,e} W[o][c][a][e] in[c][(i+a-1) mod n][(j+e-1) mod n]. */
+static void conv3x3(int n, int cin, int cout, const double* W, const double* b,
+                    const double* in, double* out) {
+    for (int o = 0; o < cout; o++)
+        for (int i = 0; i < n; i++)
+            for (int j = 0; j < n; j++) {
+                double acc = b[o];
+                for (int c = 0; c < cin; c++)
+                    for (int a = 0; a < 3; a++)
+                        for (int e = 0; e < 3; e++) {
+                            int ii = (i + a - 1 + n) % n, jj = (j + e - 1 + n) % n;
+                            acc += W[((o * cin + c) * 3 + a) * 3 + e] * in[((size_t)c * n + ii) * n + jj];
+                        }
+                out[((size_t)o * n + i) * n + j] = acc;
+            }
+}
+
+static void layer_dims(const or_cnn* d, int l, int* cin, int* cout) {
+    *cin = (l == 0) ? 1 : d->channels;
+    *cout = (l == d->layers - 1) ? 1 : d->channels;
+}
+
+/* Forward pass.  If pre_acts != NULL, stores every layer's pre-activation
+ * (z_l, [cout][n][n]) and post-activation input (a_l) for the backward pass;
+ * the buffers are laid out layer after layer, C*n*n doubles per layer. */
+static void cnn_forward_impl(const or_cnn* d, int n, const double* u, double* out,
+                             double* pre_acts, double* inputs) {
+    size_t m = (size_t)n * n;
+    int C = d->channels > 1 ? d->channels : 1;
+    double* a = malloc(sizeof(double) * C * m);
+    double* z = malloc(sizeof(double) * C * m);
+    for (size_t i = 0; i < m; i++) a[i] = d->bf16 ? or_round_bf16(u[i]) : u[i];
+    const double* W = d->w;
+    const double* B = d->b;
+    int nw_total = 0, nb_total = 0;
+    for (int l = 0; l < d->layers; l++) { int ci, co; layer_dims(d, l, &ci, &co); nw_total += ci * co * 9; nb_total += co; }
+    double* wr = malloc(sizeof(double) * nw_total);
+    for (int i = 0; i < nw_total; i++) wr[i] = d->bf16 ? or_round_bf16(W[i]) : W[i];
+    int woff = 0, boff = 0;
+    for (int l = 0; l < d->layers; l++) {
+        int cin, cout;
+        layer_dims(d, l, &cin, &cout);
+        if (inputs) memcpy(inputs + (size_t)l * C * m, a, sizeof(double) * cin * m);
+        conv3x3(n, cin, cout, wr + woff, B + boff, a, z);
+        if (pre_acts) memcpy(pre_acts + (size_t)l * C * m, z, sizeof(double) * cout * m);
+        woff += cin * cout * 9;
+        boff += cout;
+        if (l < d->layers - 1) {
+            for (size_t i = 0; i < (size_t)cout * m; i++) {
+                double v = act_fn(d->act, z[i]);
+                a[i] = d->bf16 ? or_round_bf16(v) : v;
+            }
+        }
+    }
+    /* z holds the last layer's output (one channel) */
+    for (size_t i = 0; i < m; i++) out[i] = d->residual ? u[i] + z[i] : z[i];
+    if (d->mass_fix) {
+        double mi = 0.0, mo = 0.0;
+        for (size_t i = 0; i < m; i++) { mi += u[i]; mo += out[i]; }
+        double shift = (mi - mo) / (double)m;
+        for (size_t i = 0; i < m; i++) out[i] += shift;
+    }
+    if (d->limiter)
+        for (size_t i = 0; i < m; i++) out[i] = out[i] < d->lo ? d->lo : (out[i] > d->hi ? d->hi : out[i]);
+    free(a); free(z); free(wr);
+}
+
+void or_cnn_forward(const or_cnn* d, int n, const double* u, double* out) {
+    cnn_forward_impl(d, n, u, out, NULL, NULL);
+}
+
+void or_cnn_forward_batch(const or_cnn* d, int n, int batch, const double* u, double* out) {
+    for (int b = 0; b < batch; b++)
+        cnn_forward_impl(d, n, u + (size_t)b * n * n, out + (size_t)b * n * n, NULL, NULL);
+}
+
+/* Backward pass of the plain stack (residual on, no mass shift, no limiter,
+ * no bf16 rounding): given dL/dout, returns dL/du, dL/dW, dL/db (accumulated
+ * into gw, gb, which the caller zeroes). */
+void or_cnn_backward(const or_cnn* d, int n, const double* u, const double* gout,
+                     double* gin, double* gw, double* gb) {
+    size_t m = (size_t)n * n;
+    int C = d->channels > 1 ? d->channels : 1;
+    int L = d->layers;
+    double* pre = malloc(sizeof(double) * (size_t)L * C * m);
+    double* ins = malloc(sizeof(double) * (size_t)L * C * m);
+    double* out = malloc(sizeof(double) * m);
+    cnn_forward_impl(d, n, u, out, pre, ins);
+    int* woffs = malloc(sizeof(int) * L);
+    int* boffs = malloc(sizeof(int) * L);
+    int woff = 0, boff = 0;
+    for (int l = 0; l < L; l++) {
+        int ci, co; layer_dims(d, l, &ci, &co);
+        woffs[l] = woff; boffs[l] = boff; woff += ci * co * 9; boff += co;
+    }
+    double* gz = malloc(sizeof(double) * C * m);   /* dL/dz_l */
+    double* ga = malloc(sizeof(double) * C * m);   /* dL/da_l (layer input) */
+    memcpy(gz, gout, sizeof(double) * m);          /* last layer: out = u + z_L */
+    for (int l = L - 1; l >= 0; l--) {
+        int cin, cout;
+        layer_dims(d, l, &cin, &cout);
+        const double* W = d->w + woffs[l];
+        const double* a = ins + (size_t)l * C * m;
+        /* db, dW */
+        for (int o = 0; o < cout; o++)
+            for (size_t i = 0; i < m; i++) gb[boffs[l] + o] += gz[(size_t)o * m + i];
+        for (int o = 0; o < cout; o++)
+            for (int c = 0; c < cin; c++)
+                for (int aa = 0; aa < 3; aa++)
+                    for (int e = 0; e < 3; e++) {
+                        double acc = 0.0;
+                        for (int i = 0; i < n; i++)
+                            for (int j = 0; j < n; j++) {
+                                int ii = (i + aa - 1 + n) % n, jj = (j + e - 1 + n) % n;
+                                acc += gz[((size_t)o * n + i) * n + j] * a[((size_t)c * n + ii) * n + jj];
+                            }
+                        gw[woffs[l] + ((o * cin + c) * 3 + aa) * 3 + e] += acc;
+                    }
+        /* d input: scatter each output gradient back through the stencil */
+        memset(ga, 0, sizeof(double) * cin * m);
+        for (int o = 0; o < cout; o++)
+            for (int i = 0; i < n; i++)
+                for (int j = 0; j < n; j++) {
+                    double g = gz[((size_t)o * n + i) * n + j];
+                    for (int c = 0; c < cin; c++)
+                        for (int aa = 0; aa < 3; aa++)
+                            for (int e = 0; e < 3; e++) {
+                                int ii = (i + aa - 1 + n) % n, jj = (j + e - 1 + n) % n;
+                                ga[((size_t)c * n + ii) * n + jj] += W[((o * cin + c) * 3 + aa) * 3 + e] * g;
+                            }
+                }
+        if (l > 0) {
+            const double* zprev = pre + (size_t)(l - 1) * C * m;
+            for (size_t i = 0; i < (size_t)cin * m; i++) gz[i] = ga[i] * act_grad(d->act, zprev[i]);
+        }
+    }
+    for (size_t i = 0; i < m; i++) gin[i] = gout[i] + ga[i];   /* residual skip + stack */
+    free(pre); free(ins); free(out); free(woffs); free(boffs); free(gz); free(ga);
+}
+
+/* ---------------------------------------------------------- Parareal ---- */
+/* Relative L2 and sup-norm increments between two trajectories over slices
+ * j = 1..s (Sec. 3.3 convergence test; relative L2 reading of the tolerance). */
+void or_residual(int s, int n, const double* Unew, const double* Uold, double* l2, double* mx) {
+    size_t m = (size_t)n * n;
+    double num = 0.0, den = 0.0, mxv = 0.0;
+    for (int j = 1; j <= s; j++)
+        for (size_t i = 0; i < m; i++) {
+            double a = Unew[(size_t)j * m + i], d = a - Uold[(size_t)j * m + i];
+            num += d * d;
+            den += a * a;
+            if (fabs(d) > mxv) mxv = fabs(d);
+        }
+    *l2 = den > 0 ? sqrt(num) / sqrt(den) : sqrt(num);
+    *mx = mxv;
+}
+
+/* Algorithm 2.  U: [s+1][n][n] output trajectory (the last iterate).
+ * res_l2 / res_max: per-iteration increments (index k = 1..); iters: the k at
+ * which the loop stopped.  If coarse == NULL, G is the fine propagator itself
+ * with `coarse_steps` fine steps (for the G = F property).  Returns the number
+ * of coarse-propagator evaluations (the cost-model count of Sec. 3.4: the
+ * stored G(U^{k-1}_n) values are reused, and U^k_{k-1} = U^{k-1}_{k-1} makes its
+ * G value known).  G is re-evaluated literally as Algorithm 2 states it only
+ * when `literal` is set. */
+long or_parareal(const or_params* p, const or_cnn* coarse, int coarse_steps, int s, int c,
+                 int kmax, double tol, int literal, const double* u0, double* U,
+                 double* res_l2, double* res_max, int* iters) {
+    int n = p->n;
+    size_t m = (size_t)n * n;
+    double* Uold = malloc(sizeof(double) * m * (s + 1));
+    double* Gold = malloc(sizeof(double) * m * s);
+    double* Ff = malloc(sizeof(double) * m * s);
+    double* g = malloc(sizeof(double) * m);
+    long gcalls = 0;
+#define GAPPLY(in, out) do { if (coarse) or_cnn_forward(coarse, n, (in), (out)); \
+                             else or_fine_propagate(p, coarse_steps, (in), (out)); gcalls++; } while (0)
+    /* k = 0: sequential coarse sweep */
+    memcpy(U, u0, sizeof(double) * m);
+    for (int j = 0; j < s; j++) {
+        GAPPLY(U + j * m, Gold + j * m);
+        memcpy(U + (j + 1) * m, Gold + j * m, sizeof(double) * m);
+    }
+    int k;
+    for (k = 1; k <= kmax && k <= s; k++) {
+        memcpy(Uold, U, sizeof(double) * m * (s + 1));
+        /* fine solves, independent over n = k-1 .. s-1 */
+        for (int j = k - 1; j < s; j++) or_fine_propagate(p, c, Uold + j * m, Ff + j * m);
+        /* sequential correction */
+        for (int j = k - 1; j < s; j++) {
+            if (literal) {
+                double* gn = malloc(sizeof(double) * m);
+                double* go = malloc(sizeof(double) * m);
+                GAPPLY(U + j * m, gn);
+                GAPPLY(Uold + j * m, go);
+                for (size_t i = 0; i < m; i++) U[(j + 1) * m + i] = Ff[j * m + i] + (gn[i] - go[i]);
+                free(gn); free(go);
+            } else {
+                if (j == k - 1) {
+                    /* U^k_{k-1} = U^{k-1}_{k-1}: the new G value is the stored one */
+                    for (size_t i = 0; i < m; i++)
+                        U[(j + 1) * m + i] = Ff[j * m + i] + (Gold[j * m + i] - Gold[j * m + i]);
+                } else {
+                    GAPPLY(U + j * m, g);
+                    for (size_t i = 0; i < m; i++) U[(j + 1) * m + i] = Ff[j * m + i] + (g[i] - Gold[j * m + i]);
+                    memcpy(Gold + j * m, g, sizeof(double) * m);
+                }
+            }
+        }
+        or_residual(s, n, U, Uold, &res_l2[k], &res_max[k]);
+        if (res_l2[k] < tol) break;
+    }
+    if (k > kmax || k > s) k--;
+    *iters = k;
+    free(Uold); free(Gold); free(Ff); free(g);
+#undef GAPPLY
+    return gcalls;
+}
