@@ -1,0 +1,196 @@
+/*
+ * acpr.h -- C ABI of the GB300 (sm_103a) Parareal / Allen-Cahn library.
+ *
+ * The method (Parareal with a learned convolutional coarse propagator for the
+ * classic and mass-conservative Allen-Cahn equations) is the one of Sec. 3 of
+ * "Operator-learning-enabled Parareal for Allen-Cahn equations" (arXiv 2510.07672).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Fields are row-major [batch][n][n] arrays, contiguous, of float64 when the
+ *   precision is AC_F64 and float32 when it is AC_F32.  Grid point (i, j)
+ *   is x = (-L/2 + i h, -L/2 + j h), h = L / n, periodic in both directions
+ *   (Sec. 3.1: N unknowns per side, U^0 = U^N).  Base pointers must be 16-byte
+ *   aligned (what cudaMalloc and torch give).
+ * - Pointers documented as "device" must point to memory of the current CUDA
+ *   device; "host" pointers are ordinary host memory.  The library never takes
+ *   ownership of caller memory.
+ * - Every call is asynchronous on `stream` (NULL = the legacy default stream)
+ *   unless documented as synchronous.  Calls return AC_OK (0) or a negative
+ *   error code; ac_last_error() gives a text message for the calling thread.
+ * - There is no CPU fallback: a call that cannot run on the GPU fails.
+ */
+#ifndef ACPR_H
+#define ACPR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* acpr_stream; /* same type as cudaStream_t */
+
+enum {
+    AC_OK = 0,
+    AC_ERR_ARG = -1,           /* invalid argument (null pointer, bad size, ...) */
+    AC_ERR_UNSUPPORTED = -2,   /* size / precision combination not built */
+    AC_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+    AC_ERR_TIMEOUT = -4,       /* a bounded device-side wait gave up */
+    AC_ERR_NONFINITE = -5,     /* a residual came out NaN or Inf */
+    AC_ERR_NOT_CONVERGED = -6, /* k reached its limit without meeting tol */
+    AC_ERR_NOMEM = -7          /* device allocation failed (create calls only) */
+};
+
+enum { AC_CLASSIC = 0, AC_MASS_CONSERVING = 1 };
+enum { AC_F64 = 0, AC_F32 = 1 };
+enum { AC_ACT_TANH = 0, AC_ACT_GELU = 1 };
+
+/* Problem statement of one Allen-Cahn model on the periodic square (Sec. 2,
+ * Sec. 3.1).  The fine step is the stabilised linear semi-implicit scheme
+ *   (1 + S dt) u' - dt eps^2 Lap_h u' = (1 + S dt) u + dt (f(u) - beta),
+ * f(u) = u - u^3, Lap_h the periodic 5-point Laplacian, beta = 0 for
+ * AC_CLASSIC and beta = mean(f(u)) (the Lagrange multiplier of Eq. mass_AC_eq,
+ * explicit at u) for AC_MASS_CONSERVING. */
+typedef struct {
+    int n;          /* grid points per side: power of two, see ac_fine_supported */
+    double length;  /* side L of the square (the paper uses [-0.5, 0.5]^2, L = 1) */
+    double eps;     /* interface parameter epsilon */
+    double S;       /* stabilisation constant (S >= 2 keeps the MBP) */
+    double dt;      /* fine time step */
+    int variant;    /* AC_CLASSIC or AC_MASS_CONSERVING */
+    int precision;  /* AC_F64 (float64 fields) or AC_F32 (float32 fields) */
+} ac_params;
+
+/* Coarse propagator G: a stack of `layers` 3x3 convolutions with circular
+ * padding 1 (cross-correlation, as torch.nn.Conv2d), widths
+ * 1 -> C -> ... -> C -> 1, activation after every layer but the last, and a
+ * global residual connection out = u + stack(u) when `residual` is set
+ * (Sec. 3.2).  Optional mACNN mass shift (add mean(u) - mean(out)) and bound
+ * limiter (clamp to [lo, hi]), applied in that order after the residual add.
+ *
+ * precision AC_F64: `w`, `b` are device float64 arrays and the conv runs in
+ *   float64 on CUDA cores (fields float64).
+ * precision AC_F32: `w`, `b` are device float32 master arrays; the conv runs
+ *   with bf16 operands (inputs, weights, hidden activations rounded to
+ *   nearest-even bf16) and float32 accumulation, fields float32, residual add
+ *   in float32.  `packed` must then point to cnn_packed_bytes(desc) bytes of
+ *   device memory (caller-owned), filled by cnn_pack_weights() whenever w or b
+ *   change.
+ * Layout of w: concatenation over layers l of W_l[cout][cin][3][3]; b: the
+ * concatenation of b_l[cout]. */
+typedef struct {
+    int layers;      /* >= 1 */
+    int channels;    /* hidden width C (AC_F32: 16, 32 or 64) */
+    int act;         /* AC_ACT_TANH or AC_ACT_GELU (exact erf form) */
+    int residual;    /* 1: global skip connection */
+    int mass_fix;    /* 1: mACNN uniform mass shift */
+    int limiter;     /* 1: clamp to [lo, hi] */
+    double lo, hi;
+    int precision;   /* AC_F64 or AC_F32 */
+    const void* w;   /* device */
+    const void* b;   /* device */
+    void* packed;    /* device, cnn_packed_bytes() bytes (AC_F32), else NULL */
+    void* work;      /* device scratch for hidden activations, caller-owned */
+    size_t work_bytes; /* size of `work`; see cnn_work_bytes() */
+} cnn_desc;
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char* ac_last_error(void);
+
+/* 1 if the fine-step kernels are built for this (n, precision), else 0. */
+int ac_fine_supported(int n, int precision);
+
+/* One fine step (Sec. 3.1 fine operator with one step) for each of `batch`
+ * fields.  u_in, u_out: device [batch][n][n] in params->precision; they may
+ * not overlap.  batch = 0 is a no-op. */
+int ac_fine_step(const ac_params* params, int batch, const void* u_in, void* u_out,
+                 acpr_stream stream);
+
+/* The fine propagator F(t_n, t_{n+1}, U_n) of Eq. (fine_operator): for every
+ * one of `num_fields` independent fields, `steps_per_slice` fine steps
+ * (Algorithm 2: the parallel fine solves of all slices).  The field stays on
+ * chip for all steps; HBM is touched once on entry and once on exit.  In the
+ * mass-conserving variant the spectrum's mean mode is held at the field's
+ * float64 mean taken on entry, so mass is conserved to rounding.
+ * u_starts, u_ends: device [num_fields][n][n]; they may not overlap. */
+int ac_fine_propagate_slices(const ac_params* params, int num_fields, int steps_per_slice,
+                             const void* u_starts, void* u_ends, acpr_stream stream);
+
+/* Bytes of device workspace cnn_desc.packed needs (0 for AC_F64). */
+size_t cnn_packed_bytes(const cnn_desc* desc);
+
+/* Bytes of `work` one cnn_coarse_step call on `batch` n x n fields needs. */
+size_t cnn_work_bytes(const cnn_desc* desc, int n, int batch);
+
+/* Convert the float32 master weights into the packed bf16 layout the tensor
+ * core kernel reads.  Asynchronous on `stream`. */
+int cnn_pack_weights(const cnn_desc* desc, acpr_stream stream);
+
+/* One application of the coarse propagator G (Sec. 3.2) to each of `batch`
+ * fields.  u_in, u_out: device [batch][n][n] (float64 for AC_F64, float32 for
+ * AC_F32); they may not overlap.  n: power of two, 8 <= n <= 1024. */
+int cnn_coarse_step(const cnn_desc* desc, int n, int batch, const void* u_in, void* u_out,
+                    acpr_stream stream);
+
+/* Convergence increment of Algorithm 2 between two trajectories
+ * U[num_slices + 1][n][n] (slice 0, the fixed initial datum, is skipped):
+ *   rel_l2  = sqrt(sum_{j=1..s} |U_new_j - U_old_j|^2) / sqrt(sum_j |U_new_j|^2)
+ *   max_abs = max_{j, x} |U_new_j - U_old_j|            (the paper's sup norm)
+ * accumulated in float64.  SYNCHRONOUS: returns after the results are in the
+ * host doubles *rel_l2_out and *max_abs_out.  Uses a library-owned device
+ * scratch buffer, allocated on the first call on each device and kept until
+ * process exit; calls are serialised by a lock.  Returns AC_ERR_NONFINITE
+ * (with the outputs written) if a NaN or Inf was met. */
+int parareal_residual(int num_slices, int n, int precision, const void* U_new,
+                      const void* U_old, double* rel_l2_out, double* max_abs_out,
+                      acpr_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Parareal driver (Algorithm 2) for `problems` independent problems that
+ * share one ac_params, one coarse propagator, s slices of c fine steps.
+ * ------------------------------------------------------------------------ */
+typedef struct ac_parareal ac_parareal;
+
+/* Allocates the device state (trajectory U[problems][s+1][n][n], stored coarse
+ * values, fine results, residual scratch) and copies the initial data
+ * u0 (device [problems][n][n], precision of params).  *out receives the
+ * handle.  The cnn_desc is copied; its device buffers must outlive the handle. */
+int ac_parareal_create(const ac_params* params, const cnn_desc* coarse, int problems,
+                       int num_slices, int steps_per_slice, const void* u0,
+                       ac_parareal** out);
+
+/* One iteration of Algorithm 2 on every problem not yet converged.
+ * *k_inout = 0 runs the initial coarse sweep U^0_{n+1} = G(U^0_n); k >= 1 runs
+ * the fine solves F(U^{k-1}_n), n = k-1..s-1, then the sequential correction
+ * U^k_{n+1} = G(U^k_n) + F(U^{k-1}_n) - G(U^{k-1}_n) (the new coarse values are
+ * stored for the next iteration), then the convergence increment of each
+ * problem into rel_l2_out[p], max_abs_out[p] (host arrays of `problems`
+ * doubles; untouched for k = 0).  On return *k_inout is k + 1.
+ * SYNCHRONOUS (the increments are read back). */
+int parareal_iterate(ac_parareal* state, int* k_inout, double* rel_l2_out, double* max_abs_out,
+                     acpr_stream stream);
+
+/* Mark problem p converged (it is skipped by later iterations) or active. */
+int ac_parareal_set_active(ac_parareal* state, int problem, int active);
+
+/* Device pointer to the trajectory U[problems][s+1][n][n] (owned by state). */
+const void* ac_parareal_trajectory(const ac_parareal* state);
+
+/* Copy the trajectory U[problems][s+1][n][n] into the device buffer dst
+ * (precision of the params).  Asynchronous on `stream`. */
+int ac_parareal_copy_trajectory(const ac_parareal* state, void* dst, acpr_stream stream);
+
+/* Run iterations until every problem has rel_l2 < tol or k = kmax (k <= s).
+ * iters_out: host int[problems], the iteration at which each problem stopped;
+ * rel_l2_out: host double[problems], its last increment.  SYNCHRONOUS.
+ * Returns AC_ERR_NOT_CONVERGED if a problem reached kmax above tol. */
+int ac_parareal_solve(ac_parareal* state, double tol, int kmax, int* iters_out,
+                      double* rel_l2_out, acpr_stream stream);
+
+void ac_parareal_destroy(ac_parareal* state);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACPR_H */

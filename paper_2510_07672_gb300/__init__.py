@@ -1,0 +1,16 @@
+"""GB300-native Parareal with a convolutional coarse propagator for the classic
+and mass-conservative Allen-Cahn equations (arXiv 2510.07672, Sec. 3).
+
+The compute path is the C-ABI library ``libacpr.so`` (hand-written sm_103a CUDA,
+declared in ``include/acpr.h``).  This package only builds and loads it and
+marshals arguments: torch tensors supply device memory and the current CUDA
+stream.  There is no CPU fallback; every call fails loudly if the library or a
+GPU is missing.
+"""
+from .abi import (  # noqa: F401
+    AC_CLASSIC, AC_MASS_CONSERVING, AC_F64, AC_F32, AC_ACT_TANH, AC_ACT_GELU,
+    AcprError, load, lib_path,
+    ac_fine_supported, ac_fine_step, ac_fine_propagate_slices,
+    cnn_packed_bytes, cnn_work_bytes, cnn_pack_weights, cnn_coarse_step,
+    parareal_residual, Parareal, CoarseNet, FineParams,
+)

@@ -1,0 +1,287 @@
+"""ctypes binding of include/acpr.h: same entry-point names, argument marshalling only.
+
+Device buffers are torch CUDA tensors (contiguous, the dtype of the call's
+precision); the stream is torch's current stream unless one is passed.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+AC_OK = 0
+AC_CLASSIC, AC_MASS_CONSERVING = 0, 1
+AC_F64, AC_F32 = 0, 1
+AC_ACT_TANH, AC_ACT_GELU = 0, 1
+_ERRS = {-1: "AC_ERR_ARG", -2: "AC_ERR_UNSUPPORTED", -3: "AC_ERR_CUDA", -4: "AC_ERR_TIMEOUT",
+         -5: "AC_ERR_NONFINITE", -6: "AC_ERR_NOT_CONVERGED", -7: "AC_ERR_NOMEM"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class AcprError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ac_params(C.Structure):
+    _fields_ = [("n", C.c_int), ("length", C.c_double), ("eps", C.c_double), ("S", C.c_double),
+                ("dt", C.c_double), ("variant", C.c_int), ("precision", C.c_int)]
+
+
+class cnn_desc(C.Structure):
+    _fields_ = [("layers", C.c_int), ("channels", C.c_int), ("act", C.c_int), ("residual", C.c_int),
+                ("mass_fix", C.c_int), ("limiter", C.c_int), ("lo", C.c_double), ("hi", C.c_double),
+                ("precision", C.c_int), ("w", C.c_void_p), ("b", C.c_void_p), ("packed", C.c_void_p),
+                ("work", C.c_void_p), ("work_bytes", C.c_size_t)]
+
+
+EXPORTS = ["ac_last_error", "ac_fine_supported", "ac_fine_step", "ac_fine_propagate_slices",
+           "cnn_packed_bytes", "cnn_work_bytes", "cnn_pack_weights", "cnn_coarse_step",
+           "parareal_residual", "ac_parareal_create", "parareal_iterate", "ac_parareal_set_active",
+           "ac_parareal_trajectory", "ac_parareal_copy_trajectory", "ac_parareal_solve", "ac_parareal_destroy"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libacpr.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"acpr library not built: {path}")
+        L = C.CDLL(path)
+        P, I, D, S = C.POINTER, C.c_int, C.c_double, C.c_void_p
+        L.ac_last_error.restype = C.c_char_p
+        L.ac_fine_supported.argtypes = [I, I]
+        L.ac_fine_step.argtypes = [P(ac_params), I, S, S, S]
+        L.ac_fine_propagate_slices.argtypes = [P(ac_params), I, I, S, S, S]
+        L.cnn_packed_bytes.argtypes = [P(cnn_desc)]
+        L.cnn_packed_bytes.restype = C.c_size_t
+        L.cnn_work_bytes.argtypes = [P(cnn_desc), I, I]
+        L.cnn_work_bytes.restype = C.c_size_t
+        L.cnn_pack_weights.argtypes = [P(cnn_desc), S]
+        L.cnn_coarse_step.argtypes = [P(cnn_desc), I, I, S, S, S]
+        L.parareal_residual.argtypes = [I, I, I, S, S, P(D), P(D), S]
+        L.ac_parareal_create.argtypes = [P(ac_params), P(cnn_desc), I, I, I, S, P(S)]
+        L.parareal_iterate.argtypes = [S, P(I), P(D), P(D), S]
+        L.ac_parareal_set_active.argtypes = [S, I, I]
+        L.ac_parareal_trajectory.argtypes = [S]
+        L.ac_parareal_trajectory.restype = S
+        L.ac_parareal_copy_trajectory.argtypes = [S, S, S]
+        L.ac_parareal_solve.argtypes = [S, D, I, P(I), P(D), S]
+        L.ac_parareal_destroy.argtypes = [S]
+        L.ac_parareal_destroy.restype = None
+        _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != AC_OK:
+        raise AcprError(rc, load().ac_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dtype(precision):
+    import torch
+    return torch.float64 if precision == AC_F64 else torch.float32
+
+
+def _dev(t, dtype=None, name="tensor"):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (no CPU path exists)")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+class FineParams:
+    """Python view of ac_params (Sec. 3.1 problem statement)."""
+
+    def __init__(self, n, eps, S, dt, variant=AC_CLASSIC, precision=AC_F32, length=1.0):
+        self.n, self.eps, self.S, self.dt = int(n), float(eps), float(S), float(dt)
+        self.variant, self.precision, self.length = int(variant), int(precision), float(length)
+
+    def c(self) -> ac_params:
+        return ac_params(self.n, self.length, self.eps, self.S, self.dt, self.variant, self.precision)
+
+    @property
+    def dtype(self):
+        return _dtype(self.precision)
+
+
+def ac_fine_supported(n: int, precision: int) -> bool:
+    return bool(load().ac_fine_supported(int(n), int(precision)))
+
+
+def ac_fine_step(params: FineParams, u_in, u_out=None, stream=None):
+    u_out = u_out if u_out is not None else u_in.new_empty(u_in.shape)
+    batch = u_in.numel() // (params.n * params.n)
+    p = params.c()
+    _check(load().ac_fine_step(C.byref(p), batch, _dev(u_in, params.dtype, "u_in"),
+                               _dev(u_out, params.dtype, "u_out"), _stream(stream)))
+    return u_out
+
+
+def ac_fine_propagate_slices(params: FineParams, steps: int, u_in, u_out=None, stream=None):
+    u_out = u_out if u_out is not None else u_in.new_empty(u_in.shape)
+    fields = u_in.numel() // (params.n * params.n)
+    p = params.c()
+    _check(load().ac_fine_propagate_slices(C.byref(p), fields, int(steps), _dev(u_in, params.dtype, "u_in"),
+                                           _dev(u_out, params.dtype, "u_out"), _stream(stream)))
+    return u_out
+
+
+class CoarseNet:
+    """Device-side conv stack G (Sec. 3.2): owns torch buffers for the weights,
+    the packed bf16 copy and the activation workspace."""
+
+    def __init__(self, layers, channels, w, b, act=AC_ACT_TANH, precision=AC_F32, residual=1,
+                 mass_fix=0, limiter=0, lo=-1.0, hi=1.0, device="cuda"):
+        import torch
+        dt = _dtype(precision)
+        self.layers, self.channels, self.act, self.precision = int(layers), int(channels), int(act), int(precision)
+        self.residual, self.mass_fix, self.limiter, self.lo, self.hi = int(residual), int(mass_fix), int(limiter), float(lo), float(hi)
+        self.w = torch.as_tensor(w, dtype=dt).to(device).contiguous()
+        self.b = torch.as_tensor(b, dtype=dt).to(device).contiguous()
+        self._packed = None
+        self._work = None
+        d = self.desc()
+        nb = load().cnn_packed_bytes(C.byref(d))
+        if nb:
+            self._packed = torch.empty(nb, dtype=torch.uint8, device=device)
+        self.repack()
+
+    def desc(self) -> cnn_desc:
+        return cnn_desc(self.layers, self.channels, self.act, self.residual, self.mass_fix, self.limiter,
+                        self.lo, self.hi, self.precision, self.w.data_ptr(), self.b.data_ptr(),
+                        self._packed.data_ptr() if self._packed is not None else None,
+                        self._work.data_ptr() if self._work is not None else None,
+                        self._work.numel() if self._work is not None else 0)
+
+    def repack(self, stream=None):
+        if self._packed is not None:
+            d = self.desc()
+            _check(load().cnn_pack_weights(C.byref(d), _stream(stream)))
+
+    def ensure_work(self, n, batch):
+        import torch
+        d = self.desc()
+        need = load().cnn_work_bytes(C.byref(d), int(n), int(batch))
+        if self._work is None or self._work.numel() < need:
+            self._work = torch.empty(max(need, 16), dtype=torch.uint8, device=self.w.device)
+
+
+def cnn_packed_bytes(net: CoarseNet) -> int:
+    d = net.desc()
+    return load().cnn_packed_bytes(C.byref(d))
+
+
+def cnn_work_bytes(net: CoarseNet, n: int, batch: int) -> int:
+    d = net.desc()
+    return load().cnn_work_bytes(C.byref(d), int(n), int(batch))
+
+
+def cnn_pack_weights(net: CoarseNet, stream=None):
+    net.repack(stream)
+
+
+def cnn_coarse_step(net: CoarseNet, u_in, u_out=None, stream=None):
+    n = u_in.shape[-1]
+    batch = u_in.numel() // (n * n)
+    net.ensure_work(n, batch)
+    u_out = u_out if u_out is not None else u_in.new_empty(u_in.shape)
+    d = net.desc()
+    dt = _dtype(net.precision)
+    _check(load().cnn_coarse_step(C.byref(d), n, batch, _dev(u_in, dt, "u_in"), _dev(u_out, dt, "u_out"),
+                                  _stream(stream)))
+    return u_out
+
+
+def parareal_residual(U_new, U_old, precision=None, stream=None):
+    """(rel_l2, max_abs) between two [s+1][n][n] trajectories (slices 1..s)."""
+    import torch
+    precision = precision if precision is not None else (AC_F64 if U_new.dtype == torch.float64 else AC_F32)
+    s = U_new.shape[0] - 1
+    n = U_new.shape[-1]
+    l2, mx = C.c_double(), C.c_double()
+    dt = _dtype(precision)
+    _check(load().parareal_residual(s, n, precision, _dev(U_new, dt, "U_new"), _dev(U_old, dt, "U_old"),
+                                    C.byref(l2), C.byref(mx), _stream(stream)))
+    return l2.value, mx.value
+
+
+class Parareal:
+    """Handle on ac_parareal: Algorithm 2 for `problems` independent problems."""
+
+    def __init__(self, params: FineParams, net: CoarseNet, u0, slices: int, steps: int):
+        import torch
+        self.params, self.net = params, net
+        self.problems = u0.shape[0] if u0.dim() == 3 else 1
+        self.s, self.c = int(slices), int(steps)
+        self._u0 = u0.contiguous()
+        p = params.c()
+        d = net.desc()
+        h = C.c_void_p()
+        _check(load().ac_parareal_create(C.byref(p), C.byref(d), self.problems, self.s, self.c,
+                                         _dev(self._u0, params.dtype, "u0"), C.byref(h)))
+        self._h = h
+        self.k = 0
+
+    def iterate(self, stream=None):
+        kk = C.c_int(self.k)
+        l2 = (C.c_double * self.problems)()
+        mx = (C.c_double * self.problems)()
+        _check(load().parareal_iterate(self._h, C.byref(kk), l2, mx, _stream(stream)))
+        self.k = kk.value
+        return list(l2), list(mx)
+
+    def set_active(self, p: int, active: bool):
+        _check(load().ac_parareal_set_active(self._h, int(p), int(active)))
+
+    def solve(self, tol: float, kmax: int, stream=None, allow_unconverged=False):
+        it = (C.c_int * self.problems)()
+        l2 = (C.c_double * self.problems)()
+        rc = load().ac_parareal_solve(self._h, float(tol), int(kmax), it, l2, _stream(stream))
+        if rc != AC_OK and not (allow_unconverged and rc == -6):
+            _check(rc)
+        self.k = max(self.k, max(list(it)) + 1)
+        return list(it), list(l2)
+
+    def trajectory(self, out=None, stream=None):
+        """Copy of U[problems][s+1][n][n] (the last iterate) into a torch tensor."""
+        import torch
+        n = self.params.n
+        if out is None:
+            out = torch.empty((self.problems, self.s + 1, n, n), dtype=self.params.dtype, device="cuda")
+        _check(load().ac_parareal_copy_trajectory(self._h, _dev(out, self.params.dtype, "out"), _stream(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ac_parareal_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+

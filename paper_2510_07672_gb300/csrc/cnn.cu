@@ -1,0 +1,409 @@
+// cnn.cu -- the coarse propagator G (Sec. 3.2): a stack of 3x3 circular-padded
+// convolutions 1 -> C -> ... -> C -> 1 with an activation after every layer but
+// the last and a global residual connection, plus the optional mACNN mass
+// shift and bound limiter.
+//
+// Two numeric paths:
+//   AC_F64: float64 fields, weights and activations; planar [B][C][N][N]
+//           hidden activations; CUDA-core direct convolution.
+//   AC_F32: float32 fields; bf16 conv operands with float32 accumulation;
+//           hidden activations stored as bf16 in the channel-chunked layout
+//           [B][C/8][N][N][8] (16 bytes per pixel and chunk), the layout the
+//           tensor-core layer kernel (cnn_tc.cu) consumes.  The first layer
+//           (1 -> C, K = 9) and the last (C -> 1) run on CUDA cores; the
+//           hidden C -> C layers run on tcgen05 (cnn_tc.cu) when available.
+#include <cuda_bf16.h>
+
+#include "cnn.cuh"
+#include "common.cuh"
+
+namespace acpr {
+
+__device__ __forceinline__ float bf16r(float x) {
+    return __bfloat162float(__float2bfloat16_rn(x));
+}
+
+template <typename T>
+__device__ __forceinline__ T act_apply(int act, T x) {
+    if (act == AC_ACT_TANH) return tanh(x);
+    // exact GELU, x * Phi(x) = 0.5 x (1 + erf(x / sqrt 2))
+    return T(0.5) * x * (T(1) + erf(x * T(0.70710678118654752440)));
+}
+
+__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// ---------------------------------------------------------------- float64 --
+// One thread per output pixel, all output channels.
+// Batch entry b of the input field starts at in + fi(b) * in_bs with
+// fi(b) = in_map ? in_map[b] : b; the output field at out + fo(b) * out_bs with
+// fo(b) = out_map ? out_map[b] : b.  Hidden activations are compact
+// ([b][C]...).  in_mapped / out_mapped tell a layer whether its own input /
+// output is a field (first / last layer) or an activation tensor.
+struct BatchIO {
+    const int* in_map;
+    const int* out_map;
+    long long in_bs, out_bs;
+    int in_mapped, out_mapped;
+};
+
+__device__ __forceinline__ long long bsel(const int* map, int b) { return map ? map[b] : b; }
+
+template <int COUT_MAX>
+__global__ void conv_f64_kernel(const double* __restrict__ in, double* __restrict__ out,
+                                const double* __restrict__ W, const double* __restrict__ bias,
+                                int batch, int n, int cin, int cout, int act, int apply_act,
+                                const double* __restrict__ resid, BatchIO io) {
+    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nn = (long long)n * n;
+    if (pix >= nn * batch) return;
+    const int b = int(pix / nn);
+    const int y = int((pix % nn) / n), x = int(pix % n);
+    const long long fi = bsel(io.in_map, b), fo = bsel(io.out_map, b);
+    const double* inb = io.in_mapped ? in + fi * io.in_bs : in + (long long)b * cin * nn;
+    double* outb = io.out_mapped ? out + fo * io.out_bs : out + (long long)b * cout * nn;
+    double acc[COUT_MAX];
+    for (int o = 0; o < cout; ++o) acc[o] = bias[o];
+    for (int c = 0; c < cin; ++c) {
+        const double* plane = inb + (long long)c * nn;
+        double v[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int e = 0; e < 3; ++e) v[a * 3 + e] = plane[(long long)wrap(y + a - 1, n) * n + wrap(x + e - 1, n)];
+        for (int o = 0; o < cout; ++o) {
+            const double* w = W + ((long long)o * cin + c) * 9;
+            double s = acc[o];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) s += w[t] * v[t];
+            acc[o] = s;
+        }
+    }
+    for (int o = 0; o < cout; ++o) {
+        double z = acc[o];
+        if (apply_act) z = act_apply<double>(act, z);
+        if (resid) z += resid[fi * io.in_bs + (long long)y * n + x];
+        outb[(long long)o * nn + (long long)y * n + x] = z;
+    }
+}
+
+// ------------------------------------------------------------ bf16 / f32 --
+// First layer: float32 field -> bf16 chunked activations (K = 9 on CUDA cores).
+template <int C>
+__global__ void conv_first_bf16_kernel(const float* __restrict__ u, __nv_bfloat16* __restrict__ act,
+                                       const float* __restrict__ W, const float* __restrict__ bias,
+                                       int batch, int n, int act_kind, BatchIO io) {
+    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nn = (long long)n * n;
+    if (pix >= nn * batch) return;
+    const int b = int(pix / nn);
+    const int y = int((pix % nn) / n), x = int(pix % n);
+    const float* f = u + bsel(io.in_map, b) * io.in_bs;
+    float v[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int e = 0; e < 3; ++e) v[a * 3 + e] = bf16r(f[(long long)wrap(y + a - 1, n) * n + wrap(x + e - 1, n)]);
+#pragma unroll
+    for (int kc = 0; kc < C / 8; ++kc) {
+        __align__(16) __nv_bfloat16 o8[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int o = kc * 8 + i;
+            float s = 0.f;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) s = fmaf(bf16r(W[o * 9 + t]), v[t], s);
+            s += bias[o];
+            o8[i] = __float2bfloat16_rn(act_apply<float>(act_kind, s));
+        }
+        *reinterpret_cast<uint4*>(act + ((((long long)b * (C / 8) + kc) * nn) + pix % nn) * 8) =
+            *reinterpret_cast<const uint4*>(o8);
+    }
+}
+
+// Hidden layer C -> C (CUDA-core path).  w: float32 masters [C][C][3][3].
+template <int C>
+__global__ void conv_hidden_bf16_cc_kernel(const __nv_bfloat16* __restrict__ in,
+                                           __nv_bfloat16* __restrict__ out,
+                                           const float* __restrict__ W,
+                                           const float* __restrict__ bias, int batch, int n,
+                                           int act_kind) {
+    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nn = (long long)n * n;
+    if (pix >= nn * batch) return;
+    const int b = int(pix / nn);
+    const int y = int((pix % nn) / n), x = int(pix % n);
+    float acc[C];
+#pragma unroll
+    for (int o = 0; o < C; ++o) acc[o] = 0.f;
+    for (int kc = 0; kc < C / 8; ++kc) {
+        const __nv_bfloat16* plane = in + ((long long)b * (C / 8) + kc) * nn * 8;
+        for (int t = 0; t < 9; ++t) {
+            const int yy = wrap(y + t / 3 - 1, n), xx = wrap(x + t % 3 - 1, n);
+            const uint4 raw = *reinterpret_cast<const uint4*>(plane + ((long long)yy * n + xx) * 8);
+            const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&raw);
+            float v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = __bfloat162float(v8[i]);
+#pragma unroll
+            for (int o = 0; o < C; ++o) {
+                float s = acc[o];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) s = fmaf(bf16r(__ldg(W + ((o * C + kc * 8 + i) * 9 + t))), v[i], s);
+                acc[o] = s;
+            }
+        }
+    }
+#pragma unroll
+    for (int kc = 0; kc < C / 8; ++kc) {
+        __align__(16) __nv_bfloat16 o8[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            o8[i] = __float2bfloat16_rn(act_apply<float>(act_kind, acc[kc * 8 + i] + bias[kc * 8 + i]));
+        *reinterpret_cast<uint4*>(out + ((((long long)b * (C / 8) + kc) * nn) + pix % nn) * 8) =
+            *reinterpret_cast<const uint4*>(o8);
+    }
+}
+
+// Last layer C -> 1 with the residual add in float32.
+template <int C>
+__global__ void conv_last_bf16_kernel(const __nv_bfloat16* __restrict__ in, float* __restrict__ out,
+                                      const float* __restrict__ W, const float* __restrict__ bias,
+                                      const float* __restrict__ u, int batch, int n, int residual,
+                                      BatchIO io) {
+    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nn = (long long)n * n;
+    if (pix >= nn * batch) return;
+    const int b = int(pix / nn);
+    const int y = int((pix % nn) / n), x = int(pix % n);
+    const long long fi = bsel(io.in_map, b), fo = bsel(io.out_map, b);
+    float acc = 0.f;
+    for (int kc = 0; kc < C / 8; ++kc) {
+        const __nv_bfloat16* plane = in + ((long long)b * (C / 8) + kc) * nn * 8;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int yy = wrap(y + t / 3 - 1, n), xx = wrap(x + t % 3 - 1, n);
+            const uint4 raw = *reinterpret_cast<const uint4*>(plane + ((long long)yy * n + xx) * 8);
+            const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&raw);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                acc = fmaf(bf16r(__ldg(W + ((kc * 8 + i) * 9 + t))), __bfloat162float(v8[i]), acc);
+        }
+    }
+    float z = acc + bias[0];
+    if (residual) z += u[fi * io.in_bs + pix % nn];
+    out[fo * io.out_bs + pix % nn] = z;
+}
+
+// mACNN mass shift then bound limiter, one block per field (deterministic
+// float64 reduction of mean(u) - mean(out) in a fixed order).
+template <typename T>
+__global__ void post_kernel(const T* __restrict__ u, T* __restrict__ out, int n, int mass_fix,
+                            int limiter, double lo, double hi, BatchIO io) {
+    const long long nn = (long long)n * n;
+    const T* ub = u + bsel(io.in_map, blockIdx.x) * io.in_bs;
+    T* ob = out + bsel(io.out_map, blockIdx.x) * io.out_bs;
+    __shared__ double red[32];
+    double shift = 0.0;
+    if (mass_fix) {
+        double s = 0.0;
+        for (long long i = threadIdx.x; i < nn; i += blockDim.x) s += double(ub[i]) - double(ob[i]);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[w];
+            red[0] = t / double(nn);
+        }
+        __syncthreads();
+        shift = red[0];
+    }
+    for (long long i = threadIdx.x; i < nn; i += blockDim.x) {
+        double v = double(ob[i]) + shift;
+        if (limiter) v = v < lo ? lo : (v > hi ? hi : v);
+        ob[i] = T(v);
+    }
+}
+
+// ------------------------------------------------------------------ host --
+static void layer_dims(const cnn_desc* d, int l, int* cin, int* cout) {
+    *cin = l == 0 ? 1 : d->channels;
+    *cout = l == d->layers - 1 ? 1 : d->channels;
+}
+
+static size_t weight_count(const cnn_desc* d, size_t* nb) {
+    size_t nw = 0, b = 0;
+    for (int l = 0; l < d->layers; ++l) {
+        int ci, co;
+        layer_dims(d, l, &ci, &co);
+        nw += size_t(ci) * co * 9;
+        b += co;
+    }
+    if (nb) *nb = b;
+    return nw;
+}
+
+int check_cnn(const cnn_desc* d) {
+    ACPR_CHECK_ARG(d != nullptr, "cnn_desc is NULL");
+    ACPR_CHECK_ARG(d->layers >= 2, "need at least 2 layers (1 -> C -> 1), got %d", d->layers);
+    ACPR_CHECK_ARG(d->precision == AC_F64 || d->precision == AC_F32, "bad cnn precision");
+    ACPR_CHECK_ARG(d->act == AC_ACT_TANH || d->act == AC_ACT_GELU, "bad activation %d", d->act);
+    ACPR_CHECK_ARG(d->w && d->b, "null weight pointer");
+    if (d->precision == AC_F64) {
+        ACPR_CHECK_ARG(d->channels >= 1 && d->channels <= 64, "AC_F64 channels must be 1..64");
+    } else if (!(d->channels == 16 || d->channels == 32 || d->channels == 64)) {
+        set_error("AC_F32 conv: channels must be 16, 32 or 64 (got %d)", d->channels);
+        return AC_ERR_UNSUPPORTED;
+    }
+    return AC_OK;
+}
+
+size_t work_bytes_for(const cnn_desc* d, int n, int batch) {
+    const size_t act = size_t(batch) * d->channels * n * n * (d->precision == AC_F64 ? 8 : 2);
+    return 2 * act;
+}
+
+template <int C>
+static int run_f32(const cnn_desc* d, int n, int batch, const float* u, float* out, const BatchIO& io,
+                   cudaStream_t st) {
+    const long long pixels = (long long)n * n * batch;
+    const int threads = 128;
+    const unsigned blocks = unsigned((pixels + threads - 1) / threads);
+    const float* W = static_cast<const float*>(d->w);
+    const float* Bv = static_cast<const float*>(d->b);
+    const size_t act_elems = size_t(batch) * C * n * n;
+    __nv_bfloat16* a0 = static_cast<__nv_bfloat16*>(d->work);
+    __nv_bfloat16* a1 = a0 + act_elems;
+    conv_first_bf16_kernel<C><<<blocks, threads, 0, st>>>(u, a0, W, Bv, batch, n, d->act, io);
+    ACPR_LAUNCH_CHECK();
+    size_t woff = size_t(C) * 9, boff = C;
+    for (int l = 1; l < d->layers - 1; ++l) {
+        int rc = hidden_layer_bf16(d, l, n, batch, a0, a1, W + woff, Bv + boff, st);
+        if (rc == AC_ERR_UNSUPPORTED) {
+            conv_hidden_bf16_cc_kernel<C><<<blocks, threads, 0, st>>>(a0, a1, W + woff, Bv + boff, batch, n, d->act);
+            ACPR_LAUNCH_CHECK();
+        } else if (rc) {
+            return rc;
+        }
+        woff += size_t(C) * C * 9;
+        boff += C;
+        __nv_bfloat16* t = a0; a0 = a1; a1 = t;
+    }
+    conv_last_bf16_kernel<C><<<blocks, threads, 0, st>>>(a0, out, W + woff, Bv + boff, u, batch, n, d->residual, io);
+    ACPR_LAUNCH_CHECK();
+    return AC_OK;
+}
+
+static int run_f64(const cnn_desc* d, int n, int batch, const double* u, double* out, const BatchIO& io,
+                   cudaStream_t st) {
+    const long long pixels = (long long)n * n * batch;
+    const int threads = 128;
+    const unsigned blocks = unsigned((pixels + threads - 1) / threads);
+    const double* W = static_cast<const double*>(d->w);
+    const double* Bv = static_cast<const double*>(d->b);
+    const size_t act_elems = size_t(batch) * d->channels * n * n;
+    double* a0 = static_cast<double*>(d->work);
+    double* a1 = a0 + act_elems;
+    size_t woff = 0, boff = 0;
+    const double* cur = u;
+    for (int l = 0; l < d->layers; ++l) {
+        int cin, cout;
+        layer_dims(d, l, &cin, &cout);
+        const bool last = l == d->layers - 1;
+        double* dst = last ? out : (l % 2 == 0 ? a0 : a1);
+        BatchIO lio = io;
+        lio.in_mapped = l == 0;
+        lio.out_mapped = last;
+        conv_f64_kernel<64><<<blocks, threads, 0, st>>>(cur, dst, W + woff, Bv + boff, batch, n, cin, cout,
+                                                        d->act, last ? 0 : 1, (last && d->residual) ? u : nullptr, lio);
+        ACPR_LAUNCH_CHECK();
+        cur = dst;
+        woff += size_t(cin) * cout * 9;
+        boff += cout;
+    }
+    return AC_OK;
+}
+
+int coarse_step_mapped(const cnn_desc* d, int n, int batch, const void* u_in, long long in_bs,
+                       const int* in_map, void* u_out, long long out_bs, const int* out_map,
+                       cudaStream_t st) {
+    int rc = check_cnn(d);
+    if (rc) return rc;
+    ACPR_CHECK_ARG(batch >= 0, "batch must be >= 0");
+    if (batch == 0) return AC_OK;
+    if (!is_pow2(n) || n < 8 || n > 1024) {
+        set_error("cnn_coarse_step: n=%d unsupported (power of two in [8, 1024])", n);
+        return AC_ERR_UNSUPPORTED;
+    }
+    ACPR_CHECK_ARG(u_in && u_out && u_in != u_out, "bad field pointers");
+    ACPR_CHECK_ARG(d->work && d->work_bytes >= work_bytes_for(d, n, batch),
+                   "cnn work buffer too small: need %zu bytes", work_bytes_for(d, n, batch));
+    BatchIO io;
+    io.in_map = in_map;
+    io.out_map = out_map;
+    io.in_bs = in_bs;
+    io.out_bs = out_bs;
+    io.in_mapped = 1;
+    io.out_mapped = 1;
+    if (d->precision == AC_F64) {
+        rc = run_f64(d, n, batch, static_cast<const double*>(u_in), static_cast<double*>(u_out), io, st);
+    } else {
+        ACPR_CHECK_ARG(d->packed != nullptr, "AC_F32 conv needs the packed weight buffer");
+        const float* ui = static_cast<const float*>(u_in);
+        float* uo = static_cast<float*>(u_out);
+        switch (d->channels) {
+            case 16: rc = run_f32<16>(d, n, batch, ui, uo, io, st); break;
+            case 32: rc = run_f32<32>(d, n, batch, ui, uo, io, st); break;
+            default: rc = run_f32<64>(d, n, batch, ui, uo, io, st); break;
+        }
+    }
+    if (rc) return rc;
+    if (d->mass_fix || d->limiter) {
+        if (d->precision == AC_F64)
+            post_kernel<double><<<batch, 256, 0, st>>>(static_cast<const double*>(u_in), static_cast<double*>(u_out), n,
+                                                       d->mass_fix, d->limiter, d->lo, d->hi, io);
+        else
+            post_kernel<float><<<batch, 256, 0, st>>>(static_cast<const float*>(u_in), static_cast<float*>(u_out), n,
+                                                      d->mass_fix, d->limiter, d->lo, d->hi, io);
+        ACPR_LAUNCH_CHECK();
+    }
+    return AC_OK;
+}
+
+int coarse_step(const cnn_desc* d, int n, int batch, const void* u_in, void* u_out, cudaStream_t st) {
+    const long long nn = (long long)n * n;
+    return coarse_step_mapped(d, n, batch, u_in, nn, nullptr, u_out, nn, nullptr, st);
+}
+
+size_t packed_bytes_for(const cnn_desc* d) {
+    if (d->precision == AC_F64) return 0;
+    return packed_hidden_bytes(d);
+}
+
+}  // namespace acpr
+
+extern "C" size_t cnn_packed_bytes(const cnn_desc* desc) {
+    if (acpr::check_cnn(desc)) return 0;
+    return acpr::packed_bytes_for(desc);
+}
+
+extern "C" size_t cnn_work_bytes(const cnn_desc* desc, int n, int batch) {
+    if (acpr::check_cnn(desc) || n <= 0 || batch < 0) return 0;
+    return acpr::work_bytes_for(desc, n, batch);
+}
+
+extern "C" int cnn_pack_weights(const cnn_desc* desc, acpr_stream stream) {
+    int rc = acpr::check_cnn(desc);
+    if (rc) return rc;
+    if (desc->precision == AC_F64) return AC_OK;
+    if (!desc->packed) {
+        acpr::set_error("cnn_pack_weights: packed buffer is NULL");
+        return AC_ERR_ARG;
+    }
+    return acpr::pack_hidden_weights(desc, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int cnn_coarse_step(const cnn_desc* desc, int n, int batch, const void* u_in, void* u_out,
+                               acpr_stream stream) {
+    return acpr::coarse_step(desc, n, batch, u_in, u_out, reinterpret_cast<cudaStream_t>(stream));
+}

@@ -1,0 +1,33 @@
+// cnn.cuh -- internal interface between the conv-stack driver (cnn.cu) and the
+// tensor-core hidden-layer kernel (cnn_tc.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace acpr {
+
+int check_cnn(const cnn_desc* d);
+int coarse_step(const cnn_desc* d, int n, int batch, const void* u_in, void* u_out, cudaStream_t st);
+// Batch entry b reads the field at u_in + in_map[b] * in_bs and writes the
+// field at u_out + out_map[b] * out_bs (a NULL map means b; strides in
+// elements).
+int coarse_step_mapped(const cnn_desc* d, int n, int batch, const void* u_in, long long in_bs,
+                       const int* in_map, void* u_out, long long out_bs, const int* out_map,
+                       cudaStream_t st);
+size_t work_bytes_for(const cnn_desc* d, int n, int batch);
+
+// Packed bf16 weights of the hidden C -> C layers, per layer
+// [tap 9][k-chunk C/8][cout C][8 input channels] (the K-major core-matrix
+// layout of the tcgen05 B operand).
+size_t packed_hidden_bytes(const cnn_desc* d);
+int pack_hidden_weights(const cnn_desc* d, cudaStream_t st);
+
+// Hidden layer l (1 <= l <= layers - 2) on the tensor cores:
+// in/out are [batch][C/8][n][n][8] bf16.  Returns AC_ERR_UNSUPPORTED when the
+// shape has no tensor-core kernel.
+int hidden_layer_bf16(const cnn_desc* d, int l, int n, int batch, const __nv_bfloat16* in,
+                      __nv_bfloat16* out, const float* w_master, const float* bias, cudaStream_t st);
+
+}  // namespace acpr

@@ -1,0 +1,21 @@
+// errors.cu -- per-thread error text for ac_last_error().
+#include <cstdarg>
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace acpr {
+namespace {
+thread_local char g_err[512] = {0};
+}
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+}  // namespace acpr
+
+extern "C" const char* ac_last_error(void) { return acpr::g_err; }

@@ -1,0 +1,161 @@
+// fft_reg.cuh -- small complex DFTs held entirely in one thread's registers,
+// and the two-pass (four-step) 1D transform of length N = A * B that a group of
+// B threads performs on one line of a field with one shared-memory exchange.
+//
+// Layout invariant ("stride layout"): thread j of a line holds element
+// j + B * t in slot t, t = 0..A-1, both before and after a 1D transform (the
+// output is in natural frequency order).  This lets a forward and an inverse
+// transform follow each other without any reordering.
+#pragma once
+
+#include "common.cuh"
+
+namespace acpr {
+
+// cos(2 pi m / 32) for m = 0..8; other angles follow by symmetry.
+__host__ __device__ constexpr double cos32_quarter(int m) {
+    return m == 0 ? 1.0
+         : m == 1 ? 0.98078528040323044912618223613424
+         : m == 2 ? 0.92387953251128675612818318939679
+         : m == 3 ? 0.83146961230254523707878837761791
+         : m == 4 ? 0.70710678118654752440084436210485
+         : m == 5 ? 0.55557023301960222474283081394853
+         : m == 6 ? 0.38268343236508977172845998403040
+         : m == 7 ? 0.19509032201612826784828486847702
+                  : 0.0;
+}
+
+__host__ __device__ constexpr double cos32(int m) {
+    // cos(2 pi m / 32), m in [0, 32)
+    return m <= 8 ? cos32_quarter(m)
+         : m <= 16 ? -cos32_quarter(16 - m)
+         : m <= 24 ? -cos32_quarter(m - 16)
+                   : cos32_quarter(32 - m);
+}
+__host__ __device__ constexpr double sin32(int m) {
+    // sin(2 pi m / 32) = cos(2 pi (m - 8) / 32)
+    return cos32((m + 24) & 31);
+}
+
+__host__ __device__ constexpr int bit_reverse(int i, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+__host__ __device__ constexpr int ilog2(int m) { return m <= 1 ? 0 : 1 + ilog2(m / 2); }
+
+// (vr + i vi) *= exp(SIGN * 2 pi i m / 32), m a compile-time constant after
+// unrolling; quarter turns are done as swaps.
+template <typename T, int SIGN>
+__device__ __forceinline__ void twiddle32(int m, T& vr, T& vi) {
+    if (m == 0) return;
+    if (m == 8) {  // multiply by SIGN * i
+        T t = vr;
+        vr = -T(SIGN) * vi;
+        vi = T(SIGN) * t;
+        return;
+    }
+    const T c = T(cos32(m));
+    const T s = T(SIGN) * T(sin32(m));
+    T r = vr * c - vi * s;
+    vi = vr * s + vi * c;
+    vr = r;
+}
+
+// One butterfly stage of span LEN, then the next (template recursion keeps
+// every index a compile-time constant so the arrays stay in registers).
+template <typename T, int M, int SIGN, int LEN>
+__device__ __forceinline__ void dit_stages(T (&re)[M], T (&im)[M]) {
+    if constexpr (LEN <= M) {
+#pragma unroll
+        for (int i = 0; i < M; i += LEN) {
+#pragma unroll
+            for (int k = 0; k < LEN / 2; ++k) {
+                T vr = re[i + k + LEN / 2], vi = im[i + k + LEN / 2];
+                twiddle32<T, SIGN>(k * (32 / LEN), vr, vi);
+                const T ur = re[i + k], ui = im[i + k];
+                re[i + k] = ur + vr;
+                im[i + k] = ui + vi;
+                re[i + k + LEN / 2] = ur - vr;
+                im[i + k + LEN / 2] = ui - vi;
+            }
+        }
+        dit_stages<T, M, SIGN, 2 * LEN>(re, im);
+    }
+}
+
+// In-register radix-2 DIT DFT of size M (M <= 32, power of two),
+// X_k = sum_j x_j exp(SIGN 2 pi i j k / M), natural order in and out.
+template <typename T, int M, int SIGN>
+__device__ __forceinline__ void reg_dft(T (&re)[M], T (&im)[M]) {
+    static_assert(M >= 1 && M <= 32 && (M & (M - 1)) == 0, "M must be a power of two <= 32");
+    constexpr int bits = ilog2(M);
+    T r2[M], i2[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        r2[bit_reverse(i, bits)] = re[i];
+        i2[bit_reverse(i, bits)] = im[i];
+    }
+#pragma unroll
+    for (int i = 0; i < M; ++i) { re[i] = r2[i]; im[i] = i2[i]; }
+    dit_stages<T, M, SIGN, 2>(re, im);
+}
+
+// One line transform of length N = A * B by the B threads of that line.
+//   x:    this thread's A elements (stride layout), transformed in place.
+//   tw:   shared table exp(-2 pi i m / N), m = 0..N-1 (the inverse uses the
+//         conjugates); every lane of a warp reads the same entry (broadcast).
+//   line: base of this line's exchange area in shared memory (>= N elements);
+//   j:    this thread's lane within the line.
+// Unnormalised, X_k = sum_n x_n exp(SIGN 2 pi i n k / N).
+// Contains __syncthreads(): every thread of the block must call it.
+template <typename T, int N, int A, int B, int SIGN>
+__device__ __forceinline__ void line_fft(vec2_t<T> (&x)[A], const vec2_t<T>* __restrict__ tw,
+                                         vec2_t<T>* line, int j) {
+    static_assert(A * B == N && A % B == 0, "N = A * B with B | A");
+    T re[A], im[A];
+#pragma unroll
+    for (int t = 0; t < A; ++t) { re[t] = x[t].x; im[t] = x[t].y; }
+    // pass 1: A-point DFT over n1 of x[B n1 + j]
+    reg_dft<T, A, SIGN>(re, im);
+    // twiddle exp(SIGN 2 pi i j k1 / N)
+#pragma unroll
+    for (int k1 = 1; k1 < A; ++k1) {
+        const vec2_t<T> w = tw[(j * k1) & (N - 1)];
+        const T c = w.x;
+        const T s = SIGN < 0 ? w.y : -w.y;
+        const T r = re[k1] * c - im[k1] * s;
+        im[k1] = re[k1] * s + im[k1] * c;
+        re[k1] = r;
+    }
+    __syncthreads();  // previous readers of `line` are done
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) {
+        vec2_t<T> v;
+        v.x = re[k1];
+        v.y = im[k1];
+        line[k1 * B + j] = v;
+    }
+    __syncthreads();
+    // pass 2: for k1 = j + B m, a B-point DFT over n2
+#pragma unroll
+    for (int m = 0; m < A / B; ++m) {
+        const int k1 = j + B * m;
+        T br[B], bi[B];
+#pragma unroll
+        for (int n2 = 0; n2 < B; ++n2) {
+            const vec2_t<T> v = line[k1 * B + n2];
+            br[n2] = v.x;
+            bi[n2] = v.y;
+        }
+        reg_dft<T, B, SIGN>(br, bi);
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) {
+            // output index k1 + A k2 = j + B (m + (A/B) k2)
+            x[m + (A / B) * k2].x = br[k2];
+            x[m + (A / B) * k2].y = bi[k2];
+        }
+    }
+}
+
+}  // namespace acpr

@@ -1,0 +1,411 @@
+// fine.cu -- the fine propagator F: stabilised semi-implicit Allen-Cahn steps
+// on a periodic n x n grid, many independent fields at once.
+//
+// One step (Sec. 3.1 fine operator, the stabilised linear scheme):
+//   r      = (1 + S dt) u + dt f(u),                f(u) = u - u^3
+//   u_hat' = FFT2(r)_kl / (N^2 D_kl),   D_kl = 1 + S dt + dt eps^2 (mu_k + mu_l),
+//   u'     = IFFT2(u_hat')               (unnormalised inverse),
+// mu_k = (4/h^2) sin^2(pi k / N) (minus the eigenvalues of the periodic 5-point
+// Laplacian).  For the mass-conserving model (Eq. mass_AC_eq) the Lagrange
+// multiplier beta = mean f(u) only moves the (0,0) mode, where it cancels
+// dt * mean f(u); the (0,0) mode of u_hat' is therefore the mean of u, which
+// the kernel holds at the float64 mean taken when the field was loaded.
+//
+// GB300 mapping.  A thread-block cluster of P CTAs owns one field for all
+// `steps` steps; CTA q holds rows [qR, qR + R), R = N / P.  The field is real,
+// so two rows of the same field travel as the real and imaginary parts of one
+// complex line (rows qR + l and qR + l + R/2): every rounding then depends on
+// this field alone, which makes F a deterministic function of its input, the
+// property that lets converged Parareal slices stop changing bitwise.
+//   row phase:    R/2 complex lines per CTA, N-point row FFTs;
+//   transpose:    the row spectra Z_p[k] go straight into the peer CTAs'
+//                 shared memory (DSMEM), column c receiving Z_p[c] and
+//                 Z_p[N - c] of every row pair p;
+//   column phase: the column owner splits each pair into the two real rows'
+//                 half spectra (Hermitian symmetry), N/2 complex columns per
+//                 field with the real DC and Nyquist columns packed into
+//                 column 0, N-point column FFTs, symbol divide, inverse;
+//   and back the same way.  Each 1D transform is a two-pass radix-A x radix-B
+// register FFT with one shared-memory exchange.  Two cluster barriers per step
+// order the transposes; HBM is read once when the field is loaded and written
+// once when it is stored.
+#include "common.cuh"
+#include "fft_reg.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace acpr {
+
+struct FineArgs {
+    const void* in;
+    void* out;
+    int num_fields;
+    int steps;
+    // Field f = g * per_group + i reads field (map[g] * in_gs + in_off + i) of
+    // `in` and writes field (map[g] * out_gs + out_off + i) of `out` (map NULL:
+    // identity).  Plain batched calls use per_group = num_fields.
+    int per_group;
+    long long in_gs, in_off, out_gs, out_off;
+    const int* map;
+    int mass;        // 1: hold the (0,0) mode at the entry mean
+    double a;        // 1 + S dt
+    double dt;
+    double lam_scale;  // dt eps^2 (4 / h^2)
+};
+
+template <typename T, int N, int P, int A, int B>
+struct FineShape {
+    static constexpr int R = N / P;           // rows per CTA
+    static constexpr int L = R / 2;           // lines per CTA (row pairs, then columns)
+    static constexpr int HALF = N / 2;
+    static constexpr int THREADS = L * B;     // (line, lane) pairs
+    static constexpr int PITCH = N + 1;       // complex elements per smem line
+    static constexpr size_t BUF = sizeof(vec2_t<T>) * size_t(L) * PITCH;
+    static constexpr size_t SMEM = 2 * BUF + sizeof(vec2_t<T>) * N + sizeof(T) * N + 4 * sizeof(double);
+    static_assert(R >= 2 && R % 2 == 0, "need at least two rows per CTA");
+};
+
+template <int P>
+__device__ __forceinline__ void cluster_barrier() {
+    if constexpr (P > 1) {
+        cg::this_cluster().sync();
+    } else {
+        __syncthreads();
+    }
+}
+
+template <int P, typename V>
+__device__ __forceinline__ V* peer_ptr(V* local, int rank) {
+    if constexpr (P > 1) {
+        return cg::this_cluster().map_shared_rank(local, rank);
+    } else {
+        return local;
+    }
+}
+
+template <typename T, int N, int P, int A, int B>
+__global__ void __launch_bounds__(FineShape<T, N, P, A, B>::THREADS, (FineShape<T, N, P, A, B>::THREADS <= 256 ? 2 : 1))
+fine_field_kernel(FineArgs args) {
+    using Sh = FineShape<T, N, P, A, B>;
+    using V = vec2_t<T>;
+    constexpr int R = Sh::R, L = Sh::L, HALF = Sh::HALF, PITCH = Sh::PITCH;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* bufR = reinterpret_cast<V*>(smem_raw);         // row-phase lines
+    V* bufC = bufR + L * PITCH;                        // column-phase lines
+    V* tw = bufC + L * PITCH;                          // exp(-2 pi i m / N)
+    T* lam = reinterpret_cast<T*>(tw + N);             // dt eps^2 mu_k
+    double* part = reinterpret_cast<double*>(lam + N); // mass partial
+
+    const int tid = threadIdx.x;
+    const int j = tid / L;       // lane within a line
+    const int line = tid % L;    // local line index
+    int rank = 0;
+    if constexpr (P > 1) rank = int(cg::this_cluster().block_rank());
+    const int field = blockIdx.x / P;
+    const size_t NN = size_t(N) * N;
+    long long fin, fout;
+    {
+        const int g = field / args.per_group, i = field % args.per_group;
+        const long long pg = args.map ? args.map[g] : g;
+        fin = pg * args.in_gs + args.in_off + i;
+        fout = pg * args.out_gs + args.out_off + i;
+    }
+    const T* in = static_cast<const T*>(args.in) + size_t(fin) * NN + size_t(rank) * R * N;
+    T* out = static_cast<T*>(args.out) + size_t(fout) * NN + size_t(rank) * R * N;
+
+    for (int k = tid; k < N; k += Sh::THREADS) {
+        double sn, cs;
+        sincospi(-2.0 * double(k) / N, &sn, &cs);
+        tw[k].x = T(cs);
+        tw[k].y = T(sn);
+        const double s = sinpi(double(k) / N);
+        lam[k] = T(args.lam_scale * s * s);
+    }
+
+    // load rows [rank R, rank R + R): line l holds rows l (real) and l + L (imag)
+    double msum = 0.0;
+    for (int idx = tid; idx < R * N; idx += Sh::THREADS) {
+        const int row = idx / N, c = idx % N;
+        const T v = in[idx];
+        msum += double(v);
+        reinterpret_cast<T*>(bufR)[2 * ((row % L) * PITCH + c) + row / L] = v;
+    }
+    double mean = 0.0;
+    if (args.mass) {
+        // float64 sum: warp shuffle, one value per warp, then the cluster
+        constexpr int WARP = Sh::THREADS < 32 ? Sh::THREADS : 32;
+        constexpr unsigned MASK = WARP == 32 ? 0xffffffffu : ((1u << WARP) - 1u);
+#pragma unroll
+        for (int o = WARP / 2; o > 0; o >>= 1) msum += __shfl_xor_sync(MASK, msum, o, WARP);
+        double* wsum = reinterpret_cast<double*>(bufC);  // scratch before first use
+        if ((tid % WARP) == 0) wsum[tid / WARP] = msum;
+        __syncthreads();
+        if (tid == 0) {
+            double sa = 0.0;
+            for (int w = 0; w < Sh::THREADS / WARP; ++w) sa += wsum[w];
+            part[0] = sa;
+        }
+        cluster_barrier<P>();
+        double sa = 0.0;
+        for (int q = 0; q < P; ++q) sa += *peer_ptr<P>(part, q);
+        mean = sa / double(NN);
+        cluster_barrier<P>();  // peers are done reading `part`
+    }
+    __syncthreads();
+
+    V x[A];
+    V* myR = bufR + line * PITCH;
+    V* myC = bufC + line * PITCH;
+#pragma unroll
+    for (int t = 0; t < A; ++t) x[t] = myR[j + B * t];
+
+    const T a = T(args.a);
+    const T dt = T(args.dt);
+    const T inv_nn = T(1.0 / double(NN));
+    const T half = T(0.5);
+    const int pair = rank * L + line;  // global row-pair index (row phase)
+    const int col = rank * L + line;   // global column index (column phase)
+    for (int step = 0; step < args.steps; ++step) {
+        // pointwise right-hand side on both rows of the line
+#pragma unroll
+        for (int t = 0; t < A; ++t) {
+            const T ur = x[t].x, ui = x[t].y;
+            x[t].x = a * ur + dt * (ur - ur * ur * ur);
+            x[t].y = a * ui + dt * (ui - ui * ui * ui);
+        }
+        line_fft<T, N, A, B, -1>(x, tw, myR, j);
+        // row spectra Z_p[k] -> column min(k, N - k) (k = 0, N/2 -> column 0)
+#pragma unroll
+        for (int t = 0; t < A; ++t) {
+            const int k = j + B * t;
+            const int c = (k == HALF) ? 0 : (k < HALF ? k : N - k);
+            const int slot = (k == 0 || k < HALF) ? 0 : 1;
+            V* dst = peer_ptr<P>(bufC, c / L);
+            dst[(c % L) * PITCH + slot * HALF + pair] = x[t];
+        }
+        cluster_barrier<P>();
+        // split each row pair into its two rows' half spectra
+#pragma unroll
+        for (int t = 0; t < A; ++t) {
+            const int r = j + B * t;
+            const int lr = r % R;
+            const int pp = (r / R) * L + (lr % L);
+            const V za = myC[pp], zb = myC[HALF + pp];
+            V v;
+            if (col == 0) {  // packed DC and Nyquist columns
+                if (lr < L) { v.x = za.x; v.y = zb.x; }
+                else        { v.x = za.y; v.y = zb.y; }
+            } else if (lr < L) {  // (za + conj zb) / 2
+                v.x = half * (za.x + zb.x);
+                v.y = half * (za.y - zb.y);
+            } else {              // (za - conj zb) / (2i)
+                v.x = half * (za.y + zb.y);
+                v.y = half * (zb.x - za.x);
+            }
+            x[t] = v;
+        }
+        line_fft<T, N, A, B, -1>(x, tw, myC, j);
+        // divide by the symbol, with 1/N^2 of the inverse folded in
+        if (col != 0) {
+            const T lam_l = lam[col];
+#pragma unroll
+            for (int t = 0; t < A; ++t) {
+                const T s = inv_nn / (a + (lam[j + B * t] + lam_l));
+                x[t].x *= s;
+                x[t].y *= s;
+            }
+        }
+        {
+            // column 0 carries columns 0 and N/2 as C = F0 + i FN: separate
+            // them with C[N - k], scale each by its own symbol, recombine:
+            // C'[k] = C[k] (s0 + sN) / 2 + conj(C[N - k]) (s0 - sN) / 2
+            __syncthreads();
+            if (col == 0) {
+#pragma unroll
+                for (int t = 0; t < A; ++t) myC[j + B * t] = x[t];
+            }
+            __syncthreads();
+            if (col == 0) {
+                const T lam_n = lam[HALF];
+#pragma unroll
+                for (int t = 0; t < A; ++t) {
+                    const int k = j + B * t;
+                    const V zc = x[t];
+                    const V zp = myC[(N - k) & (N - 1)];
+                    const T lk = lam[k];
+                    const T s0 = inv_nn / (a + lk);
+                    const T sn = inv_nn / (a + (lk + lam_n));
+                    const T sp = half * (s0 + sn), sm = half * (s0 - sn);
+                    x[t].x = zc.x * sp + zp.x * sm;
+                    x[t].y = zc.y * sp - zp.y * sm;
+                    if (k == 0 && args.mass) {
+                        // mean mode of u held at the entry mean (F0'(0) = mean)
+                        x[t].x = T(mean);
+                        x[t].y = zc.y * sn;
+                    }
+                }
+            }
+        }
+        line_fft<T, N, A, B, +1>(x, tw, myC, j);
+        // column values V_r[c] -> owner of row r, slot (row role) and column c
+#pragma unroll
+        for (int t = 0; t < A; ++t) {
+            const int r = j + B * t;
+            const int lr = r % R;
+            V* dst = peer_ptr<P>(bufR, r / R);
+            dst[(lr % L) * PITCH + (lr / L) * HALF + col] = x[t];
+        }
+        cluster_barrier<P>();
+        // rebuild each pair's full row spectrum from the half spectra
+#pragma unroll
+        for (int t = 0; t < A; ++t) {
+            const int k = j + B * t;
+            V z;
+            if (k == 0 || k == HALF) {
+                const V va = myR[0], vb = myR[HALF];
+                if (k == 0) { z.x = va.x; z.y = vb.x; }
+                else        { z.x = va.y; z.y = vb.y; }
+            } else if (k < HALF) {  // Va + i Vb
+                const V va = myR[k], vb = myR[HALF + k];
+                z.x = va.x - vb.y;
+                z.y = va.y + vb.x;
+            } else {                // conj(Va) + i conj(Vb) at N - k
+                const V va = myR[N - k], vb = myR[HALF + N - k];
+                z.x = va.x + vb.y;
+                z.y = vb.x - va.y;
+            }
+            x[t] = z;
+        }
+        line_fft<T, N, A, B, +1>(x, tw, myR, j);
+    }
+
+    // store rows, coalesced, through bufR
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < A; ++t) myR[j + B * t] = x[t];
+    __syncthreads();
+    for (int idx = tid; idx < R * N; idx += Sh::THREADS) {
+        const int row = idx / N, c = idx % N;
+        out[idx] = reinterpret_cast<const T*>(bufR)[2 * ((row % L) * PITCH + c) + row / L];
+    }
+}
+
+// ---------------------------------------------------------------- launch --
+template <typename T, int N, int P, int A, int B>
+static int launch_fine(const FineArgs& args, cudaStream_t stream) {
+    using Sh = FineShape<T, N, P, A, B>;
+    auto kern = fine_field_kernel<T, N, P, A, B>;
+    static bool configured = false;  // attribute set once per process and device 0.. (idempotent)
+    if (!configured) {
+        ACPR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::SMEM)));
+        if (P > 8)
+            ACPR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        configured = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(args.num_fields * P), 1, 1);
+    cfg.blockDim = dim3(Sh::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = Sh::SMEM;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = P;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ACPR_CUDA(cudaLaunchKernelEx(&cfg, kern, args));
+    return AC_OK;
+}
+
+// (precision, n) -> instantiated shape: N = A * B with B | A, P CTAs per field.
+template <typename T>
+static int dispatch_fine(int n, const FineArgs& args, cudaStream_t stream) {
+    constexpr bool F32 = sizeof(T) == 4;
+    switch (n) {
+        case 8: return launch_fine<T, 8, 1, 4, 2>(args, stream);
+        case 16: return launch_fine<T, 16, 1, 4, 4>(args, stream);
+        case 32: return launch_fine<T, 32, 1, 8, 4>(args, stream);
+        case 64: return launch_fine<T, 64, 1, 8, 8>(args, stream);
+        case 128:
+            if constexpr (F32) return launch_fine<T, 128, 2, 16, 8>(args, stream);
+            else return launch_fine<T, 128, 4, 16, 8>(args, stream);
+        case 256:
+            if constexpr (F32) return launch_fine<T, 256, 8, 16, 16>(args, stream);
+            else return launch_fine<T, 256, 8, 16, 16>(args, stream);
+        default: break;
+    }
+    set_error("ac_fine: n=%d not built for %s", n, F32 ? "AC_F32" : "AC_F64");
+    return AC_ERR_UNSUPPORTED;
+}
+
+static bool fine_built(int n, int) {
+    return n == 8 || n == 16 || n == 32 || n == 64 || n == 128 || n == 256;
+}
+
+static int check_params(const ac_params* p) {
+    ACPR_CHECK_ARG(p != nullptr, "ac_params is NULL");
+    ACPR_CHECK_ARG(p->precision == AC_F32 || p->precision == AC_F64, "bad precision %d", p->precision);
+    ACPR_CHECK_ARG(p->variant == AC_CLASSIC || p->variant == AC_MASS_CONSERVING, "bad variant %d", p->variant);
+    ACPR_CHECK_ARG(p->length > 0 && p->dt > 0 && p->eps >= 0 && p->S >= 0,
+                   "need length > 0, dt > 0, eps >= 0, S >= 0");
+    if (!is_pow2(p->n) || !fine_built(p->n, p->precision)) {
+        set_error("ac_fine: n=%d (precision %d) not supported", p->n, p->precision);
+        return AC_ERR_UNSUPPORTED;
+    }
+    return AC_OK;
+}
+
+int fine_propagate_mapped(const ac_params* p, int groups, int per_group, int steps, const void* in,
+                          long long in_gs, long long in_off, void* out, long long out_gs,
+                          long long out_off, const int* map, cudaStream_t stream) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    ACPR_CHECK_ARG(groups >= 0 && per_group >= 0 && steps >= 0, "counts must be >= 0");
+    if (groups == 0 || per_group == 0) return AC_OK;
+    ACPR_CHECK_ARG(in && out, "null field pointer");
+    ACPR_CHECK_ARG(in != out, "u_in and u_out must not overlap");
+    ACPR_CHECK_ARG((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % 16 == 0,
+                   "field pointers must be 16-byte aligned");
+    ACPR_CHECK_ARG((long long)groups * per_group < (1LL << 30), "too many fields");
+    FineArgs a;
+    a.in = in;
+    a.out = out;
+    a.num_fields = groups * per_group;
+    a.steps = steps;
+    a.per_group = per_group;
+    a.in_gs = in_gs;
+    a.in_off = in_off;
+    a.out_gs = out_gs;
+    a.out_off = out_off;
+    a.map = map;
+    a.mass = p->variant == AC_MASS_CONSERVING;
+    a.a = 1.0 + p->S * p->dt;
+    a.dt = p->dt;
+    const double h = p->length / p->n;
+    a.lam_scale = p->dt * p->eps * p->eps * 4.0 / (h * h);
+    if (p->precision == AC_F64) return dispatch_fine<double>(p->n, a, stream);
+    return dispatch_fine<float>(p->n, a, stream);
+}
+
+int fine_propagate(const ac_params* p, int num_fields, int steps, const void* in, void* out,
+                   cudaStream_t stream) {
+    return fine_propagate_mapped(p, 1, num_fields, steps, in, 0, 0, out, 0, 0, nullptr, stream);
+}
+
+}  // namespace acpr
+
+extern "C" int ac_fine_supported(int n, int precision) {
+    return acpr::is_pow2(n) && acpr::fine_built(n, precision) ? 1 : 0;
+}
+
+extern "C" int ac_fine_step(const ac_params* params, int batch, const void* u_in, void* u_out,
+                            acpr_stream stream) {
+    return acpr::fine_propagate(params, batch, 1, u_in, u_out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int ac_fine_propagate_slices(const ac_params* params, int num_fields, int steps_per_slice,
+                                        const void* u_starts, void* u_ends, acpr_stream stream) {
+    return acpr::fine_propagate(params, num_fields, steps_per_slice, u_starts, u_ends,
+                                reinterpret_cast<cudaStream_t>(stream));
+}

@@ -1,0 +1,67 @@
+"""Host-side checks of the C-ABI library: it builds for sm_103a, loads, and
+exports every function include/acpr.h declares; argument validation runs on the
+host and never touches a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_2510_07672_gb300 as G
+from paper_2510_07672_gb300 import abi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z_0-9]*\s*\**\s*([a-z_][a-z_0-9]*)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    L = G.load()
+    decl = declared_functions()
+    assert len(decl) >= 15
+    missing = [n for n in decl if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(abi.EXPORTS) <= set(decl)
+
+
+def test_supported_sizes():
+    assert G.ac_fine_supported(256, G.AC_F32)
+    assert G.ac_fine_supported(64, G.AC_F64)
+    assert not G.ac_fine_supported(48, G.AC_F32)
+    assert not G.ac_fine_supported(4096, G.AC_F32)
+
+
+def test_argument_errors_are_reported_on_the_host():
+    L = G.load()
+    assert L.ac_fine_step(None, 1, None, None, None) == -1
+    assert b"NULL" in L.ac_last_error()
+    p = abi.ac_params(48, 1.0, 0.01, 2.0, 1e-4, 0, 1)
+    assert L.ac_fine_step(C.byref(p), 1, None, None, None) == -2      # unsupported size
+    p = abi.ac_params(64, 1.0, 0.01, 2.0, -1.0, 0, 1)
+    assert L.ac_fine_step(C.byref(p), 1, None, None, None) == -1      # dt <= 0
+    p = abi.ac_params(64, 1.0, 0.01, 2.0, 1e-4, 0, 1)
+    assert L.ac_fine_step(C.byref(p), 0, None, None, None) == 0       # empty batch is a no-op
+    assert L.ac_fine_step(C.byref(p), 2, None, None, None) == -1      # null fields
+    d = abi.cnn_desc(4, 24, 0, 1, 0, 0, -1.0, 1.0, 1, None, None, None, None, 0)
+    assert L.cnn_coarse_step(C.byref(d), 64, 1, None, None, None) == -1   # null weights first
+    d = abi.cnn_desc(4, 24, 0, 1, 0, 0, -1.0, 1.0, 1, 16, 16, None, None, 0)
+    assert L.cnn_coarse_step(C.byref(d), 64, 1, None, None, None) == -2   # C=24 not built for bf16
+    h = C.c_void_p()
+    assert L.ac_parareal_create(None, None, 1, 1, 1, None, C.byref(h)) == -1
+    assert L.parareal_iterate(None, None, None, None, None) == -1
+
+
+def test_binding_refuses_cpu_tensors():
+    torch = pytest.importorskip("torch")
+    fp = G.FineParams(64, 0.01, 2.0, 1e-4)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        G.ac_fine_step(fp, torch.zeros(1, 64, 64))

@@ -1,0 +1,72 @@
+"""GPU parity of the coarse propagator (cnn_coarse_step) against the oracle.
+
+float64 mode: 1e-12 max-abs (the same arithmetic up to summation order and
+libm vs CUDA tanh/erf ulps).
+bf16 mode: compared with the oracle's bf16-emulating mode (weights, conv input
+and hidden activations rounded to bf16, everything else float64).  The kernel
+accumulates in float32 and so may round an activation to the neighbouring bf16
+value (a relative change of 2^-8 in that activation); with weights of size
+sigma the effect on the output is of order 2^-8 * sigma * |activation| per
+flip, so the test allows 2e-3 * sigma-scaled max-abs and checks that the
+median error is at float32 level.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import acpr_inputs as I
+import oracle as O
+import paper_2510_07672_gb300 as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n,L,C,act", [(64, 4, 16, 0), (32, 3, 5, 1), (16, 2, 1, 0)])
+def test_cnn_f64(n, L, C, act):
+    w, b = I.cnn_weights(L, C, seed=1, sigma=0.3)
+    u = np.stack([I.random_field(n, seed=s) for s in range(3)])
+    net = G.CoarseNet(L, C, w, b, act=act, precision=G.AC_F64)
+    got = G.cnn_coarse_step(net, torch.tensor(u, device="cuda")).cpu().numpy()
+    spec = O.CnnSpec(L, C, w, b, act=act)
+    ref = O.cnn_forward(spec, u)
+    assert np.abs(got - ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("n,L,C,act,sigma", [(64, 6, 32, 1, 0.1), (32, 4, 16, 0, 0.2), (16, 8, 64, 1, 0.05),
+                                             (256, 6, 32, 1, 0.01)])
+def test_cnn_bf16(n, L, C, act, sigma):
+    w, b = I.cnn_weights(L, C, seed=2, sigma=sigma)
+    u = np.stack([I.random_field(n, seed=s) for s in range(2)]).astype(np.float32)
+    w32, b32 = w.astype(np.float32), b.astype(np.float32)
+    net = G.CoarseNet(L, C, w32, b32, act=act, precision=G.AC_F32)
+    got = G.cnn_coarse_step(net, torch.tensor(u, device="cuda")).double().cpu().numpy()
+    spec = O.CnnSpec(L, C, w32.astype(np.float64), b32.astype(np.float64), act=act, bf16=1)
+    ref = O.cnn_forward(spec, u.astype(np.float64))
+    err = np.abs(got - ref)
+    scale = max(np.abs(ref - u).max(), 1e-3)  # size of the stack's contribution
+    assert err.max() < 2e-2 * scale + 1e-6
+    assert np.median(err) < 1e-3 * scale + 1e-7
+
+
+def test_cnn_mass_fix_and_limiter_f64():
+    n, L, C = 32, 3, 4
+    w, b = I.cnn_weights(L, C, seed=5, sigma=0.5)
+    u = I.random_field(n, seed=1)[None]
+    net = G.CoarseNet(L, C, w, b, act=0, precision=G.AC_F64, mass_fix=1, limiter=1, lo=-0.6, hi=0.6)
+    got = G.cnn_coarse_step(net, torch.tensor(u, device="cuda")).cpu().numpy()
+    ref = O.cnn_forward(O.CnnSpec(L, C, w, b, act=0, mass_fix=1, limiter=1, lo=-0.6, hi=0.6), u[0])
+    assert np.abs(got[0] - ref).max() < 1e-12
+
+
+def test_cnn_deterministic():
+    """Same input, same output bits (no atomics): needed for the exactness of
+    Parareal (U^k_k equals the fine result bitwise)."""
+    n, L, C = 64, 6, 32
+    w, b = I.cnn_weights(L, C, seed=3, sigma=0.05)
+    net = G.CoarseNet(L, C, w.astype(np.float32), b.astype(np.float32), act=1, precision=G.AC_F32)
+    u = torch.tensor(I.random_field(n, 0)[None].repeat(4, 0), dtype=torch.float32, device="cuda")
+    a = G.cnn_coarse_step(net, u)
+    bb = G.cnn_coarse_step(net, u)
+    assert torch.equal(a, bb)
+    assert torch.equal(a[0], a[3])

@@ -1,0 +1,123 @@
+"""GPU parity of the fine propagator (ac_fine_step, ac_fine_propagate_slices)
+against the float64 oracle, through the C ABI.
+
+Tolerances: float64 mode 1e-10 max-abs end to end; float32 mode 2e-5 max-abs
+per fine step (the FFT round-off of an N^2-point float32 transform is about
+eps_32 * log2(N^2) * |u| ~ 1e-6), and 2e-5 * sqrt(steps) over a slice, whose
+errors add like a random walk while the scheme damps them.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import acpr_inputs as I
+import oracle as O
+import paper_2510_07672_gb300 as G
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a, dtype):
+    return torch.tensor(np.asarray(a), dtype=dtype, device="cuda")
+
+
+CASES_F64 = [(8, 0), (16, 1), (32, 0), (64, 0), (64, 1), (128, 1)]
+CASES_F32 = [(16, 0), (64, 1), (128, 0), (128, 1), (256, 0), (256, 1)]
+
+
+@pytest.mark.parametrize("n,variant", CASES_F64)
+def test_fine_step_f64(n, variant):
+    eps = 2.5 / n
+    batch = 3  # odd: the last pair carries one field
+    u = np.stack([I.random_field(n, seed=10 + i, zero_mean=bool(variant)) for i in range(batch)])
+    fp = G.FineParams(n, eps, 2.0, 1e-4, variant=variant, precision=G.AC_F64)
+    got = G.ac_fine_step(fp, dev(u, torch.float64)).cpu().numpy()
+    p = O.params(n, eps, 2.0, 1e-4, variant)
+    for i in range(batch):
+        assert np.abs(got[i] - O.fine_step(p, u[i])).max() < 1e-12
+
+
+@pytest.mark.parametrize("n,variant", CASES_F32)
+def test_fine_step_f32(n, variant):
+    eps = 2.5 / n
+    batch = 5
+    u = np.stack([I.random_field(n, seed=20 + i, zero_mean=bool(variant)) for i in range(batch)])
+    u32 = u.astype(np.float32)
+    fp = G.FineParams(n, eps, 2.0, 5e-5, variant=variant, precision=G.AC_F32)
+    got = G.ac_fine_step(fp, dev(u32, torch.float32)).cpu().numpy()
+    p = O.params(n, eps, 2.0, 5e-5, variant)
+    for i in range(batch):
+        ref = O.fine_step(p, u32[i].astype(np.float64))
+        assert np.abs(got[i] - ref).max() < 2e-5
+
+
+@pytest.mark.parametrize("n,variant,steps", [(64, 0, 100), (64, 1, 60), (128, 1, 20)])
+def test_propagate_f64(n, variant, steps):
+    eps = 0.025 if n == 64 else 2.5 / n
+    u = np.stack([I.random_field(n, seed=i, zero_mean=bool(variant)) for i in range(2)])
+    fp = G.FineParams(n, eps, 2.0, 1e-4, variant=variant, precision=G.AC_F64)
+    got = G.ac_fine_propagate_slices(fp, steps, dev(u, torch.float64)).cpu().numpy()
+    p = O.params(n, eps, 2.0, 1e-4, variant)
+    for i in range(2):
+        assert np.abs(got[i] - O.fine_propagate(p, steps, u[i])).max() < 1e-10
+
+
+@pytest.mark.parametrize("n,variant,steps", [(128, 0, 50), (256, 1, 200)])
+def test_propagate_f32(n, variant, steps):
+    eps = 0.01 if n == 256 else 2.5 / n
+    u = np.stack([I.random_field(n, seed=40 + i, zero_mean=bool(variant)) for i in range(3)]).astype(np.float32)
+    fp = G.FineParams(n, eps, 2.0, 5e-5, variant=variant, precision=G.AC_F32)
+    got = G.ac_fine_propagate_slices(fp, steps, dev(u, torch.float32)).double().cpu().numpy()
+    p = O.params(n, eps, 2.0, 5e-5, variant)
+    ref = O.fine_propagate(p, steps, u[1].astype(np.float64))
+    assert np.abs(got[1] - ref).max() < 2e-5 * np.sqrt(steps)
+    if variant:
+        # mass held at its float64 entry value to float32 rounding
+        for i in range(3):
+            assert abs(got[i].mean() - u[i].astype(np.float64).mean()) < 1e-7
+
+
+def test_propagate_zero_steps_and_empty():
+    n = 64
+    u = dev(I.random_field(n, 1)[None].repeat(3, 0), torch.float32)
+    fp = G.FineParams(n, 0.04, 2.0, 1e-4, precision=G.AC_F32)
+    out = G.ac_fine_propagate_slices(fp, 0, u)
+    assert torch.equal(out, u)
+    empty = torch.empty(0, n, n, device="cuda")
+    assert G.ac_fine_propagate_slices(fp, 10, empty).numel() == 0
+
+
+def test_mass_conservation_long_run_f32():
+    """Mass stays at its entry value over 2000 steps (the mean mode is held)."""
+    n = 256
+    u = I.random_field(n, seed=3)
+    u = (u - u.mean() + 0.1).astype(np.float32)
+    m0 = u.astype(np.float64).mean()
+    fp = G.FineParams(n, 0.01, 2.0, 5e-5, variant=G.AC_MASS_CONSERVING, precision=G.AC_F32)
+    out = G.ac_fine_propagate_slices(fp, 2000, dev(u[None], torch.float32))
+    assert abs(out.double().mean().item() - m0) < 1e-7
+    assert out.abs().max().item() <= 2 / np.sqrt(3) + 1e-4
+
+
+def test_maximum_bound_principle_f32():
+    n = 128
+    u = I.random_field(n, seed=4, amp=1.0).astype(np.float32)
+    fp = G.FineParams(n, 2.5 / n, 2.0, 1e-2, variant=G.AC_CLASSIC, precision=G.AC_F32)
+    out = G.ac_fine_propagate_slices(fp, 300, dev(u[None], torch.float32))
+    assert out.abs().max().item() <= 1.0 + 1e-5
+
+
+def test_full_size_sampled():
+    """The 256^2 mass-conserving workload in the bench's launch shape (512
+    fields, 200 steps); sampled fields are checked against the oracle."""
+    n, steps = 256, 200
+    w = I.MASS_F32_256
+    ics = np.stack([I.random_field(n, seed=s, zero_mean=True) for s in range(512)]).astype(np.float32)
+    fp = G.FineParams(n, w.eps, w.S, w.dt, variant=w.variant, precision=G.AC_F32)
+    out = G.ac_fine_propagate_slices(fp, steps, dev(ics, torch.float32)).double().cpu().numpy()
+    p = O.params(n, w.eps, w.S, w.dt, w.variant)
+    for f in (0, 311, 511):
+        ref = O.fine_propagate(p, steps, ics[f].astype(np.float64))
+        assert np.abs(out[f] - ref).max() < 2e-5 * np.sqrt(steps)
+    assert np.isfinite(out).all()

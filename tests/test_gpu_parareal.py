@@ -1,0 +1,103 @@
+"""GPU parity of the Parareal driver (parareal_iterate / ac_parareal_solve) and
+the convergence increment (parareal_residual) against the oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import acpr_inputs as I
+import oracle as O
+import paper_2510_07672_gb300 as G
+
+pytestmark = pytest.mark.gpu
+
+
+def test_residual_matches_oracle():
+    s, n = 5, 64
+    a = np.random.default_rng(0).standard_normal((s + 1, n, n))
+    b = a + 1e-3 * np.random.default_rng(1).standard_normal((s + 1, n, n))
+    for dt in (torch.float64, torch.float32):
+        A = torch.tensor(a, dtype=dt, device="cuda")
+        B = torch.tensor(b, dtype=dt, device="cuda")
+        l2, mx = G.parareal_residual(A, B)
+        rl2, rmx = O.residual(A.double().cpu().numpy(), B.double().cpu().numpy())
+        assert abs(l2 - rl2) <= 1e-12 * rl2
+        assert mx == rmx
+
+
+def test_residual_nonfinite_is_reported():
+    s, n = 2, 16
+    A = torch.zeros(s + 1, n, n, device="cuda")
+    B = torch.zeros(s + 1, n, n, device="cuda")
+    A[2, 3, 4] = float("nan")
+    with pytest.raises(G.AcprError, match="NONFINITE"):
+        G.parareal_residual(A, B)
+
+
+def test_plain_f64_workload_end_to_end():
+    """64^2 classic AC in float64, 8 slices x 100 steps, tanh conv 1-16-16-16-1
+    with N(0, 0.01^2) weights: every iteration's increment and the final
+    trajectory match the oracle to 1e-10."""
+    w = I.PLAIN_F64_64
+    u0 = w.ics()
+    wt, bs = w.weights()
+    fp = G.FineParams(w.n, w.eps, w.S, w.dt, variant=w.variant, precision=G.AC_F64)
+    net = G.CoarseNet(w.layers, w.channels, wt, bs, act=w.act, precision=G.AC_F64)
+    pr = G.Parareal(fp, net, torch.tensor(u0, device="cuda"), w.slices, w.steps)
+    pr.iterate()  # k = 0
+    incs = []
+    for k in range(1, w.kmax + 1):
+        l2, mx = pr.iterate()
+        incs.append(l2[0])
+    U = pr.trajectory()[0].cpu().numpy()
+    ref = O.parareal(O.params(w.n, w.eps, w.S, w.dt, w.variant), O.CnnSpec(w.layers, w.channels, wt, bs, act=w.act),
+                     w.slices, w.steps, kmax=w.kmax, tol=0.0, u0=u0[0])
+    assert np.abs(U - ref["U"]).max() < 1e-10
+    assert np.allclose(incs, ref["res_l2"], rtol=1e-6, atol=1e-14)
+
+
+def test_exactness_on_gpu_f32():
+    """After k iterations slices 0..k equal the GPU's own sequential fine solve
+    bitwise (Sec. 3.3), in float32 with the bf16 conv."""
+    n, s, c = 64, 6, 30
+    fp = G.FineParams(n, 0.04, 2.0, 1e-4, variant=G.AC_MASS_CONSERVING, precision=G.AC_F32)
+    wt, bs = I.cnn_weights(6, 32, seed=0)
+    net = G.CoarseNet(6, 32, wt.astype(np.float32), bs.astype(np.float32), act=1, precision=G.AC_F32)
+    u0 = torch.tensor(np.stack([I.random_field(n, 7, zero_mean=True), I.random_field(n, 8, zero_mean=True)]),
+                      dtype=torch.float32, device="cuda")
+    seq = [u0]
+    for j in range(s):
+        seq.append(G.ac_fine_propagate_slices(fp, c, seq[-1]))
+    seq = torch.stack(seq, 1)  # [problems][s+1][n][n]
+    pr = G.Parareal(fp, net, u0, s, c)
+    pr.iterate()
+    for k in range(1, s + 1):
+        pr.iterate()
+        U = pr.trajectory()
+        assert torch.equal(U[:, : k + 1], seq[:, : k + 1]), k
+    assert torch.equal(U, seq)
+
+
+def test_mass_f32_workload_small_converges_like_oracle():
+    """A reduced mass-conserving float32 problem (64^2, 8 slices): the solve
+    stops on the 1e-6 increment and its trajectory is within 1e-5 (relative
+    L2) of the oracle's float64 sequential fine solve, the limit Parareal
+    converges to."""
+    n, s, c = 64, 8, 50
+    eps, S, dt = 0.04, 2.0, 5e-5
+    wt, bs = I.cnn_weights(6, 32, seed=0)
+    u0 = np.stack([I.random_field(n, seed=p, zero_mean=True) for p in range(3)])
+    fp = G.FineParams(n, eps, S, dt, variant=1, precision=G.AC_F32)
+    net = G.CoarseNet(6, 32, wt.astype(np.float32), bs.astype(np.float32), act=1, precision=G.AC_F32)
+    pr = G.Parareal(fp, net, torch.tensor(u0, dtype=torch.float32, device="cuda"), s, c)
+    its, l2 = pr.solve(tol=1e-6, kmax=s)
+    U = pr.trajectory().double().cpu().numpy()
+    for p in range(3):
+        assert l2[p] < 1e-6 or its[p] == s
+        op = O.params(n, eps, S, dt, 1)
+        fine = [u0[p].astype(np.float32).astype(np.float64)]
+        for j in range(s):
+            fine.append(O.fine_propagate(op, c, fine[-1]))
+        fine = np.stack(fine)
+        rel = np.linalg.norm(U[p] - fine) / np.linalg.norm(fine)
+        assert rel < 1e-5
