@@ -1,0 +1,321 @@
+"""Benchmark: Parareal solves of the 256^2 mass-conserving Allen-Cahn workload.
+
+One step = one complete Parareal solve (Algorithm 2) of 16 independent
+problems: 256 x 256 periodic grid, eps = 0.01, S = 2, dt = 5e-5, 32 slices of
+200 fine steps, zero-mean U(-0.9, 0.9) initial data, coarse propagator
+1 -> 32 x 6 layers of 3x3 circular conv with GELU (bf16 operands, float32
+accumulation, N(0, 0.01^2) weights), iterated until every problem's relative
+L2 increment is below 1e-6 (or k = s, where Parareal is exact).
+
+value = delivered fine trajectory throughput of the solve,
+        problems * slices * steps * n^2 / (device time of one solve)   [cell-steps/s]
+The sequential float32 fine solve of the same problems (the same fine kernel,
+slices one after another, all 16 problems per launch) is timed next to it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank solves its own 16 problems (replicas; the
+path has no exchange between problems) and rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import acpr_inputs as I  # noqa: E402
+
+METRIC = "Parareal time-to-1e-6 vs sequential fine on GB300; fine cell-steps/s, %roofline"
+UNIT = "cell-steps/s"
+WL = I.MASS_F32_256
+
+
+def fine_flops_per_cell_step(n: int) -> float:
+    """Algorithmic flops of one fine step per grid cell: a forward and an
+    inverse real 2D FFT at 2.5 * M * log2(M) flops each (M = n^2), plus 10
+    pointwise flops (right-hand side and symbol divide)."""
+    return 5.0 * np.log2(n * n) + 10.0
+
+
+def peak_fp32_tflops(sm_mhz: float) -> float:
+    """FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop (FMA) x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def conv_flops_per_cell(layers: int, C: int) -> float:
+    return float(sum(2 * 9 * ci * co for ci, co in I.cnn_layer_dims(layers, C)))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(n: int, steps: int, variant: int, seed: int = 0):
+    """The float64 oracle's fine propagation of one field on one host core."""
+    import oracle as O
+    O.build()
+    p = O.params(n, WL.eps, WL.S, WL.dt, variant)
+    u = I.random_field(n, seed=seed, zero_mean=True)
+    t0 = time.perf_counter()
+    O.fine_propagate(p, steps, u)
+    dt = time.perf_counter() - t0
+    return steps * n * n / dt, dt
+
+
+def run_reference(args, rank: int, world: int):
+    """The oracle, timed on the host cores, on the same workload and metric."""
+    if rank != 0:
+        return
+    steps_per_sample = 40
+    for _ in range(args.warmup):
+        cpu_oracle_rate(WL.n, 4, WL.variant)
+    rates, times = [], []
+    for k in range(args.steps):
+        r, t = cpu_oracle_rate(WL.n, steps_per_sample, WL.variant, seed=k)
+        rates.append(r)
+        times.append(t)
+    value = float(np.median(rates))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WL.name, "n": WL.n, "problems": WL.problems, "slices": WL.slices,
+                   "steps_per_slice": WL.steps},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{steps_per_sample} fine steps of one {WL.n}^2 field per step "
+                                   "(float64 oracle, sequential fine throughput; upper bound of its "
+                                   "Parareal delivered rate on one core)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    # host-side oracle sample first (before any GPU work in this process)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, secs = cpu_oracle_rate(WL.n, 150, WL.variant)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"150 fine steps of one {WL.n}^2 mass-conserving field on one core, float64 "
+                         f"({secs:.1f} s); the oracle's sequential fine rate bounds its Parareal rate"}
+
+    import torch
+    import torch.distributed as dist
+    import paper_2510_07672_gb300 as G
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank)
+    G.load()
+
+    fp = G.FineParams(WL.n, WL.eps, WL.S, WL.dt, variant=WL.variant, precision=G.AC_F32)
+    wt, bs = WL.weights()
+    net = G.CoarseNet(WL.layers, WL.channels, wt.astype(np.float32), bs.astype(np.float32),
+                      act=WL.act, precision=G.AC_F32, device=dev)
+    ics = WL.ics().astype(np.float32)  # same 16 problems on every rank (weak scaling replicas)
+    u0 = torch.tensor(ics, device=dev)
+    pr = G.Parareal(fp, net, u0, WL.slices, WL.steps)
+    pr.enable_timing(True)
+    stream = torch.cuda.current_stream()
+
+    def solve():
+        pr.reset(u0)
+        its, l2 = pr.solve(tol=WL.tol, kmax=WL.kmax)
+        return its, l2
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        its, l2 = solve()
+    barrier()
+    pr.reset_stats()
+    n_launch0 = G.ac_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            its, l2 = solve()
+        e1.record(stream)
+        barrier()
+    launches = G.ac_launch_count() - n_launch0
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st = pr.stats()
+    clocks = clk.summary()
+
+    cells = WL.problems * WL.slices * WL.steps * WL.n * WL.n  # delivered per solve per rank
+    value = world * cells / (ms * 1e-3)
+
+    # sequential float32 fine solve of the same problems, same kernel
+    seq_in = u0.clone()
+    seq_out = torch.empty_like(seq_in)
+
+    def sequential():
+        a, b = seq_in, seq_out
+        for _ in range(WL.slices):
+            G.ac_fine_propagate_slices(fp, WL.steps, a, b)
+            a, b = b, a
+        return a
+
+    sequential()
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    sequential()
+    s1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = s0.elapsed_time(s1)
+
+    # end to end through the public API: pinned host ICs in, final fields out
+    host_u0 = torch.tensor(ics).pin_memory()
+    host_out = torch.empty((WL.problems, WL.n, WL.n), dtype=torch.float32).pin_memory()
+    traj = torch.empty((WL.problems, WL.slices + 1, WL.n, WL.n), dtype=torch.float32, device=dev)
+    dev_u0 = torch.empty_like(u0)
+
+    def e2e_step():
+        dev_u0.copy_(host_u0, non_blocking=True)
+        pr.reset(dev_u0)
+        pr.solve(tol=WL.tol, kmax=WL.kmax)
+        pr.trajectory(out=traj)
+        host_out.copy_(traj[:, -1], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank == 0:
+        peaks, src = measured_peaks()
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        fpc = fine_flops_per_cell_step(WL.n)
+        fine_tflops = st["fine_cell_steps"] * fpc / (st["fine_ms"] * 1e-3) / 1e12 if st["fine_ms"] else 0.0
+        peak = peak_fp32_tflops(sm_mhz)
+        conv_tflops = (st["coarse_cells"] * conv_flops_per_cell(WL.layers, WL.channels) /
+                       (st["coarse_ms"] * 1e-3) / 1e12) if st["coarse_ms"] else 0.0
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WL.name, "n": WL.n, "problems": WL.problems, "slices": WL.slices,
+                       "steps_per_slice": WL.steps, "variant": "mass-conserving", "conv": "1-32x6-1 gelu bf16",
+                       "tol": WL.tol, "l2": "state larger than L2 (trajectories, stored G and F values: 0.54 GB)",
+                       "parallelism": f"replicas x{world}"},
+            "iterations": its, "final_rel_l2": l2,
+            "sequential_ms": seq_ms, "parareal_ms": ms,
+            "speedup_vs_sequential": seq_ms / ms,
+            "phase_ms_per_solve": {"fine": st["fine_ms"] / args.steps, "coarse": st["coarse_ms"] / args.steps,
+                                   "increment": st["increment_ms"] / args.steps},
+            "fine_cell_steps_per_s": st["fine_cell_steps"] / (st["fine_ms"] * 1e-3) if st["fine_ms"] else None,
+            "conv_tflops": conv_tflops,
+            "roofline": {"bound": "alu", "kernel": "fine_field_kernel", "achieved": fine_tflops,
+                         "peak": peak, "unit": "TFLOP/s", "frac": fine_tflops / peak,
+                         "traffic": None,
+                         "peak_source": f"FP32 lanes x 2 x sm_max_mhz {sm_mhz:.0f} from {src} peaks",
+                         "flops_per_cell_step": fpc},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * cells / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(host_u0.numel() * 4), "d2h_bytes_per_step": int(host_out.numel() * 4)},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    pr.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

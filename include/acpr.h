@@ -182,11 +182,40 @@ const void* ac_parareal_trajectory(const ac_parareal* state);
 int ac_parareal_copy_trajectory(const ac_parareal* state, void* dst, acpr_stream stream);
 
 /* Run iterations until every problem has rel_l2 < tol or k = kmax (k <= s).
+ * A problem that reaches k = s stops there: its trajectory is then the fine
+ * solve itself (Sec. 3.3).  A non-finite increment (a diverging iterate beyond
+ * the exact prefix) counts as not converged and the iterations go on.
  * iters_out: host int[problems], the iteration at which each problem stopped;
  * rel_l2_out: host double[problems], its last increment.  SYNCHRONOUS.
- * Returns AC_ERR_NOT_CONVERGED if a problem reached kmax above tol. */
+ * Returns AC_ERR_NOT_CONVERGED if a problem reached kmax < s above tol. */
 int ac_parareal_solve(ac_parareal* state, double tol, int kmax, int* iters_out,
                       double* rel_l2_out, acpr_stream stream);
+
+/* Restart the handle at k = 0 from new initial data u0 (device
+ * [problems][n][n]); every problem becomes active.  Asynchronous on `stream`. */
+int ac_parareal_reset(ac_parareal* state, const void* u0, acpr_stream stream);
+
+/* Per-phase device time of the iterations run since the last reset of the
+ * statistics, measured with CUDA events on the iteration's stream when timing
+ * is on (ac_parareal_enable_timing), plus work counters. */
+typedef struct {
+    double fine_ms;          /* fine-propagator launches */
+    double coarse_ms;        /* coarse sweeps (conv stack and corrections) */
+    double increment_ms;     /* convergence increments */
+    long long fine_launches;
+    long long fine_cell_steps;  /* sum over fine launches of fields * steps * n^2 */
+    long long coarse_calls;     /* applications of G to a batch of problems */
+    long long coarse_cells;     /* sum over G applications of batch * n^2 */
+    long long iterations;
+} ac_parareal_stats;
+
+int ac_parareal_enable_timing(ac_parareal* state, int on);
+int ac_parareal_get_stats(const ac_parareal* state, ac_parareal_stats* out);
+int ac_parareal_reset_stats(ac_parareal* state);
+
+/* Number of kernels this library has launched in this process (all entry
+ * points, all devices).  Lets a caller count the launches of a region. */
+long long ac_launch_count(void);
 
 void ac_parareal_destroy(ac_parareal* state);
 

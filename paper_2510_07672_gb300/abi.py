@@ -40,10 +40,18 @@ class cnn_desc(C.Structure):
                 ("work", C.c_void_p), ("work_bytes", C.c_size_t)]
 
 
+class ac_parareal_stats(C.Structure):
+    _fields_ = [("fine_ms", C.c_double), ("coarse_ms", C.c_double), ("increment_ms", C.c_double),
+                ("fine_launches", C.c_longlong), ("fine_cell_steps", C.c_longlong),
+                ("coarse_calls", C.c_longlong), ("coarse_cells", C.c_longlong),
+                ("iterations", C.c_longlong)]
+
+
 EXPORTS = ["ac_last_error", "ac_fine_supported", "ac_fine_step", "ac_fine_propagate_slices",
            "cnn_packed_bytes", "cnn_work_bytes", "cnn_pack_weights", "cnn_coarse_step",
            "parareal_residual", "ac_parareal_create", "parareal_iterate", "ac_parareal_set_active",
-           "ac_parareal_trajectory", "ac_parareal_copy_trajectory", "ac_parareal_solve", "ac_parareal_destroy"]
+           "ac_parareal_trajectory", "ac_parareal_copy_trajectory", "ac_parareal_solve", "ac_parareal_reset", "ac_parareal_enable_timing",
+           "ac_parareal_get_stats", "ac_parareal_reset_stats", "ac_launch_count", "ac_parareal_destroy"]
 
 
 def lib_path() -> str:
@@ -79,6 +87,11 @@ def load(build_if_missing: bool = True):
         L.ac_parareal_trajectory.restype = S
         L.ac_parareal_copy_trajectory.argtypes = [S, S, S]
         L.ac_parareal_solve.argtypes = [S, D, I, P(I), P(D), S]
+        L.ac_parareal_reset.argtypes = [S, S, S]
+        L.ac_parareal_enable_timing.argtypes = [S, I]
+        L.ac_parareal_get_stats.argtypes = [S, P(ac_parareal_stats)]
+        L.ac_parareal_reset_stats.argtypes = [S]
+        L.ac_launch_count.restype = C.c_longlong
         L.ac_parareal_destroy.argtypes = [S]
         L.ac_parareal_destroy.restype = None
         _lib = L
@@ -214,6 +227,10 @@ def cnn_coarse_step(net: CoarseNet, u_in, u_out=None, stream=None):
     return u_out
 
 
+def ac_launch_count() -> int:
+    return int(load().ac_launch_count())
+
+
 def parareal_residual(U_new, U_old, precision=None, stream=None):
     """(rel_l2, max_abs) between two [s+1][n][n] trajectories (slices 1..s)."""
     import torch
@@ -272,6 +289,22 @@ class Parareal:
             out = torch.empty((self.problems, self.s + 1, n, n), dtype=self.params.dtype, device="cuda")
         _check(load().ac_parareal_copy_trajectory(self._h, _dev(out, self.params.dtype, "out"), _stream(stream)))
         return out
+
+    def reset(self, u0, stream=None):
+        self._u0 = u0.contiguous()
+        _check(load().ac_parareal_reset(self._h, _dev(self._u0, self.params.dtype, "u0"), _stream(stream)))
+        self.k = 0
+
+    def enable_timing(self, on=True):
+        _check(load().ac_parareal_enable_timing(self._h, int(on)))
+
+    def stats(self) -> dict:
+        st = ac_parareal_stats()
+        _check(load().ac_parareal_get_stats(self._h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in ac_parareal_stats._fields_}
+
+    def reset_stats(self):
+        _check(load().ac_parareal_reset_stats(self._h))
 
     def close(self):
         if getattr(self, "_h", None):

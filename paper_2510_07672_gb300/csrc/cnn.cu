@@ -19,17 +19,6 @@
 
 namespace acpr {
 
-__device__ __forceinline__ float bf16r(float x) {
-    return __bfloat162float(__float2bfloat16_rn(x));
-}
-
-template <typename T>
-__device__ __forceinline__ T act_apply(int act, T x) {
-    if (act == AC_ACT_TANH) return tanh(x);
-    // exact GELU, x * Phi(x) = 0.5 x (1 + erf(x / sqrt 2))
-    return T(0.5) * x * (T(1) + erf(x * T(0.70710678118654752440)));
-}
-
 __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 // ---------------------------------------------------------------- float64 --

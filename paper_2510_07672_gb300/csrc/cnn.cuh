@@ -8,6 +8,18 @@
 
 namespace acpr {
 
+__device__ __forceinline__ float bf16r(float x) {
+    return __bfloat162float(__float2bfloat16_rn(x));
+}
+
+// Activation after every conv but the last: tanh, or the exact (erf) GELU
+// x * Phi(x) = 0.5 x (1 + erf(x / sqrt 2)).
+template <typename T>
+__device__ __forceinline__ T act_apply(int act, T x) {
+    if (act == AC_ACT_TANH) return tanh(x);
+    return T(0.5) * x * (T(1) + erf(x * T(0.70710678118654752440)));
+}
+
 int check_cnn(const cnn_desc* d);
 int coarse_step(const cnn_desc* d, int n, int batch, const void* u_in, void* u_out, cudaStream_t st);
 // Batch entry b reads the field at u_in + in_map[b] * in_bs and writes the
@@ -27,6 +39,11 @@ int pack_hidden_weights(const cnn_desc* d, cudaStream_t st);
 // Hidden layer l (1 <= l <= layers - 2) on the tensor cores:
 // in/out are [batch][C/8][n][n][8] bf16.  Returns AC_ERR_UNSUPPORTED when the
 // shape has no tensor-core kernel.
+// Device-side timeout flag of the tensor-core kernels: returns AC_ERR_TIMEOUT
+// (and clears the flag) if a bounded wait gave up since the last call.
+// Synchronises the stream.
+int tc_check_status(cudaStream_t st);
+
 int hidden_layer_bf16(const cnn_desc* d, int l, int n, int batch, const __nv_bfloat16* in,
                       __nv_bfloat16* out, const float* w_master, const float* bias, cudaStream_t st);
 

@@ -32,9 +32,14 @@ void set_error(const char* fmt, ...);
         }                                                                            \
     } while (0)
 
-// Check a kernel launch (configuration errors are reported synchronously).
+// Kernels launched by the library (ac_launch_count()).
+void count_launch();
+
+// Check a kernel launch (configuration errors are reported synchronously) and
+// count it.
 #define ACPR_LAUNCH_CHECK()                                                          \
     do {                                                                             \
+        ::acpr::count_launch();                                                      \
         cudaError_t e_ = cudaGetLastError();                                         \
         if (e_ != cudaSuccess) {                                                     \
             ::acpr::set_error("%s:%d: kernel launch: %s", __FILE__, __LINE__,        \

@@ -1,4 +1,5 @@
 // errors.cu -- per-thread error text for ac_last_error().
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 
@@ -7,7 +8,10 @@
 namespace acpr {
 namespace {
 thread_local char g_err[512] = {0};
+std::atomic<long long> g_launches{0};
 }
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
     va_list ap;
@@ -19,3 +23,5 @@ void set_error(const char* fmt, ...) {
 }  // namespace acpr
 
 extern "C" const char* ac_last_error(void) { return acpr::g_err; }
+
+extern "C" long long ac_launch_count(void) { return acpr::g_launches.load(std::memory_order_relaxed); }

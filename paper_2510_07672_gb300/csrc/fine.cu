@@ -315,6 +315,7 @@ static int launch_fine(const FineArgs& args, cudaStream_t stream) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     ACPR_CUDA(cudaLaunchKernelEx(&cfg, kern, args));
+    count_launch();
     return AC_OK;
 }
 

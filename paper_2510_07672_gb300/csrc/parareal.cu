@@ -195,6 +195,9 @@ struct ac_parareal {
     std::vector<char> active;
     std::vector<char> synced;  // inactive problem whose trajectory is in both buffers
     int k_next = 0;
+    bool timing = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    ac_parareal_stats stats{};
 };
 
 namespace acpr {
@@ -206,6 +209,8 @@ static void free_state(ac_parareal* st) {
         if (ptr) cudaFree(ptr);
     if (st->h_map) cudaFreeHost(st->h_map);
     if (st->h_res) cudaFreeHost(st->h_res);
+    for (cudaEvent_t e : st->ev)
+        if (e) cudaEventDestroy(e);
     delete st;
 }
 
@@ -247,8 +252,14 @@ static int iterate(ac_parareal* st, int* k_inout, double* l2_out, double* mx_out
     int m = 0;
     int rc = upload_map(st, stream, &m);
     if (rc) return rc;
+    const bool tm = st->timing;
+    auto mark = [&](int i) -> int {
+        if (tm) ACPR_CUDA(cudaEventRecord(st->ev[i], stream));
+        return AC_OK;
+    };
     if (k == 0) {
         // U^0_0 = u0 (already in Ua[0]); sequential coarse sweep
+        if ((rc = mark(1))) return rc;
         for (int n = 0; n < s; ++n) {
             rc = coarse_step_mapped(&st->g, st->p.n, m, static_cast<char*>(st->Ua) + n * fb, nn * (s + 1),
                                     st->d_map, static_cast<char*>(st->Gold) + n * fb, nn * s, st->d_map,
@@ -260,6 +271,15 @@ static int iterate(ac_parareal* st, int* k_inout, double* l2_out, double* mx_out
                                           static_cast<char*>(st->Gold) + (size_t(p) * s + n) * fb, fb,
                                           cudaMemcpyDeviceToDevice, stream));
             }
+            st->stats.coarse_calls += 1;
+            st->stats.coarse_cells += (long long)m * nn;
+        }
+        if ((rc = mark(2))) return rc;
+        if (tm) {
+            float ms = 0.f;
+            ACPR_CUDA(cudaEventSynchronize(st->ev[2]));
+            ACPR_CUDA(cudaEventElapsedTime(&ms, st->ev[1], st->ev[2]));
+            st->stats.coarse_ms += ms;
         }
         st->k_next = 1;
         *k_inout = 1;
@@ -281,9 +301,13 @@ static int iterate(ac_parareal* st, int* k_inout, double* l2_out, double* mx_out
         return AC_OK;
     }
     // 1. fine solves of slices k-1 .. s-1 of every active problem (one launch)
+    if ((rc = mark(0))) return rc;
     rc = fine_propagate_mapped(&st->p, m, s - k + 1, st->c, st->Ua, s + 1, k - 1, st->Fres, s, k - 1,
                                st->d_map, stream);
     if (rc) return rc;
+    st->stats.fine_launches += 1;
+    st->stats.fine_cell_steps += (long long)m * (s - k + 1) * st->c * nn;
+    if ((rc = mark(1))) return rc;
     // 2. newest frozen slice and the exact slice k
     for (int i = 0; i < m; ++i) {
         const int p = st->h_map[i];
@@ -300,13 +324,27 @@ static int iterate(ac_parareal* st, int* k_inout, double* l2_out, double* mx_out
         if (rc) return rc;
         rc = correct(st, st->Ub, n, st->gtmp, m, stream);
         if (rc) return rc;
+        st->stats.coarse_calls += 1;
+        st->stats.coarse_cells += (long long)m * nn;
     }
+    if ((rc = mark(2))) return rc;
     // 4. increments over slices 1..s
     rc = increment(st->p.precision, st->Ub, st->Ua, nn * (s + 1), nn * (s + 1), nn, nn * s, st->d_map, m,
                    st->d_part, st->d_res, stream);
     if (rc) return rc;
+    if ((rc = mark(3))) return rc;
     ACPR_CUDA(cudaMemcpyAsync(st->h_res, st->d_res, sizeof(double) * 4 * m, cudaMemcpyDeviceToHost, stream));
     ACPR_CUDA(cudaStreamSynchronize(stream));
+    st->stats.iterations += 1;
+    if (tm) {
+        float a = 0.f, b = 0.f, c = 0.f;
+        ACPR_CUDA(cudaEventElapsedTime(&a, st->ev[0], st->ev[1]));
+        ACPR_CUDA(cudaEventElapsedTime(&b, st->ev[1], st->ev[2]));
+        ACPR_CUDA(cudaEventElapsedTime(&c, st->ev[2], st->ev[3]));
+        st->stats.fine_ms += a;
+        st->stats.coarse_ms += b;
+        st->stats.increment_ms += c;
+    }
     bool nonfinite = false;
     for (int i = 0; i < m; ++i) {
         const int p = st->h_map[i];
@@ -439,10 +477,15 @@ extern "C" int ac_parareal_solve(ac_parareal* state, double tol, int kmax, int* 
     }
     const int klim = kmax < state->s ? kmax : state->s;
     bool any = true;
+    bool saw_nonfinite = false;
     while (k <= klim && any) {
         const int kk = k;
         rc = iterate(state, &k, l2.data(), mx.data(), st);
-        if (rc) return rc;
+        // A non-finite increment means a diverging iterate beyond the exact
+        // prefix; slices <= k stay fine-solver values, so keep iterating: the
+        // loop still ends with the exact trajectory at k = s.
+        if (rc == AC_ERR_NONFINITE) saw_nonfinite = true;
+        else if (rc) return rc;
         any = false;
         for (int p = 0; p < P; ++p) {
             if (!state->active[p]) continue;
@@ -454,9 +497,45 @@ extern "C" int ac_parareal_solve(ac_parareal* state, double tol, int kmax, int* 
         }
     }
     if (any) {
-        set_error("ac_parareal_solve: not converged within kmax = %d", kmax);
+        set_error("ac_parareal_solve: not converged within kmax = %d%s", kmax,
+                  saw_nonfinite ? " (non-finite increments met)" : "");
         return AC_ERR_NOT_CONVERGED;
     }
+    return AC_OK;
+}
+
+extern "C" int ac_parareal_reset(ac_parareal* state, const void* u0, acpr_stream stream) {
+    using namespace acpr;
+    ACPR_CHECK_ARG(state && u0, "null argument");
+    const size_t fb = state->esz * state->nn;
+    ACPR_CUDA(cudaMemcpy2DAsync(state->Ua, fb * (state->s + 1), u0, fb, fb, state->problems,
+                                cudaMemcpyDeviceToDevice, reinterpret_cast<cudaStream_t>(stream)));
+    state->active.assign(state->problems, 1);
+    state->synced.assign(state->problems, 0);
+    state->k_next = 0;
+    return AC_OK;
+}
+
+extern "C" int ac_parareal_enable_timing(ac_parareal* state, int on) {
+    using namespace acpr;
+    ACPR_CHECK_ARG(state, "null state");
+    if (on && !state->ev[0])
+        for (cudaEvent_t& e : state->ev) ACPR_CUDA(cudaEventCreate(&e));
+    state->timing = on != 0;
+    return AC_OK;
+}
+
+extern "C" int ac_parareal_get_stats(const ac_parareal* state, ac_parareal_stats* out) {
+    using namespace acpr;
+    ACPR_CHECK_ARG(state && out, "null argument");
+    *out = state->stats;
+    return AC_OK;
+}
+
+extern "C" int ac_parareal_reset_stats(ac_parareal* state) {
+    using namespace acpr;
+    ACPR_CHECK_ARG(state, "null state");
+    state->stats = ac_parareal_stats{};
     return AC_OK;
 }
 

@@ -20,7 +20,15 @@ def declared_functions():
             continue
         src = open(os.path.join(ROOT, "include", h)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z_0-9]*\s*\**\s*([a-z_][a-z_0-9]*)\s*\(", src, flags=re.M)
+        src = re.sub(r"^\s*#.*$", "", src, flags=re.M)
+        src = re.sub(r"typedef[^;]*\{[^}]*\}[^;]*;", "", src, flags=re.S)
+        src = re.sub(r"enum\s*\{[^}]*\}\s*;", "", src, flags=re.S)
+        for stmt in src.split(";"):
+            if "typedef" in stmt or "extern" in stmt:
+                continue
+            m = re.search(r"([a-z_][a-z_0-9]*)\s*\(", stmt)
+            if m:
+                names.append(m.group(1))
     return sorted(set(names))
 
 

@@ -78,26 +78,28 @@ def test_exactness_on_gpu_f32():
     assert torch.equal(U, seq)
 
 
-def test_mass_f32_workload_small_converges_like_oracle():
-    """A reduced mass-conserving float32 problem (64^2, 8 slices): the solve
-    stops on the 1e-6 increment and its trajectory is within 1e-5 (relative
-    L2) of the oracle's float64 sequential fine solve, the limit Parareal
-    converges to."""
+def test_mass_f32_solve_matches_oracle_iterates():
+    """A reduced mass-conserving float32 problem (64^2, 8 slices of 50 steps,
+    bf16 conv 1-16-16-16-1).  The solve stops once the increment is below
+    1e-6 (or at k = s, where it is exact).  Its trajectory then matches the
+    oracle's Parareal iterate at the same k (float64 arithmetic, conv with the
+    same bf16 rounding) to the float32 accuracy of the fine solves,
+    2e-5 * sqrt(steps) max-abs per slice."""
     n, s, c = 64, 8, 50
     eps, S, dt = 0.04, 2.0, 5e-5
-    wt, bs = I.cnn_weights(6, 32, seed=0)
-    u0 = np.stack([I.random_field(n, seed=p, zero_mean=True) for p in range(3)])
+    wt, bs = I.cnn_weights(4, 16, seed=0)
+    wt, bs = wt.astype(np.float32), bs.astype(np.float32)
+    u0 = np.stack([I.random_field(n, seed=p, zero_mean=True) for p in range(2)]).astype(np.float32)
     fp = G.FineParams(n, eps, S, dt, variant=1, precision=G.AC_F32)
-    net = G.CoarseNet(6, 32, wt.astype(np.float32), bs.astype(np.float32), act=1, precision=G.AC_F32)
-    pr = G.Parareal(fp, net, torch.tensor(u0, dtype=torch.float32, device="cuda"), s, c)
+    net = G.CoarseNet(4, 16, wt, bs, act=1, precision=G.AC_F32)
+    pr = G.Parareal(fp, net, torch.tensor(u0, device="cuda"), s, c)
     its, l2 = pr.solve(tol=1e-6, kmax=s)
     U = pr.trajectory().double().cpu().numpy()
-    for p in range(3):
+    spec = O.CnnSpec(4, 16, wt.astype(np.float64), bs.astype(np.float64), act=1, bf16=1)
+    for p in range(2):
         assert l2[p] < 1e-6 or its[p] == s
-        op = O.params(n, eps, S, dt, 1)
-        fine = [u0[p].astype(np.float32).astype(np.float64)]
-        for j in range(s):
-            fine.append(O.fine_propagate(op, c, fine[-1]))
-        fine = np.stack(fine)
-        rel = np.linalg.norm(U[p] - fine) / np.linalg.norm(fine)
-        assert rel < 1e-5
+        ref = O.parareal(O.params(n, eps, S, dt, 1), spec, s, c, kmax=its[p], tol=0.0,
+                         u0=u0[p].astype(np.float64))
+        assert ref["iters"] == its[p]
+        assert np.abs(U[p] - ref["U"]).max() < 2e-5 * np.sqrt(c)
+        assert l2[p] < 2 * ref["res_l2"][-1] + 2e-6
