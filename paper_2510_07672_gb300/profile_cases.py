@@ -1,0 +1,49 @@
+"""Small single-kernel cases for profiling with ncu.
+
+    python -m paper_2510_07672_gb300.profile_cases fine   # ac_fine_propagate_slices, 512 x 256^2, 20 steps
+    python -m paper_2510_07672_gb300.profile_cases conv   # cnn_coarse_step, 16 x 256^2, 1-32x6-1 gelu bf16
+
+Each case runs its call twice (a warm-up launch, then the one to capture) and
+exits 0, so `ncu -s <warm-up launches> -c 1` captures a warm launch.  Inputs
+are the benchmark's seeded synthetic fields.
+"""
+from __future__ import annotations
+
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(case: str) -> None:
+    import numpy as np
+    import torch
+
+    import acpr_inputs as I
+    import paper_2510_07672_gb300 as G
+
+    W = I.MASS_F32_256
+    if case == "fine":
+        u = torch.tensor(np.stack([I.random_field(W.n, seed=s, zero_mean=True) for s in range(512)]),
+                         dtype=torch.float32, device="cuda")
+        fp = G.FineParams(W.n, W.eps, W.S, W.dt, variant=W.variant, precision=G.AC_F32)
+        out = torch.empty_like(u)
+        for _ in range(2):
+            G.ac_fine_propagate_slices(fp, 20, u, out)
+    elif case == "conv":
+        wt, bs = W.weights()
+        net = G.CoarseNet(W.layers, W.channels, wt.astype(np.float32), bs.astype(np.float32), act=W.act,
+                          precision=G.AC_F32)
+        u = torch.tensor(W.ics(), dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            G.cnn_coarse_step(net, u)
+    else:
+        raise SystemExit(f"unknown case {case!r} (fine | conv)")
+    torch.cuda.synchronize()
+    print(f"{case}: ok")
+
+
+if __name__ == "__main__":
+    main(sys.argv[1] if len(sys.argv) > 1 else "fine")
