@@ -146,6 +146,30 @@ int parareal_residual(int num_slices, int n, int precision, const void* U_new,
                       const void* U_old, double* rel_l2_out, double* max_abs_out,
                       acpr_stream stream);
 
+/* The same increment as parareal_residual for callers that cannot allocate
+ * memory: code running where cudaMalloc is not allowed or not wanted, such as
+ * inside a host callback or a plugin of a framework that owns every device
+ * allocation, or a real-time loop that must never wait on the allocator.  It
+ * has no counterpart in the paper; it only changes where the scratch lives.
+ *   - It allocates nothing (no cudaMalloc, no cudaFree, no pinned host
+ *     memory): the block partials live in a fixed 48 KiB device array inside
+ *     the library, which every GPU that loads the library keeps until the
+ *     process exits.
+ *   - Results go to out_dev, a device array of 4 doubles the caller owns:
+ *     out_dev[0] = rel_l2, out_dev[1] = max_abs, out_dev[2] = sum of squared
+ *     differences, out_dev[3] = sum of squared U_new (slices 1..s, float64).
+ *     Asynchronous on `stream`; nothing is read back to the host.
+ *   - At most 2048 * 16384 = 33,554,432 elements (num_slices * n * n) per
+ *     call; larger sizes return AC_ERR_UNSUPPORTED without launching.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array: calls whose kernels overlap on the GPU (on
+ *     different streams without ordering between them) race and give wrong
+ *     results.  Order them on one stream, or with events. */
+int parareal_residual_noalloc(int num_slices, int n, int precision, const void* U_new,
+                              const void* U_old, double* out_dev, acpr_stream stream);
+
 /* ------------------------------------------------------------------------
  * Parareal driver (Algorithm 2) for `problems` independent problems that
  * share one ac_params, one coarse propagator, s slices of c fine steps.

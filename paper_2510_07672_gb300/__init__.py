@@ -12,5 +12,5 @@ from .abi import (  # noqa: F401
     AcprError, load, lib_path,
     ac_fine_supported, ac_fine_step, ac_fine_propagate_slices,
     cnn_packed_bytes, cnn_work_bytes, cnn_pack_weights, cnn_coarse_step,
-    parareal_residual, ac_launch_count, Parareal, CoarseNet, FineParams,
+    parareal_residual, parareal_residual_noalloc, ac_launch_count, Parareal, CoarseNet, FineParams,
 )

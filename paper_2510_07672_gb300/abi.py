@@ -49,7 +49,7 @@ class ac_parareal_stats(C.Structure):
 
 EXPORTS = ["ac_last_error", "ac_fine_supported", "ac_fine_step", "ac_fine_propagate_slices",
            "cnn_packed_bytes", "cnn_work_bytes", "cnn_pack_weights", "cnn_coarse_step",
-           "parareal_residual", "ac_parareal_create", "parareal_iterate", "ac_parareal_set_active",
+           "parareal_residual", "parareal_residual_noalloc", "ac_parareal_create", "parareal_iterate", "ac_parareal_set_active",
            "ac_parareal_trajectory", "ac_parareal_copy_trajectory", "ac_parareal_solve", "ac_parareal_reset", "ac_parareal_enable_timing",
            "ac_parareal_get_stats", "ac_parareal_reset_stats", "ac_launch_count", "ac_parareal_destroy"]
 
@@ -80,6 +80,7 @@ def load(build_if_missing: bool = True):
         L.cnn_pack_weights.argtypes = [P(cnn_desc), S]
         L.cnn_coarse_step.argtypes = [P(cnn_desc), I, I, S, S, S]
         L.parareal_residual.argtypes = [I, I, I, S, S, P(D), P(D), S]
+        L.parareal_residual_noalloc.argtypes = [I, I, I, S, S, S, S]
         L.ac_parareal_create.argtypes = [P(ac_params), P(cnn_desc), I, I, I, S, P(S)]
         L.parareal_iterate.argtypes = [S, P(I), P(D), P(D), S]
         L.ac_parareal_set_active.argtypes = [S, I, I]
@@ -242,6 +243,19 @@ def parareal_residual(U_new, U_old, precision=None, stream=None):
     _check(load().parareal_residual(s, n, precision, _dev(U_new, dt, "U_new"), _dev(U_old, dt, "U_old"),
                                     C.byref(l2), C.byref(mx), _stream(stream)))
     return l2.value, mx.value
+
+
+def parareal_residual_noalloc(U_new, U_old, out, precision=None, stream=None):
+    """Allocation-free variant: writes (rel_l2, max_abs, sum d^2, sum U_new^2)
+    into the float64 CUDA tensor `out` (4 elements) without a host read-back."""
+    import torch
+    precision = precision if precision is not None else (AC_F64 if U_new.dtype == torch.float64 else AC_F32)
+    s = U_new.shape[0] - 1
+    n = U_new.shape[-1]
+    dt = _dtype(precision)
+    _check(load().parareal_residual_noalloc(s, n, precision, _dev(U_new, dt, "U_new"), _dev(U_old, dt, "U_old"),
+                                            _dev(out, torch.float64, "out"), _stream(stream)))
+    return out
 
 
 class Parareal:

@@ -171,6 +171,65 @@ int residual(int num_slices, int n, int precision, const void* U_new, const void
     return AC_OK;
 }
 
+// ------------------------------------------- allocation-free residual -----
+// The same two kernels as parareal_residual, but the block partials live in
+// a fixed file-scope device array instead of memory from cudaMalloc, and the
+// results go to a device buffer the caller passes.  One block reduces at most
+// kNoAllocElemsPerBlock elements, so the array bounds the problem size.
+namespace {
+constexpr int kNoAllocMaxBlocks = 2048;                  // 3 doubles each: 48 KiB
+constexpr long long kNoAllocElemsPerBlock = 16384;       // 64 per thread
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) double g_noalloc_scratch[3 * kNoAllocMaxBlocks];
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};          // device address per device
+std::mutex g_noalloc_mutex;
+}  // namespace
+
+int residual_noalloc(int num_slices, int n, int precision, const void* U_new, const void* U_old,
+                     double* out_dev, cudaStream_t st) {
+    ACPR_CHECK_ARG(num_slices >= 1 && n >= 1, "need num_slices >= 1 and n >= 1");
+    ACPR_CHECK_ARG(precision == AC_F64 || precision == AC_F32, "bad precision");
+    const long long count = (long long)n * n * num_slices;
+    const long long blocks = (count + kNoAllocElemsPerBlock - 1) / kNoAllocElemsPerBlock;
+    if (blocks > kNoAllocMaxBlocks) {
+        set_error("parareal_residual_noalloc: %lld elements exceed the fixed scratch limit of %lld "
+                  "(%d blocks x %lld elements); use parareal_residual",
+                  count, (long long)kNoAllocMaxBlocks * kNoAllocElemsPerBlock, kNoAllocMaxBlocks,
+                  kNoAllocElemsPerBlock);
+        return AC_ERR_UNSUPPORTED;
+    }
+    ACPR_CHECK_ARG(U_new && U_old && out_dev, "null pointer");
+    int dev = 0;
+    ACPR_CUDA(cudaGetDevice(&dev));
+    ACPR_CHECK_ARG(dev >= 0 && dev < kNoAllocMaxDevices, "device index %d out of range", dev);
+    double* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            // host code only sees a stand-in for the array: ask the runtime for
+            // its address on this device (once per device)
+            void* addr = nullptr;
+            ACPR_CUDA(cudaGetSymbolAddress(&addr, g_noalloc_scratch));
+            g_noalloc_ptr[dev] = static_cast<double*>(addr);
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    const long long nn = (long long)n * n;
+    dim3 grid(unsigned(blocks), 1);
+    // every scratch slot the finish kernel reads is written by this call's
+    // partials kernel first, so nothing needs clearing
+    if (precision == AC_F64)
+        increment_partials_kernel<double><<<grid, kResThreads, 0, st>>>(
+            static_cast<const double*>(U_new), static_cast<const double*>(U_old), 0, 0, nn, count, nullptr, scratch);
+    else
+        increment_partials_kernel<float><<<grid, kResThreads, 0, st>>>(
+            static_cast<const float*>(U_new), static_cast<const float*>(U_old), 0, 0, nn, count, nullptr, scratch);
+    ACPR_LAUNCH_CHECK();
+    increment_finish_kernel<<<1, 128, 0, st>>>(scratch, int(blocks), 1, out_dev);
+    ACPR_LAUNCH_CHECK();
+    return AC_OK;
+}
+
 }  // namespace acpr
 
 // ---------------------------------------------------------------- driver ---
@@ -368,6 +427,12 @@ extern "C" int parareal_residual(int num_slices, int n, int precision, const voi
                                  double* rel_l2_out, double* max_abs_out, acpr_stream stream) {
     return acpr::residual(num_slices, n, precision, U_new, U_old, rel_l2_out, max_abs_out,
                           reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int parareal_residual_noalloc(int num_slices, int n, int precision, const void* U_new,
+                                         const void* U_old, double* out_dev, acpr_stream stream) {
+    return acpr::residual_noalloc(num_slices, n, precision, U_new, U_old, out_dev,
+                                  reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" int ac_parareal_create(const ac_params* params, const cnn_desc* coarse, int problems,
