@@ -171,6 +171,47 @@ int parareal_residual_noalloc(int num_slices, int n, int precision, const void* 
                               const void* U_old, double* out_dev, acpr_stream stream);
 
 /* ------------------------------------------------------------------------
+ * Training of the coarse propagator (AC_F32 path only; residual stack with
+ * no mass shift and no limiter).  G is trained to step the fully discrete fine
+ * operator (Sec. 3.2: G(U_n) ~ F(U_n)).  Operands are bf16 as in the forward
+ * pass, accumulation float32; the weight gradients are reduced in a fixed
+ * order, so results are deterministic.
+ * ------------------------------------------------------------------------ */
+
+/* Bytes of the training workspace for `batch` n x n fields (saved layer
+ * inputs and pre-activations, gradient buffers, reduction partials). */
+size_t cnn_train_bytes(const cnn_desc* desc, int n, int batch);
+
+/* Forward pass that also saves, into train_ws, what cnn_backward needs.
+ * u_in, u_out: device float32 [batch][n][n].  desc->packed must be current
+ * (cnn_pack_weights after every weight update). */
+int cnn_forward_train(const cnn_desc* desc, int n, int batch, const float* u_in, float* u_out,
+                      void* train_ws, acpr_stream stream);
+
+/* Backward pass of the last cnn_forward_train on the same u_in and train_ws:
+ * grad_out = dL/du_out (device float32 [batch][n][n]); writes dL/du_in to
+ * grad_in (may be NULL) and dL/dW, dL/db (device float32, the layouts of
+ * desc->w and desc->b) to grad_w, grad_b, added to their contents when
+ * `accumulate` is set, else overwriting them. */
+int cnn_backward(const cnn_desc* desc, int n, int batch, const float* u_in, const float* grad_out,
+                 float* grad_in, float* grad_w, float* grad_b, int accumulate, void* train_ws,
+                 acpr_stream stream);
+
+/* One Adam update of `count` float32 parameters (device arrays w, grad and the
+ * moment estimates m, v), step number t >= 1 (bias correction 1 - beta^t). */
+int cnn_adam_step(float* w, const float* grad, float* m, float* v, long long count, double lr,
+                  double beta1, double beta2, double eps, int t, acpr_stream stream);
+
+/* Mean-squared-error term scale * sum (pred - target)^2 over `count` values:
+ * writes grad = 2 * scale * (pred - target), or adds it to grad when
+ * grad_accumulate is set (skipped if grad is NULL), and the float64 loss to
+ * loss_dev[0] (added when `accumulate` is set).  scratch_dev: device
+ * float64[64]. */
+int mse_loss_grad(const float* pred, const float* target, long long count, double scale, float* grad,
+                  int grad_accumulate, double* loss_dev, double* scratch_dev, int accumulate,
+                  acpr_stream stream);
+
+/* ------------------------------------------------------------------------
  * Parareal driver (Algorithm 2) for `problems` independent problems that
  * share one ac_params, one coarse propagator, s slices of c fine steps.
  * ------------------------------------------------------------------------ */

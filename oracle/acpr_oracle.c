@@ -345,9 +345,11 @@ void or_cnn_forward_batch(const or_cnn* d, int n, int batch, const double* u, do
         cnn_forward_impl(d, n, u + (size_t)b * n * n, out + (size_t)b * n * n, NULL, NULL);
 }
 
-/* Backward pass of the plain stack (residual on, no mass shift, no limiter,
- * no bf16 rounding): given dL/dout, returns dL/du, dL/dW, dL/db (accumulated
- * into gw, gb, which the caller zeroes). */
+/* Backward pass of the plain stack (residual on, no mass shift, no limiter):
+ * given dL/dout, returns dL/du, dL/dW, dL/db (accumulated into gw, gb, which
+ * the caller zeroes).  With bf16 set, the products use the same rounded
+ * weights and layer inputs as the forward pass (rounding is passed through as
+ * the identity, the straight-through reading of the bf16 policy). */
 void or_cnn_backward(const or_cnn* d, int n, const double* u, const double* gout,
                      double* gin, double* gw, double* gb) {
     size_t m = (size_t)n * n;
@@ -364,13 +366,16 @@ void or_cnn_backward(const or_cnn* d, int n, const double* u, const double* gout
         int ci, co; layer_dims(d, l, &ci, &co);
         woffs[l] = woff; boffs[l] = boff; woff += ci * co * 9; boff += co;
     }
+    int nw_total = woff;
+    double* wr = malloc(sizeof(double) * (nw_total > 0 ? nw_total : 1));
+    for (int i = 0; i < nw_total; i++) wr[i] = d->bf16 ? or_round_bf16(d->w[i]) : d->w[i];
     double* gz = malloc(sizeof(double) * C * m);   /* dL/dz_l */
     double* ga = malloc(sizeof(double) * C * m);   /* dL/da_l (layer input) */
     memcpy(gz, gout, sizeof(double) * m);          /* last layer: out = u + z_L */
     for (int l = L - 1; l >= 0; l--) {
         int cin, cout;
         layer_dims(d, l, &cin, &cout);
-        const double* W = d->w + woffs[l];
+        const double* W = wr + woffs[l];
         const double* a = ins + (size_t)l * C * m;
         /* db, dW */
         for (int o = 0; o < cout; o++)
@@ -406,7 +411,7 @@ void or_cnn_backward(const or_cnn* d, int n, const double* u, const double* gout
         }
     }
     for (size_t i = 0; i < m; i++) gin[i] = gout[i] + ga[i];   /* residual skip + stack */
-    free(pre); free(ins); free(out); free(woffs); free(boffs); free(gz); free(ga);
+    free(pre); free(ins); free(out); free(woffs); free(boffs); free(gz); free(ga); free(wr);
 }
 
 /* ---------------------------------------------------------- Parareal ---- */

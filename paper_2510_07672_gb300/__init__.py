@@ -13,4 +13,5 @@ from .abi import (  # noqa: F401
     ac_fine_supported, ac_fine_step, ac_fine_propagate_slices,
     cnn_packed_bytes, cnn_work_bytes, cnn_pack_weights, cnn_coarse_step,
     parareal_residual, parareal_residual_noalloc, ac_launch_count, Parareal, CoarseNet, FineParams,
+    TrainableCoarseNet, mse_loss_grad, coarse_step_function,
 )

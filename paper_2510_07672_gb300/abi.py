@@ -51,7 +51,8 @@ EXPORTS = ["ac_last_error", "ac_fine_supported", "ac_fine_step", "ac_fine_propag
            "cnn_packed_bytes", "cnn_work_bytes", "cnn_pack_weights", "cnn_coarse_step",
            "parareal_residual", "parareal_residual_noalloc", "ac_parareal_create", "parareal_iterate", "ac_parareal_set_active",
            "ac_parareal_trajectory", "ac_parareal_copy_trajectory", "ac_parareal_solve", "ac_parareal_reset", "ac_parareal_enable_timing",
-           "ac_parareal_get_stats", "ac_parareal_reset_stats", "ac_launch_count", "ac_parareal_destroy"]
+           "ac_parareal_get_stats", "ac_parareal_reset_stats", "ac_launch_count", "ac_parareal_destroy",
+           "cnn_train_bytes", "cnn_forward_train", "cnn_backward", "cnn_adam_step", "mse_loss_grad"]
 
 
 def lib_path() -> str:
@@ -93,6 +94,12 @@ def load(build_if_missing: bool = True):
         L.ac_parareal_get_stats.argtypes = [S, P(ac_parareal_stats)]
         L.ac_parareal_reset_stats.argtypes = [S]
         L.ac_launch_count.restype = C.c_longlong
+        L.cnn_train_bytes.argtypes = [P(cnn_desc), I, I]
+        L.cnn_train_bytes.restype = C.c_size_t
+        L.cnn_forward_train.argtypes = [P(cnn_desc), I, I, S, S, S, S]
+        L.cnn_backward.argtypes = [P(cnn_desc), I, I, S, S, S, S, S, I, S, S]
+        L.cnn_adam_step.argtypes = [S, S, S, S, C.c_longlong, D, D, D, D, I, S]
+        L.mse_loss_grad.argtypes = [S, S, C.c_longlong, D, S, I, S, S, I, S]
         L.ac_parareal_destroy.argtypes = [S]
         L.ac_parareal_destroy.restype = None
         _lib = L
@@ -200,6 +207,102 @@ class CoarseNet:
         need = load().cnn_work_bytes(C.byref(d), int(n), int(batch))
         if self._work is None or self._work.numel() < need:
             self._work = torch.empty(max(need, 16), dtype=torch.uint8, device=self.w.device)
+
+
+class TrainableCoarseNet(CoarseNet):
+    """CoarseNet (AC_F32) with float32 gradient buffers and Adam moments, for
+    training G to step the fine operator (Sec. 3.2)."""
+
+    def __init__(self, layers, channels, w, b, act=AC_ACT_GELU, device="cuda"):
+        import torch
+        super().__init__(layers, channels, w, b, act=act, precision=AC_F32, device=device)
+        self.gw = torch.zeros_like(self.w)
+        self.gb = torch.zeros_like(self.b)
+        self.mw, self.vw = torch.zeros_like(self.w), torch.zeros_like(self.w)
+        self.mb, self.vb = torch.zeros_like(self.b), torch.zeros_like(self.b)
+        self.t = 0
+
+    def train_bytes(self, n, batch):
+        d = self.desc()
+        return load().cnn_train_bytes(C.byref(d), int(n), int(batch))
+
+    def new_workspace(self, n, batch):
+        import torch
+        return torch.empty(self.train_bytes(n, batch), dtype=torch.uint8, device=self.w.device)
+
+    def forward_train(self, u, ws, out=None, stream=None):
+        n = u.shape[-1]
+        batch = u.numel() // (n * n)
+        out = out if out is not None else torch_empty_like(u)
+        d = self.desc()
+        _check(load().cnn_forward_train(C.byref(d), n, batch, _dev(u, None, "u"), _dev(out, None, "out"),
+                                        _dev(ws, None, "ws"), _stream(stream)))
+        return out
+
+    def backward(self, u, grad_out, ws, grad_in=None, accumulate=False, stream=None):
+        n = u.shape[-1]
+        batch = u.numel() // (n * n)
+        d = self.desc()
+        gi = _dev(grad_in, None, "grad_in") if grad_in is not None else None
+        _check(load().cnn_backward(C.byref(d), n, batch, _dev(u, None, "u"), _dev(grad_out, None, "grad_out"), gi,
+                                   _dev(self.gw, None, "gw"), _dev(self.gb, None, "gb"), int(accumulate),
+                                   _dev(ws, None, "ws"), _stream(stream)))
+        return grad_in
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        self.t += 1
+        for w, g, m, v in ((self.w, self.gw, self.mw, self.vw), (self.b, self.gb, self.mb, self.vb)):
+            _check(load().cnn_adam_step(_dev(w), _dev(g), _dev(m), _dev(v), w.numel(), lr, beta1, beta2, eps,
+                                        self.t, _stream(stream)))
+        self.repack(stream)
+
+
+def torch_empty_like(t):
+    import torch
+    return torch.empty_like(t)
+
+
+def mse_loss_grad(pred, target, scale, grad=None, grad_accumulate=False, loss=None, scratch=None,
+                  accumulate=False, stream=None):
+    """scale * sum (pred - target)^2 into loss[0] (float64 device tensor) and
+    its gradient into grad (float32), both with our kernels."""
+    import torch
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float64, device=pred.device)
+    if scratch is None:
+        scratch = torch.empty(64, dtype=torch.float64, device=pred.device)
+    g = _dev(grad, torch.float32, "grad") if grad is not None else None
+    _check(load().mse_loss_grad(_dev(pred, torch.float32, "pred"), _dev(target, torch.float32, "target"),
+                                pred.numel(), float(scale), g, int(grad_accumulate), _dev(loss, torch.float64, "loss"),
+                                _dev(scratch, torch.float64, "scratch"), int(accumulate), _stream(stream)))
+    return loss
+
+
+def coarse_step_function():
+    """torch.autograd.Function over the conv stack: forward = cnn_forward_train,
+    backward = cnn_backward (gradients for u, w and b)."""
+    import torch
+
+    class CoarseStep(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, u, w, b, net):
+            n = u.shape[-1]
+            batch = u.numel() // (n * n)
+            ws = net.new_workspace(n, batch)
+            out = net.forward_train(u.contiguous(), ws)
+            ctx.save_for_backward(u)
+            ctx.ws, ctx.net = ws, net
+            return out
+
+        @staticmethod
+        def backward(ctx, gout):
+            (u,) = ctx.saved_tensors
+            net = ctx.net
+            du = torch.empty_like(u)
+            net.backward(u.contiguous(), gout.contiguous(), ctx.ws, grad_in=du, accumulate=False)
+            return du, net.gw.clone(), net.gb.clone(), None
+
+    return CoarseStep
 
 
 def cnn_packed_bytes(net: CoarseNet) -> int:

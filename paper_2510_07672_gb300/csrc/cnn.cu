@@ -220,18 +220,6 @@ static void layer_dims(const cnn_desc* d, int l, int* cin, int* cout) {
     *cout = l == d->layers - 1 ? 1 : d->channels;
 }
 
-static size_t weight_count(const cnn_desc* d, size_t* nb) {
-    size_t nw = 0, b = 0;
-    for (int l = 0; l < d->layers; ++l) {
-        int ci, co;
-        layer_dims(d, l, &ci, &co);
-        nw += size_t(ci) * co * 9;
-        b += co;
-    }
-    if (nb) *nb = b;
-    return nw;
-}
-
 int check_cnn(const cnn_desc* d) {
     ACPR_CHECK_ARG(d != nullptr, "cnn_desc is NULL");
     ACPR_CHECK_ARG(d->layers >= 2, "need at least 2 layers (1 -> C -> 1), got %d", d->layers);

@@ -39,12 +39,31 @@ int pack_hidden_weights(const cnn_desc* d, cudaStream_t st);
 // Hidden layer l (1 <= l <= layers - 2) on the tensor cores:
 // in/out are [batch][C/8][n][n][8] bf16.  Returns AC_ERR_UNSUPPORTED when the
 // shape has no tensor-core kernel.
+// Derivative of act_apply.
+template <typename T>
+__device__ __forceinline__ T act_grad(int act, T x) {
+    if (act == AC_ACT_TANH) {
+        const T t = tanh(x);
+        return T(1) - t * t;
+    }
+    // Phi(x) + x phi(x)
+    return T(0.5) * (T(1) + erf(x * T(0.70710678118654752440))) +
+           x * exp(T(-0.5) * x * x) * T(0.39894228040143267794);
+}
+
 // Device-side timeout flag of the tensor-core kernels: returns AC_ERR_TIMEOUT
 // (and clears the flag) if a bounded wait gave up since the last call.
 // Synchronises the stream.
 int tc_check_status(cudaStream_t st);
 
 int hidden_layer_bf16(const cnn_desc* d, int l, int n, int batch, const __nv_bfloat16* in,
-                      __nv_bfloat16* out, const float* w_master, const float* bias, cudaStream_t st);
+                      __nv_bfloat16* out, const float* w_master, const float* bias, cudaStream_t st,
+                      float* zsave = nullptr);
+
+// Backward through hidden layer l+1 into layer l's pre-activation gradient:
+// dz_out = bf16(conv(dz_next, w_t) * act'(z_prev)), w_t from pack_hidden_t.
+int hidden_dgrad_bf16(int C, int act, int n, int batch, const __nv_bfloat16* dz_next, __nv_bfloat16* dz_out,
+                      const __nv_bfloat16* w_t, const float* z_prev, cudaStream_t st);
+int pack_hidden_t(int C, const float* w_layer, __nv_bfloat16* out, cudaStream_t st);
 
 }  // namespace acpr

@@ -97,11 +97,18 @@ static TcShape pick_shape(int n, int C) {
     return best;
 }
 
+// Epilogue modes: kFwd writes bf16(act(acc + bias)) and, if zio != NULL, the
+// float32 pre-activation acc + bias to zio (training forward); kDgrad writes
+// bf16(acc * act'(zio)) (backward through a hidden layer: acc is the
+// transposed-and-flipped conv of the next layer's gradient, zio the saved
+// pre-activation of this layer's input).  zio is float32 [f][C/8][n][n][8].
+enum { kFwd = 0, kDgrad = 1 };
+
 template <int C>
 __global__ void __launch_bounds__(kTcThreads)
 conv_hidden_tc_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ out,
                       const __nv_bfloat16* __restrict__ wpk, const float* __restrict__ bias, int n, int TY,
-                      int n_mt, int plane_px, int ncols, int act) {
+                      int n_mt, int plane_px, int ncols, int act, int mode, float* __restrict__ zio) {
     constexpr int KC = C / 8;
     extern __shared__ __align__(128) unsigned char smem[];
     const int W = n + 2;
@@ -189,14 +196,28 @@ conv_hidden_tc_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __res
                 tc::tmem_ld8(tmem + (uint32_t(qw * 32) << 16) + uint32_t(mt * C + kc * 8), v);
                 tc::tmem_wait_ld();
                 if (valid) {
+                    const size_t off = ((size_t(f) * KC + kc) * nn + pix) * 8;
                     __align__(16) __nv_bfloat16 o8[8];
+                    if (mode == kFwd) {
+                        __align__(16) float z8[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const float z = __uint_as_float(v[i]) + __ldg(bias + kc * 8 + i);
-                        o8[i] = __float2bfloat16_rn(act_apply<float>(act, z));
+                        for (int i = 0; i < 8; ++i) {
+                            z8[i] = __uint_as_float(v[i]) + __ldg(bias + kc * 8 + i);
+                            o8[i] = __float2bfloat16_rn(act_apply<float>(act, z8[i]));
+                        }
+                        if (zio) {
+                            reinterpret_cast<float4*>(zio + off)[0] = *reinterpret_cast<const float4*>(z8);
+                            reinterpret_cast<float4*>(zio + off)[1] = *reinterpret_cast<const float4*>(z8 + 4);
+                        }
+                    } else {
+                        const float4 za = reinterpret_cast<const float4*>(zio + off)[0];
+                        const float4 zb = reinterpret_cast<const float4*>(zio + off)[1];
+                        const float zz[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            o8[i] = __float2bfloat16_rn(__uint_as_float(v[i]) * act_grad<float>(act, zz[i]));
                     }
-                    *reinterpret_cast<uint4*>(out + ((size_t(f) * KC + kc) * nn + pix) * 8) =
-                        *reinterpret_cast<const uint4*>(o8);
+                    *reinterpret_cast<uint4*>(out + off) = *reinterpret_cast<const uint4*>(o8);
                 }
             }
         }
@@ -208,7 +229,7 @@ conv_hidden_tc_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __res
 
 template <int C>
 static int launch_hidden(int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out, const __nv_bfloat16* w,
-                         const float* bias, int act, cudaStream_t st) {
+                         const float* bias, int act, int mode, float* zio, cudaStream_t st) {
     const TcShape s = pick_shape(n, C);
     if (s.TY == 0) return AC_ERR_UNSUPPORTED;
     auto kern = conv_hidden_tc_kernel<C>;
@@ -218,22 +239,55 @@ static int launch_hidden(int n, int batch, const __nv_bfloat16* in, __nv_bfloat1
         configured = 227 * 1024;
     }
     const long long blocks = (long long)batch * (n / s.TY);
-    kern<<<unsigned(blocks), kTcThreads, s.smem, st>>>(in, out, w, bias, n, s.TY, s.n_mt, s.plane_px, s.ncols, act);
+    kern<<<unsigned(blocks), kTcThreads, s.smem, st>>>(in, out, w, bias, n, s.TY, s.n_mt, s.plane_px, s.ncols, act,
+                                                       mode, zio);
     ACPR_LAUNCH_CHECK();
     return AC_OK;
 }
 
 int hidden_layer_bf16(const cnn_desc* d, int l, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
-                      const float* /*w_master*/, const float* bias, cudaStream_t st) {
+                      const float* /*w_master*/, const float* bias, cudaStream_t st, float* zsave) {
     if (n < 8) return AC_ERR_UNSUPPORTED;
     const int C = d->channels;
     const __nv_bfloat16* w = static_cast<const __nv_bfloat16*>(d->packed) + size_t(l - 1) * 9 * C * C;
     switch (C) {
-        case 16: return launch_hidden<16>(n, batch, in, out, w, bias, d->act, st);
-        case 32: return launch_hidden<32>(n, batch, in, out, w, bias, d->act, st);
-        case 64: return launch_hidden<64>(n, batch, in, out, w, bias, d->act, st);
+        case 16: return launch_hidden<16>(n, batch, in, out, w, bias, d->act, kFwd, zsave, st);
+        case 32: return launch_hidden<32>(n, batch, in, out, w, bias, d->act, kFwd, zsave, st);
+        case 64: return launch_hidden<64>(n, batch, in, out, w, bias, d->act, kFwd, zsave, st);
         default: return AC_ERR_UNSUPPORTED;
     }
+}
+
+int hidden_dgrad_bf16(int C, int act, int n, int batch, const __nv_bfloat16* dz_next, __nv_bfloat16* dz_out,
+                      const __nv_bfloat16* w_t, const float* z_prev, cudaStream_t st) {
+    if (n < 8) return AC_ERR_UNSUPPORTED;
+    float* zp = const_cast<float*>(z_prev);
+    switch (C) {
+        case 16: return launch_hidden<16>(n, batch, dz_next, dz_out, w_t, nullptr, act, kDgrad, zp, st);
+        case 32: return launch_hidden<32>(n, batch, dz_next, dz_out, w_t, nullptr, act, kDgrad, zp, st);
+        case 64: return launch_hidden<64>(n, batch, dz_next, dz_out, w_t, nullptr, act, kDgrad, zp, st);
+        default: return AC_ERR_UNSUPPORTED;
+    }
+}
+
+// float32 master W[cout][cin][3][3] -> bf16 [tap][cout/8][cin][8] of the
+// channel-transposed, tap-flipped kernel: the B operand of the dgrad GEMM.
+__global__ void pack_hidden_t_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ out, int C) {
+    const int total = 9 * C * C;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int i = idx % 8;                     // old output channel within its chunk
+        const int c = (idx / 8) % C;               // new output channel = old input channel
+        const int oc = (idx / (8 * C)) % (C / 8);  // chunk of old output channels
+        const int tap = idx / (8 * C * (C / 8));
+        const int o = oc * 8 + i;
+        out[idx] = __float2bfloat16_rn(w[(o * C + c) * 9 + (8 - tap)]);
+    }
+}
+
+int pack_hidden_t(int C, const float* w_layer, __nv_bfloat16* out, cudaStream_t st) {
+    pack_hidden_t_kernel<<<64, 256, 0, st>>>(w_layer, out, C);
+    ACPR_LAUNCH_CHECK();
+    return AC_OK;
 }
 
 int tc_check_status(cudaStream_t st) {
