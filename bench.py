@@ -34,6 +34,7 @@ import numpy as np  # noqa: E402
 import acpr_inputs as I  # noqa: E402
 
 METRIC = "Parareal time-to-1e-6 vs sequential fine on GB300; fine cell-steps/s, %roofline"
+TRAINED = os.path.join(ROOT, "paper_2510_07672_gb300", "weights", "mass256_c32l6_gelu.npz")
 UNIT = "cell-steps/s"
 WL = I.MASS_F32_256
 
@@ -159,6 +160,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--weights", default="trained", help="'trained' (the committed G), 'untrained', or a .npz path")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -188,6 +190,13 @@ def main():
 
     fp = G.FineParams(WL.n, WL.eps, WL.S, WL.dt, variant=WL.variant, precision=G.AC_F32)
     wt, bs = WL.weights()
+    wsrc = "untrained N(0, 0.01^2)"
+    wpath = TRAINED if args.weights == "trained" else (None if args.weights == "untrained" else args.weights)
+    if wpath:
+        z = np.load(wpath)
+        wt, bs = z["w"], z["b"]
+        wsrc = (f"trained by paper_2510_07672_gb300/train.py ({int(z['iters'])} Adam steps, {int(z['unroll'])}-step "
+                f"unrolled MSE on fine trajectories from ICs disjoint from the bench's): {os.path.relpath(wpath, ROOT)}")
     net = G.CoarseNet(WL.layers, WL.channels, wt.astype(np.float32), bs.astype(np.float32),
                       act=WL.act, precision=G.AC_F32, device=dev)
     ics = WL.ics().astype(np.float32)  # same 16 problems on every rank (weak scaling replicas)
@@ -291,7 +300,8 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WL.name, "n": WL.n, "problems": WL.problems, "slices": WL.slices,
                        "steps_per_slice": WL.steps, "variant": "mass-conserving", "conv": "1-32x6-1 gelu bf16",
-                       "tol": WL.tol, "l2": "state larger than L2 (trajectories, stored G and F values: 0.54 GB)",
+                       "tol": WL.tol, "coarse_weights": wsrc,
+                       "l2": "state larger than L2 (trajectories, stored G and F values: 0.54 GB)",
                        "parallelism": f"replicas x{world}"},
             "iterations": its, "final_rel_l2": l2,
             "sequential_ms": seq_ms, "parareal_ms": ms,
