@@ -4,8 +4,10 @@ One step = one complete Parareal solve (Algorithm 2) of 16 independent
 problems: 256 x 256 periodic grid, eps = 0.01, S = 2, dt = 5e-5, 32 slices of
 200 fine steps, zero-mean U(-0.9, 0.9) initial data, coarse propagator
 1 -> 32 x 6 layers of 3x3 circular conv with GELU (bf16 operands, float32
-accumulation, N(0, 0.01^2) weights), iterated until every problem's relative
-L2 increment is below 1e-6 (or k = s, where Parareal is exact).
+accumulation; weights trained by paper_2510_07672_gb300/train.py, or the
+N(0, 0.01^2) initialisation with --weights untrained), iterated until every
+problem's relative L2 increment is below 1e-6 (or k = s, where Parareal is
+exact).
 
 value = delivered fine trajectory throughput of the solve,
         problems * slices * steps * n^2 / (device time of one solve)   [cell-steps/s]
