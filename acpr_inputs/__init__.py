@@ -131,6 +131,7 @@ class Workload:
     length: float = 1.0
     seed0: int = 0
     weight_seed: int = 0
+    mass_fix: int = 0   # mACNN uniform mass shift on the coarse net
 
     def ics(self) -> np.ndarray:
         return np.stack([random_field(self.n, self.seed0 + p, zero_mean=self.zero_mean)
@@ -150,7 +151,7 @@ PLAIN_F64_64 = Workload("ac-classic-f64-64sq-8x100", n=64, eps=0.025, S=2.0, dt=
 MASS_F32_256 = Workload("ac-mass-f32-256sq-16ic-32x200", n=256, eps=0.01, S=2.0, dt=5e-5,
                         slices=32, steps=200, variant=1, precision=1, layers=6,
                         channels=32, act=1, problems=16, tol=1e-6, kmax=32,
-                        zero_mean=True)
+                        zero_mean=True, mass_fix=1)
 
 # 1024x1024 classic AC, one problem, 128 slices x 500 steps, gelu conv C=64 L=8
 LARGE_F32_1024 = Workload("ac-classic-f32-1024sq-128x500", n=1024, eps=0.004, S=2.0, dt=2e-5,

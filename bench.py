@@ -200,7 +200,7 @@ def main():
         wsrc = (f"trained by paper_2510_07672_gb300/train.py ({int(z['iters'])} Adam steps, {int(z['unroll'])}-step "
                 f"unrolled MSE on fine trajectories from ICs disjoint from the bench's): {os.path.relpath(wpath, ROOT)}")
     net = G.CoarseNet(WL.layers, WL.channels, wt.astype(np.float32), bs.astype(np.float32),
-                      act=WL.act, precision=G.AC_F32, device=dev)
+                      act=WL.act, precision=G.AC_F32, mass_fix=WL.mass_fix, device=dev)
     ics = WL.ics().astype(np.float32)  # same 16 problems on every rank (weak scaling replicas)
     u0 = torch.tensor(ics, device=dev)
     pr = G.Parareal(fp, net, u0, WL.slices, WL.steps)
@@ -301,7 +301,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WL.name, "n": WL.n, "problems": WL.problems, "slices": WL.slices,
-                       "steps_per_slice": WL.steps, "variant": "mass-conserving", "conv": "1-32x6-1 gelu bf16",
+                       "steps_per_slice": WL.steps, "variant": "mass-conserving", "conv": "1-32x6-1 gelu bf16, mACNN mass shift",
                        "tol": WL.tol, "coarse_weights": wsrc,
                        "l2": "state larger than L2 (trajectories, stored G and F values: 0.54 GB)",
                        "parallelism": f"replicas x{world}"},

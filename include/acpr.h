@@ -171,8 +171,8 @@ int parareal_residual_noalloc(int num_slices, int n, int precision, const void* 
                               const void* U_old, double* out_dev, acpr_stream stream);
 
 /* ------------------------------------------------------------------------
- * Training of the coarse propagator (AC_F32 path only; residual stack with
- * no mass shift and no limiter).  G is trained to step the fully discrete fine
+ * Training of the coarse propagator (AC_F32 path only; residual stack, with
+ * or without the mACNN mass shift, no limiter).  G is trained to step the fully discrete fine
  * operator (Sec. 3.2: G(U_n) ~ F(U_n)).  Operands are bf16 as in the forward
  * pass, accumulation float32; the weight gradients are reduced in a fixed
  * order, so results are deterministic.

@@ -345,11 +345,13 @@ void or_cnn_forward_batch(const or_cnn* d, int n, int batch, const double* u, do
         cnn_forward_impl(d, n, u + (size_t)b * n * n, out + (size_t)b * n * n, NULL, NULL);
 }
 
-/* Backward pass of the plain stack (residual on, no mass shift, no limiter):
- * given dL/dout, returns dL/du, dL/dW, dL/db (accumulated into gw, gb, which
- * the caller zeroes).  With bf16 set, the products use the same rounded
- * weights and layer inputs as the forward pass (rounding is passed through as
- * the identity, the straight-through reading of the bf16 policy). */
+/* Backward pass of the residual stack without limiter: given dL/dout,
+ * returns dL/du, dL/dW, dL/db (accumulated into gw, gb, which the caller
+ * zeroes).  With the mACNN mass shift, out = u + s(u) - mean(s(u)), so the
+ * stack receives dL/dout minus its mean.  With bf16 set, the products use the
+ * same rounded weights and layer inputs as the forward pass (rounding is
+ * passed through as the identity, the straight-through reading of the bf16
+ * policy). */
 void or_cnn_backward(const or_cnn* d, int n, const double* u, const double* gout,
                      double* gin, double* gw, double* gb) {
     size_t m = (size_t)n * n;
@@ -372,6 +374,12 @@ void or_cnn_backward(const or_cnn* d, int n, const double* u, const double* gout
     double* gz = malloc(sizeof(double) * C * m);   /* dL/dz_l */
     double* ga = malloc(sizeof(double) * C * m);   /* dL/da_l (layer input) */
     memcpy(gz, gout, sizeof(double) * m);          /* last layer: out = u + z_L */
+    if (d->mass_fix) {
+        double gm = 0.0;
+        for (size_t i = 0; i < m; i++) gm += gout[i];
+        gm /= (double)m;
+        for (size_t i = 0; i < m; i++) gz[i] = gout[i] - gm;
+    }
     for (int l = L - 1; l >= 0; l--) {
         int cin, cout;
         layer_dims(d, l, &cin, &cout);

@@ -213,9 +213,9 @@ class TrainableCoarseNet(CoarseNet):
     """CoarseNet (AC_F32) with float32 gradient buffers and Adam moments, for
     training G to step the fine operator (Sec. 3.2)."""
 
-    def __init__(self, layers, channels, w, b, act=AC_ACT_GELU, device="cuda"):
+    def __init__(self, layers, channels, w, b, act=AC_ACT_GELU, mass_fix=0, device="cuda"):
         import torch
-        super().__init__(layers, channels, w, b, act=act, precision=AC_F32, device=device)
+        super().__init__(layers, channels, w, b, act=act, precision=AC_F32, mass_fix=mass_fix, device=device)
         self.gw = torch.zeros_like(self.w)
         self.gb = torch.zeros_like(self.b)
         self.mw, self.vw = torch.zeros_like(self.w), torch.zeros_like(self.w)

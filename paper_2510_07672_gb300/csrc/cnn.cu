@@ -352,6 +352,13 @@ int coarse_step(const cnn_desc* d, int n, int batch, const void* u_in, void* u_o
     return coarse_step_mapped(d, n, batch, u_in, nn, nullptr, u_out, nn, nullptr, st);
 }
 
+int mass_shift_f32(const float* u, float* out, int n, int batch, cudaStream_t st) {
+    BatchIO io{nullptr, nullptr, (long long)n * n, (long long)n * n, 1, 1};
+    post_kernel<float><<<batch, 256, 0, st>>>(u, out, n, 1, 0, 0.0, 0.0, io);
+    ACPR_LAUNCH_CHECK();
+    return AC_OK;
+}
+
 size_t packed_bytes_for(const cnn_desc* d) {
     if (d->precision == AC_F64) return 0;
     return packed_hidden_bytes(d);

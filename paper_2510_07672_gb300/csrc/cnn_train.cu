@@ -3,7 +3,8 @@
 // the conv stack, Adam, and the mean-squared-error loss.
 //
 // The model is out = u + stack(u), stack = conv_L o act o ... o act o conv_1
-// (Sec. 3.2).  With a_0 = bf16(u), z_l = conv_l(a_l) + b_l, a_{l+1} = bf16(act(z_l)):
+// (Sec. 3.2), optionally with the mACNN mass shift out -= mean(stack(u)), in
+// which case the stack receives the output gradient minus its mean.  With a_0 = bf16(u), z_l = conv_l(a_l) + b_l, a_{l+1} = bf16(act(z_l)):
 //   dz_L     = g = dL/dout
 //   dW_l     = sum over pixels of dz_l (x) shifted a_l,  db_l = sum dz_l
 //   dz_{l-1} = act'(z_{l-1}) * conv^T(dz_l, W_l)      (bf16, the next operand)
@@ -21,6 +22,7 @@
 //   dZ ping-pong      2 x bf16 [B][C/8][n][n][8]
 //   Wt                bf16 (L-2) x 9*C*C          transposed, flipped hidden weights
 //   partials          f32  kChunks x 9 x (C*C + C)  weight / bias gradient partials
+//   g centred         f32  [B][n][n]               (mass shift only)
 #include <cuda_bf16.h>
 
 #include "cnn.cuh"
@@ -34,7 +36,7 @@ __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >
 
 struct TrainLayout {
     size_t a_bytes, z_bytes;    // one layer
-    size_t off_a, off_z, off_dz, off_wt, off_part, total;
+    size_t off_a, off_z, off_dz, off_wt, off_part, off_gc, total;
 };
 
 static TrainLayout train_layout(const cnn_desc* d, int n, int batch) {
@@ -49,7 +51,8 @@ static TrainLayout train_layout(const cnn_desc* d, int n, int batch) {
     t.off_wt = t.off_dz + 2 * t.a_bytes;
     const size_t wt = size_t(L > 2 ? L - 2 : 0) * 9 * d->channels * d->channels * 2;
     t.off_part = (t.off_wt + wt + 255) / 256 * 256;
-    t.total = t.off_part + size_t(kChunks) * 9 * (size_t(d->channels) * d->channels + d->channels) * 4;
+    t.off_gc = t.off_part + size_t(kChunks) * 9 * (size_t(d->channels) * d->channels + d->channels) * 4;
+    t.total = t.off_gc + size_t(batch) * n * n * 4;
     return t;
 }
 
@@ -115,6 +118,27 @@ __global__ void last_fwd_kernel(const __nv_bfloat16* __restrict__ in, float* __r
 }
 
 // ------------------------------------------------------------ backward ----
+// gc = g - mean(g) per field (float64 sum in a fixed order), one block each.
+__global__ void center_kernel(const float* __restrict__ g, float* __restrict__ gc, int n) {
+    const long long nn = (long long)n * n;
+    const float* gb = g + blockIdx.x * nn;
+    float* ob = gc + blockIdx.x * nn;
+    __shared__ double red[32];
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < nn; i += blockDim.x) s += double(gb[i]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[w];
+        red[0] = t / double(nn);
+    }
+    __syncthreads();
+    const float mean = float(red[0]);
+    for (long long i = threadIdx.x; i < nn; i += blockDim.x) ob[i] = gb[i] - mean;
+}
+
 // Last layer: dz_{L-2} = bf16(act'(z_{L-2}) * sum_tap W_L[c][tap] g[p - off(tap)]).
 template <int C>
 __global__ void last_dgrad_kernel(const float* __restrict__ g, const float* __restrict__ W,
@@ -278,8 +302,8 @@ __global__ void wgrad_reduce_kernel(const float* __restrict__ part, float* __res
 static int check_train(const cnn_desc* d) {
     int rc = check_cnn(d);
     if (rc) return rc;
-    if (d->precision != AC_F32 || d->mass_fix || d->limiter || !d->residual) {
-        set_error("conv training: only the AC_F32 residual stack without mass shift or limiter");
+    if (d->precision != AC_F32 || d->limiter || !d->residual) {
+        set_error("conv training: only the AC_F32 residual stack without limiter");
         return AC_ERR_UNSUPPORTED;
     }
     return AC_OK;
@@ -317,6 +341,7 @@ static int forward_train(const cnn_desc* d, int n, int batch, const float* u, fl
     }
     last_fwd_kernel<C><<<blocks, 128, 0, st>>>(A(d->layers - 1), out, W + woff, Bv + boff, u, batch, n);
     ACPR_LAUNCH_CHECK();
+    if (d->mass_fix) return mass_shift_f32(u, out, n, batch, st);
     return AC_OK;
 }
 
@@ -343,10 +368,18 @@ static int backward(const cnn_desc* d, int n, int batch, const float* u, const f
         wo += size_t(ci) * co * 9; bo += co;
     }
     int rc;
+    // the stack's output gradient: g, or g minus its mean under the mass shift
+    const float* gs = g;
+    if (d->mass_fix) {
+        float* gc = reinterpret_cast<float*>(ws + t.off_gc);
+        center_kernel<<<batch, 256, 0, st>>>(g, gc, n);
+        ACPR_LAUNCH_CHECK();
+        gs = gc;
+    }
     // last layer
-    rc = wgrad<C, 1>(A(L - 1), g, part, gw + woffs[L - 1], gb + boffs[L - 1], batch, n, C, accumulate, st);
+    rc = wgrad<C, 1>(A(L - 1), gs, part, gw + woffs[L - 1], gb + boffs[L - 1], batch, n, C, accumulate, st);
     if (rc) return rc;
-    last_dgrad_kernel<C><<<blocks, 128, 0, st>>>(g, W + woffs[L - 1], Z(L - 2), dz[0], batch, n, d->act);
+    last_dgrad_kernel<C><<<blocks, 128, 0, st>>>(gs, W + woffs[L - 1], Z(L - 2), dz[0], batch, n, d->act);
     ACPR_LAUNCH_CHECK();
     int cur = 0;
     // hidden layers L-2 .. 1: dz[cur] holds dz_l

@@ -39,8 +39,16 @@ def make_trajectories(fp, ics, slices: int, steps: int):
 
 
 def train_coarse(net, traj, iters: int, batch: int, unroll: int, lr: float, seed: int = 0, log_every: int = 0,
-                 lr_final: float | None = None):
-    """Adam on the unrolled MSE.  Returns the list of per-iteration losses."""
+                 lr_final: float | None = None, fine=None, perturb: float = 0.0):
+    """Adam on the unrolled MSE.  Returns the list of per-iteration losses.
+
+    With `fine` (FineParams and steps per slice) and perturb > 0, each window
+    starts from a perturbed state U_t + delta instead, with targets produced by
+    the fine propagator from that state: Parareal applies G to iterates that
+    are off the fine trajectory, and its correction converges only as fast as
+    G's response to such deviations matches F's.  delta mixes a slice increment
+    of another trajectory (smooth, realistic spectrum) and white noise, with
+    relative size up to `perturb`."""
     import numpy as np
     import torch
 
@@ -65,8 +73,24 @@ def train_coarse(net, traj, iters: int, batch: int, unroll: int, lr: float, seed
         r = torch.as_tensor(rng.integers(0, R, batch), device=dev)
         t = torch.as_tensor(rng.integers(0, S - unroll + 1, batch), device=dev)
         xs[0].copy_(traj[r, t])
-        for j in range(unroll):
-            tg[j].copy_(traj[r, t + j + 1])
+        if fine is not None and perturb > 0:
+            fp, steps = fine
+            r2 = torch.as_tensor(rng.integers(0, R, batch), device=dev)
+            t2 = torch.as_tensor(rng.integers(0, S, batch), device=dev)
+            amp = torch.as_tensor(rng.uniform(0, perturb, (batch, 1, 1)), dtype=torch.float32, device=dev)
+            rms = xs[0].pow(2).mean(dim=(1, 2), keepdim=True).sqrt()
+            smooth = traj[r2, t2 + 1] - traj[r2, t2]
+            smooth = smooth / smooth.pow(2).mean(dim=(1, 2), keepdim=True).sqrt().clamp_min(1e-12)
+            white = torch.randn_like(xs[0])
+            mix = torch.as_tensor(rng.uniform(0, 1, (batch, 1, 1)), dtype=torch.float32, device=dev)
+            xs[0].add_(amp * rms * (mix * smooth + (1 - mix) * white))
+            prev = xs[0]
+            for j in range(unroll):
+                abi.ac_fine_propagate_slices(fp, steps, prev, tg[j])
+                prev = tg[j]
+        else:
+            for j in range(unroll):
+                tg[j].copy_(traj[r, t + j + 1])
         for j in range(unroll):
             net.forward_train(xs[j], ws[j], out=xs[j + 1])
         # backward through the chain: g_j = dL/dx_{j+1} (+ what flows back from step j+2)
@@ -100,6 +124,8 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--lr-final", type=float, default=1e-4)
     ap.add_argument("--seed0", type=int, default=5000)
+    ap.add_argument("--perturb", type=float, default=0.05)
+    ap.add_argument("--init", default=None, help="start from these weights (.npz)")
     args = ap.parse_args()
     W = I.MASS_F32_256
     fp = abi.FineParams(W.n, W.eps, W.S, W.dt, variant=W.variant, precision=abi.AC_F32)
@@ -110,14 +136,19 @@ def main():
     torch.cuda.synchronize()
     t1 = time.time()
     wt, bs = W.weights()
-    net = abi.TrainableCoarseNet(W.layers, W.channels, wt.astype(np.float32), bs.astype(np.float32), act=W.act)
+    if args.init:
+        z = np.load(args.init)
+        wt, bs = z["w"], z["b"]
+    net = abi.TrainableCoarseNet(W.layers, W.channels, wt.astype(np.float32), bs.astype(np.float32), act=W.act,
+                                 mass_fix=W.mass_fix)
     losses = train_coarse(net, traj, args.iters, args.batch, args.unroll, args.lr, log_every=200,
-                          lr_final=args.lr_final)
+                          lr_final=args.lr_final, fine=(fp, W.steps), perturb=args.perturb)
     torch.cuda.synchronize()
     t2 = time.time()
     np.savez(args.out, w=net.w.cpu().numpy(), b=net.b.cpu().numpy(), layers=W.layers, channels=W.channels,
              act=W.act, workload=W.name, iters=args.iters, batch=args.batch, unroll=args.unroll, lr=args.lr,
-             final_loss=losses[-1], first_loss=losses[0])
+             final_loss=losses[-1], first_loss=losses[0], perturb=args.perturb, ics=args.ics, mass_fix=W.mass_fix,
+             seed0=args.seed0)
     print(f"trajectories {t1 - t0:.1f} s, training {t2 - t1:.1f} s, loss {losses[0]:.3e} -> {losses[-1]:.3e}")
 
 

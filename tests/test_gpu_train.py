@@ -24,14 +24,15 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
-@pytest.mark.parametrize("n,L,C,act", [(32, 4, 16, 1), (16, 3, 32, 0), (64, 5, 32, 1)])
-def test_backward_matches_oracle(n, L, C, act):
+@pytest.mark.parametrize("n,L,C,act,mass_fix", [(32, 4, 16, 1, 0), (16, 3, 32, 0, 0), (64, 5, 32, 1, 0),
+                                                (32, 4, 16, 1, 1)])
+def test_backward_matches_oracle(n, L, C, act, mass_fix):
     w, b = I.cnn_weights(L, C, seed=7, sigma=0.25)
     w, b = w.astype(np.float32), b.astype(np.float32)
     batch = 2
     u = np.stack([I.random_field(n, seed=s) for s in range(batch)]).astype(np.float32)
     g = np.random.default_rng(1).standard_normal((batch, n, n)).astype(np.float32)
-    net = G.TrainableCoarseNet(L, C, w, b, act=act)
+    net = G.TrainableCoarseNet(L, C, w, b, act=act, mass_fix=mass_fix)
     ws = net.new_workspace(n, batch)
     U = torch.tensor(u, device="cuda")
     out = net.forward_train(U, ws)
@@ -39,7 +40,7 @@ def test_backward_matches_oracle(n, L, C, act):
     assert torch.equal(out, G.cnn_coarse_step(net, U))
     du = torch.empty_like(U)
     net.backward(U, torch.tensor(g, device="cuda"), ws, grad_in=du)
-    spec = O.CnnSpec(L, C, w.astype(np.float64), b.astype(np.float64), act=act, bf16=1)
+    spec = O.CnnSpec(L, C, w.astype(np.float64), b.astype(np.float64), act=act, bf16=1, mass_fix=mass_fix)
     gw_ref = np.zeros(w.size)
     gb_ref = np.zeros(b.size)
     du_ref = np.zeros((batch, n, n))

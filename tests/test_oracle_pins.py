@@ -322,18 +322,18 @@ def test_bf16_mode_rounds_inputs_and_weights():
     assert np.array_equal(O.cnn_forward(spec, u), rb(u) * rb(1.0 + 2 ** -10))
 
 
-@pytest.mark.parametrize("act", [0, 1])
-def test_conv_backward_finite_differences(act):
+@pytest.mark.parametrize("act,mass_fix", [(0, 0), (1, 0), (1, 1)])
+def test_conv_backward_finite_differences(act, mass_fix):
     n, L, C = 6, 3, 3
     w, b = I.cnn_weights(L, C, seed=5, sigma=0.4)
     u = I.random_field(n, seed=6)
     gout = rng(7).standard_normal((n, n))
-    spec = O.CnnSpec(L, C, w, b, act=act)
+    spec = O.CnnSpec(L, C, w, b, act=act, mass_fix=mass_fix)
     gin, gw, gb = O.cnn_backward(spec, u, gout)
     hh = 1e-6
 
     def J(uu, ww, bb):
-        return np.vdot(gout, O.cnn_forward(O.CnnSpec(L, C, ww, bb, act=act), uu))
+        return np.vdot(gout, O.cnn_forward(O.CnnSpec(L, C, ww, bb, act=act, mass_fix=mass_fix), uu))
 
     d = rng(8).standard_normal((n, n))
     fd = (J(u + hh * d, w, b) - J(u - hh * d, w, b)) / (2 * hh)
