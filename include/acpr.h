@@ -117,6 +117,44 @@ int ac_fine_step(const ac_params* params, int batch, const void* u_in, void* u_o
 int ac_fine_propagate_slices(const ac_params* params, int num_fields, int steps_per_slice,
                              const void* u_starts, void* u_ends, acpr_stream stream);
 
+/* The fine steps of ac_fine_propagate_slices, also storing every state:
+ * traj[s][f] = u^s of field f for s = 0..steps (device [steps+1][num_fields]
+ * [n][n]); u0: device [num_fields][n][n]. */
+int ac_fine_trajectory(const ac_params* params, int num_fields, int steps, const void* u0, void* traj,
+                       acpr_stream stream);
+
+/* Adjoint (transposed Jacobian) of `steps` fine steps, applied backwards:
+ * lambda_n = J(u_n)^T lambda_{n+1}.  With A = (1 + S dt) I - dt eps^2 Lap_h
+ * symmetric and mu = A^{-1} lambda_{n+1}:
+ *   lambda_n = (1 + S dt) mu + dt f'(u_n) * (mu - mean(mu))  (mass-conserving)
+ *   lambda_n = (1 + S dt) mu + dt f'(u_n) * mu               (classic),
+ * the exact transpose of the step of Sec. 3.1 (with beta = mean f(u_n)).
+ * states: device [steps (or more)][num_fields][n][n], states[n][f] = u_n
+ * (e.g. from ac_fine_trajectory); lam_end -> lam_start: device
+ * [num_fields][n][n]. */
+int ac_fine_adjoint(const ac_params* params, int num_fields, int steps, const void* states,
+                    const void* lam_end, void* lam_start, acpr_stream stream);
+
+/* Discrete energy E_h(u) = h^2 sum eps^2/2 (|D+x u|^2 + |D+y u|^2) + (u^2-1)^2/4
+ * of each field (Sec. 2, Eq. energy), float64, into energy_dev[num_fields]
+ * (device).  Deterministic (fixed summation order). */
+int ac_energy(const ac_params* params, int num_fields, const void* u, double* energy_dev,
+              acpr_stream stream);
+
+/* dE_h/du = h^2 (-eps^2 Lap_h u - f(u)) for each field (device, params precision). */
+int ac_energy_grad(const ac_params* params, int num_fields, const void* u, void* grad, acpr_stream stream);
+
+/* Bytes of the workspace ac_energy_gradient_ic needs. */
+size_t ac_energy_gradient_workspace(const ac_params* params, int steps, int checkpoint_every);
+
+/* Gradient of E_h(u^steps) with respect to the initial field u0 (one field,
+ * device [n][n]) through `steps` fine steps: checkpoints every
+ * `checkpoint_every` steps on the way forward, then per segment (last first)
+ * the states are recomputed from the checkpoint and the adjoint steps run
+ * through them.  workspace: caller-owned device memory. */
+int ac_energy_gradient_ic(const ac_params* params, int steps, int checkpoint_every, const void* u0,
+                          void* grad, void* workspace, size_t workspace_bytes, acpr_stream stream);
+
 /* Bytes of device workspace cnn_desc.packed needs (0 for AC_F64). */
 size_t cnn_packed_bytes(const cnn_desc* desc);
 

@@ -52,6 +52,8 @@ EXPORTS = ["ac_last_error", "ac_fine_supported", "ac_fine_step", "ac_fine_propag
            "parareal_residual", "parareal_residual_noalloc", "ac_parareal_create", "parareal_iterate", "ac_parareal_set_active",
            "ac_parareal_trajectory", "ac_parareal_copy_trajectory", "ac_parareal_solve", "ac_parareal_reset", "ac_parareal_enable_timing",
            "ac_parareal_get_stats", "ac_parareal_reset_stats", "ac_launch_count", "ac_parareal_destroy",
+           "ac_fine_trajectory", "ac_fine_adjoint", "ac_energy", "ac_energy_grad",
+           "ac_energy_gradient_workspace", "ac_energy_gradient_ic",
            "cnn_train_bytes", "cnn_forward_train", "cnn_backward", "cnn_adam_step", "mse_loss_grad"]
 
 
@@ -94,6 +96,13 @@ def load(build_if_missing: bool = True):
         L.ac_parareal_get_stats.argtypes = [S, P(ac_parareal_stats)]
         L.ac_parareal_reset_stats.argtypes = [S]
         L.ac_launch_count.restype = C.c_longlong
+        L.ac_fine_trajectory.argtypes = [P(ac_params), I, I, S, S, S]
+        L.ac_fine_adjoint.argtypes = [P(ac_params), I, I, S, S, S, S]
+        L.ac_energy.argtypes = [P(ac_params), I, S, S, S]
+        L.ac_energy_grad.argtypes = [P(ac_params), I, S, S, S]
+        L.ac_energy_gradient_workspace.argtypes = [P(ac_params), I, I]
+        L.ac_energy_gradient_workspace.restype = C.c_size_t
+        L.ac_energy_gradient_ic.argtypes = [P(ac_params), I, I, S, S, S, C.c_size_t, S]
         L.cnn_train_bytes.argtypes = [P(cnn_desc), I, I]
         L.cnn_train_bytes.restype = C.c_size_t
         L.cnn_forward_train.argtypes = [P(cnn_desc), I, I, S, S, S, S]
@@ -167,6 +176,63 @@ def ac_fine_propagate_slices(params: FineParams, steps: int, u_in, u_out=None, s
     _check(load().ac_fine_propagate_slices(C.byref(p), fields, int(steps), _dev(u_in, params.dtype, "u_in"),
                                            _dev(u_out, params.dtype, "u_out"), _stream(stream)))
     return u_out
+
+
+def ac_fine_trajectory(params: FineParams, steps: int, u0, traj=None, stream=None):
+    """traj[s][f] = u^s, s = 0..steps (device tensor [steps+1][fields][n][n])."""
+    import torch
+    n = params.n
+    fields = u0.numel() // (n * n)
+    if traj is None:
+        traj = torch.empty((steps + 1, fields, n, n), dtype=params.dtype, device=u0.device)
+    p = params.c()
+    _check(load().ac_fine_trajectory(C.byref(p), fields, int(steps), _dev(u0, params.dtype, "u0"),
+                                     _dev(traj, params.dtype, "traj"), _stream(stream)))
+    return traj
+
+
+def ac_fine_adjoint(params: FineParams, steps: int, states, lam_end, lam_start=None, stream=None):
+    n = params.n
+    fields = lam_end.numel() // (n * n)
+    lam_start = lam_start if lam_start is not None else lam_end.new_empty(lam_end.shape)
+    p = params.c()
+    _check(load().ac_fine_adjoint(C.byref(p), fields, int(steps), _dev(states, params.dtype, "states"),
+                                  _dev(lam_end, params.dtype, "lam_end"), _dev(lam_start, params.dtype, "lam_start"),
+                                  _stream(stream)))
+    return lam_start
+
+
+def ac_energy(params: FineParams, u, stream=None):
+    import torch
+    n = params.n
+    fields = u.numel() // (n * n)
+    e = torch.empty(fields, dtype=torch.float64, device=u.device)
+    p = params.c()
+    _check(load().ac_energy(C.byref(p), fields, _dev(u, params.dtype, "u"), _dev(e, torch.float64, "e"),
+                            _stream(stream)))
+    return e
+
+
+def ac_energy_grad(params: FineParams, u, g=None, stream=None):
+    n = params.n
+    fields = u.numel() // (n * n)
+    g = g if g is not None else u.new_empty(u.shape)
+    p = params.c()
+    _check(load().ac_energy_grad(C.byref(p), fields, _dev(u, params.dtype, "u"), _dev(g, params.dtype, "g"),
+                                 _stream(stream)))
+    return g
+
+
+def ac_energy_gradient_ic(params: FineParams, steps: int, u0, checkpoint_every=32, stream=None):
+    """dE_h(u^steps)/du0 for one field by the checkpointed adjoint."""
+    import torch
+    p = params.c()
+    nbytes = load().ac_energy_gradient_workspace(C.byref(p), int(steps), int(checkpoint_every))
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=u0.device)
+    g = u0.new_empty(u0.shape)
+    _check(load().ac_energy_gradient_ic(C.byref(p), int(steps), int(checkpoint_every), _dev(u0, params.dtype, "u0"),
+                                        _dev(g, params.dtype, "grad"), _dev(ws, None, "ws"), nbytes, _stream(stream)))
+    return g
 
 
 class CoarseNet:

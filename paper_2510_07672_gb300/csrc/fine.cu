@@ -48,6 +48,14 @@ struct FineArgs {
     long long in_gs, in_off, out_gs, out_off;
     const int* map;
     int mass;        // 1: hold the (0,0) mode at the entry mean
+    // adjoint = 1 runs the transposed steps: lambda_n = a mu + dt f'(u_n) * (mu -
+    // [mass] mean mu), mu = A^{-1} lambda_{n+1}, with u_n read from
+    // states[n][field] (n = steps-1 .. 0, plain field index).
+    int adjoint;
+    const void* states;
+    // traj != NULL stores the state before the first step and after every
+    // step: traj[s][field] for s = 0..steps (plain field index).
+    void* traj;
     double a;        // 1 + S dt
     double dt;
     double lam_scale;  // dt eps^2 (4 / h^2)
@@ -94,7 +102,7 @@ fine_field_kernel(FineArgs args) {
     V* bufC = bufR + L * PITCH;                        // column-phase lines
     V* tw = bufC + L * PITCH;                          // exp(-2 pi i m / N)
     T* lam = reinterpret_cast<T*>(tw + N);             // dt eps^2 mu_k
-    double* part = reinterpret_cast<double*>(lam + N); // mass partial
+    double* part = reinterpret_cast<double*>(lam + N); // mass partial, adjoint mean
 
     const int tid = threadIdx.x;
     const int j = tid / L;       // lane within a line
@@ -124,14 +132,17 @@ fine_field_kernel(FineArgs args) {
 
     // load rows [rank R, rank R + R): line l holds rows l (real) and l + L (imag)
     double msum = 0.0;
+    T* traj0 = args.traj ? static_cast<T*>(args.traj) + size_t(field) * NN + size_t(rank) * R * N : nullptr;
+    const size_t traj_step = size_t(args.num_fields) * NN;
     for (int idx = tid; idx < R * N; idx += Sh::THREADS) {
         const int row = idx / N, c = idx % N;
         const T v = in[idx];
         msum += double(v);
         reinterpret_cast<T*>(bufR)[2 * ((row % L) * PITCH + c) + row / L] = v;
+        if (traj0) traj0[idx] = v;
     }
     double mean = 0.0;
-    if (args.mass) {
+    if (args.mass && !args.adjoint) {
         // float64 sum: warp shuffle, one value per warp, then the cluster
         constexpr int WARP = Sh::THREADS < 32 ? Sh::THREADS : 32;
         constexpr unsigned MASK = WARP == 32 ? 0xffffffffu : ((1u << WARP) - 1u);
@@ -166,12 +177,14 @@ fine_field_kernel(FineArgs args) {
     const int pair = rank * L + line;  // global row-pair index (row phase)
     const int col = rank * L + line;   // global column index (column phase)
     for (int step = 0; step < args.steps; ++step) {
-        // pointwise right-hand side on both rows of the line
+        if (!args.adjoint) {
+            // pointwise right-hand side on both rows of the line
 #pragma unroll
-        for (int t = 0; t < A; ++t) {
-            const T ur = x[t].x, ui = x[t].y;
-            x[t].x = a * ur + dt * (ur - ur * ur * ur);
-            x[t].y = a * ui + dt * (ui - ui * ui * ui);
+            for (int t = 0; t < A; ++t) {
+                const T ur = x[t].x, ui = x[t].y;
+                x[t].x = a * ur + dt * (ur - ur * ur * ur);
+                x[t].y = a * ui + dt * (ui - ui * ui * ui);
+            }
         }
         line_fft<T, N, A, B, -1>(x, tw, myR, j);
         // row spectra Z_p[k] -> column min(k, N - k) (k = 0, N/2 -> column 0)
@@ -239,9 +252,15 @@ fine_field_kernel(FineArgs args) {
                     x[t].x = zc.x * sp + zp.x * sm;
                     x[t].y = zc.y * sp - zp.y * sm;
                     if (k == 0 && args.mass) {
-                        // mean mode of u held at the entry mean (F0'(0) = mean)
-                        x[t].x = T(mean);
-                        x[t].y = zc.y * sn;
+                        if (!args.adjoint) {
+                            // mean mode of u held at the entry mean (F0'(0) = mean)
+                            x[t].x = T(mean);
+                            x[t].y = zc.y * sn;
+                        } else {
+                            // F0'(0) is mean(mu): hand it to every CTA of the
+                            // cluster before the barrier that ends the phase
+                            for (int q = 0; q < P; ++q) peer_ptr<P>(part, q)[1] = double(x[t].x);
+                        }
                     }
                 }
             }
@@ -277,6 +296,33 @@ fine_field_kernel(FineArgs args) {
             x[t] = z;
         }
         line_fft<T, N, A, B, +1>(x, tw, myR, j);
+        if (args.adjoint) {
+            // lambda_n = a mu + dt f'(u_n) (mu - mean mu), rows r0 (real) and r1 (imag)
+            const int n_state = args.steps - 1 - step;
+            const T* un = static_cast<const T*>(args.states) + (size_t(n_state) * args.num_fields + field) * NN +
+                          size_t(rank * R + line) * N;
+            const T mbar = args.mass ? T(part[1]) : T(0);
+#pragma unroll
+            for (int t = 0; t < A; ++t) {
+                const int c = j + B * t;
+                const T u0 = un[c], u1 = un[size_t(L) * N + c];
+                const T f0 = T(1) - T(3) * u0 * u0, f1 = T(1) - T(3) * u1 * u1;
+                x[t].x = a * x[t].x + dt * f0 * (x[t].x - mbar);
+                x[t].y = a * x[t].y + dt * f1 * (x[t].y - mbar);
+            }
+        }
+        if (args.traj) {
+            __syncthreads();
+#pragma unroll
+            for (int t = 0; t < A; ++t) myR[j + B * t] = x[t];
+            __syncthreads();
+            T* ts = static_cast<T*>(args.traj) + (size_t(step + 1) * traj_step) + size_t(field) * NN +
+                    size_t(rank) * R * N;
+            for (int idx = tid; idx < R * N; idx += Sh::THREADS) {
+                const int row = idx / N, c = idx % N;
+                ts[idx] = reinterpret_cast<const T*>(bufR)[2 * ((row % L) * PITCH + c) + row / L];
+            }
+        }
     }
 
     // store rows, coalesced, through bufR
@@ -357,9 +403,9 @@ static int check_params(const ac_params* p) {
     return AC_OK;
 }
 
-int fine_propagate_mapped(const ac_params* p, int groups, int per_group, int steps, const void* in,
-                          long long in_gs, long long in_off, void* out, long long out_gs,
-                          long long out_off, const int* map, cudaStream_t stream) {
+int fine_run(const ac_params* p, int groups, int per_group, int steps, const void* in, long long in_gs,
+             long long in_off, void* out, long long out_gs, long long out_off, const int* map, int adjoint,
+             const void* states, void* traj, cudaStream_t stream) {
     int rc = check_params(p);
     if (rc) return rc;
     ACPR_CHECK_ARG(groups >= 0 && per_group >= 0 && steps >= 0, "counts must be >= 0");
@@ -380,6 +426,9 @@ int fine_propagate_mapped(const ac_params* p, int groups, int per_group, int ste
     a.out_gs = out_gs;
     a.out_off = out_off;
     a.map = map;
+    a.adjoint = adjoint;
+    a.states = states;
+    a.traj = traj;
     a.mass = p->variant == AC_MASS_CONSERVING;
     a.a = 1.0 + p->S * p->dt;
     a.dt = p->dt;
@@ -387,6 +436,13 @@ int fine_propagate_mapped(const ac_params* p, int groups, int per_group, int ste
     a.lam_scale = p->dt * p->eps * p->eps * 4.0 / (h * h);
     if (p->precision == AC_F64) return dispatch_fine<double>(p->n, a, stream);
     return dispatch_fine<float>(p->n, a, stream);
+}
+
+int fine_propagate_mapped(const ac_params* p, int groups, int per_group, int steps, const void* in,
+                          long long in_gs, long long in_off, void* out, long long out_gs,
+                          long long out_off, const int* map, cudaStream_t stream) {
+    return fine_run(p, groups, per_group, steps, in, in_gs, in_off, out, out_gs, out_off, map, 0, nullptr,
+                    nullptr, stream);
 }
 
 int fine_propagate(const ac_params* p, int num_fields, int steps, const void* in, void* out,
@@ -409,4 +465,24 @@ extern "C" int ac_fine_propagate_slices(const ac_params* params, int num_fields,
                                         const void* u_starts, void* u_ends, acpr_stream stream) {
     return acpr::fine_propagate(params, num_fields, steps_per_slice, u_starts, u_ends,
                                 reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int ac_fine_trajectory(const ac_params* params, int num_fields, int steps, const void* u0, void* traj,
+                                  acpr_stream stream) {
+    using namespace acpr;
+    ACPR_CHECK_ARG(traj != nullptr, "traj is NULL");
+    // the final state also lands in traj[steps]; `out` receives it too
+    const size_t esz = params ? elem_size(params->precision) : 8;
+    void* last = params ? static_cast<char*>(traj) + size_t(steps) * num_fields * params->n * params->n * esz
+                        : nullptr;
+    return fine_run(params, 1, num_fields, steps, u0, 0, 0, last, 0, 0, nullptr, 0, nullptr, traj,
+                    reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int ac_fine_adjoint(const ac_params* params, int num_fields, int steps, const void* states,
+                               const void* lam_end, void* lam_start, acpr_stream stream) {
+    using namespace acpr;
+    ACPR_CHECK_ARG(states != nullptr, "states is NULL");
+    return fine_run(params, 1, num_fields, steps, lam_end, 0, 0, lam_start, 0, 0, nullptr, 1, states, nullptr,
+                    reinterpret_cast<cudaStream_t>(stream));
 }
