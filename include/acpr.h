@@ -101,6 +101,23 @@ const char* ac_last_error(void);
 /* 1 if the fine-step kernels are built for this (n, precision), else 0. */
 int ac_fine_supported(int n, int precision);
 
+/* Launch shapes of the fine kernel built for (n, precision) -- cluster size,
+ * threads per CTA, occupancy target -- and the one in use.  Every shape
+ * computes the same steps; they differ in how the field is split over CTAs
+ * and so in which rows share a complex line, which moves results by
+ * round-off.  Each shape is a deterministic function of its input; do not
+ * change the shape in the middle of a Parareal solve.  ac_fine_autotune runs each shape on the caller's problem
+ * (u_in -> u_out, num_fields fields, `steps` steps; twice after a warm-up),
+ * writes the mean time per call in ms to ms_out[i] (may be NULL; room for
+ * ac_fine_variant_count entries) and keeps the fastest for later calls of this
+ * process.  SYNCHRONOUS. */
+int ac_fine_variant_count(int n, int precision);
+const char* ac_fine_variant_name(int n, int precision, int index);
+int ac_fine_get_variant(int n, int precision);
+int ac_fine_set_variant(int n, int precision, int index);
+int ac_fine_autotune(const ac_params* params, int num_fields, int steps, const void* u_in, void* u_out,
+                     float* ms_out, acpr_stream stream);
+
 /* One fine step (Sec. 3.1 fine operator with one step) for each of `batch`
  * fields.  u_in, u_out: device [batch][n][n] in params->precision; they may
  * not overlap.  batch = 0 is a no-op. */

@@ -52,7 +52,8 @@ EXPORTS = ["ac_last_error", "ac_fine_supported", "ac_fine_step", "ac_fine_propag
            "parareal_residual", "parareal_residual_noalloc", "ac_parareal_create", "parareal_iterate", "ac_parareal_set_active",
            "ac_parareal_trajectory", "ac_parareal_copy_trajectory", "ac_parareal_solve", "ac_parareal_reset", "ac_parareal_enable_timing",
            "ac_parareal_get_stats", "ac_parareal_reset_stats", "ac_launch_count", "ac_parareal_destroy",
-           "ac_fine_trajectory", "ac_fine_adjoint", "ac_energy", "ac_energy_grad",
+           "ac_fine_variant_count", "ac_fine_variant_name", "ac_fine_get_variant", "ac_fine_set_variant",
+           "ac_fine_autotune", "ac_fine_trajectory", "ac_fine_adjoint", "ac_energy", "ac_energy_grad",
            "ac_energy_gradient_workspace", "ac_energy_gradient_ic",
            "cnn_train_bytes", "cnn_forward_train", "cnn_backward", "cnn_adam_step", "mse_loss_grad"]
 
@@ -96,6 +97,12 @@ def load(build_if_missing: bool = True):
         L.ac_parareal_get_stats.argtypes = [S, P(ac_parareal_stats)]
         L.ac_parareal_reset_stats.argtypes = [S]
         L.ac_launch_count.restype = C.c_longlong
+        L.ac_fine_variant_count.argtypes = [I, I]
+        L.ac_fine_variant_name.argtypes = [I, I, I]
+        L.ac_fine_variant_name.restype = C.c_char_p
+        L.ac_fine_get_variant.argtypes = [I, I]
+        L.ac_fine_set_variant.argtypes = [I, I, I]
+        L.ac_fine_autotune.argtypes = [P(ac_params), I, I, S, S, P(C.c_float), S]
         L.ac_fine_trajectory.argtypes = [P(ac_params), I, I, S, S, S]
         L.ac_fine_adjoint.argtypes = [P(ac_params), I, I, S, S, S, S]
         L.ac_energy.argtypes = [P(ac_params), I, S, S, S]
@@ -176,6 +183,34 @@ def ac_fine_propagate_slices(params: FineParams, steps: int, u_in, u_out=None, s
     _check(load().ac_fine_propagate_slices(C.byref(p), fields, int(steps), _dev(u_in, params.dtype, "u_in"),
                                            _dev(u_out, params.dtype, "u_out"), _stream(stream)))
     return u_out
+
+
+def ac_fine_variants(n: int, precision: int):
+    L = load()
+    return [L.ac_fine_variant_name(int(n), int(precision), i).decode()
+            for i in range(L.ac_fine_variant_count(int(n), int(precision)))]
+
+
+def ac_fine_set_variant(n: int, precision: int, index: int):
+    _check(load().ac_fine_set_variant(int(n), int(precision), int(index)))
+
+
+def ac_fine_get_variant(n: int, precision: int) -> int:
+    return int(load().ac_fine_get_variant(int(n), int(precision)))
+
+
+def ac_fine_autotune(params: FineParams, steps: int, u_in, u_out, stream=None):
+    """Time every launch shape on this problem, keep the fastest; returns
+    {name: ms per call} and the chosen index."""
+    L = load()
+    cnt = L.ac_fine_variant_count(params.n, params.precision)
+    ms = (C.c_float * max(cnt, 1))()
+    fields = u_in.numel() // (params.n * params.n)
+    p = params.c()
+    _check(L.ac_fine_autotune(C.byref(p), fields, int(steps), _dev(u_in, params.dtype, "u_in"),
+                              _dev(u_out, params.dtype, "u_out"), ms, _stream(stream)))
+    names = ac_fine_variants(params.n, params.precision)
+    return {names[i]: ms[i] for i in range(cnt)}, ac_fine_get_variant(params.n, params.precision)
 
 
 def ac_fine_trajectory(params: FineParams, steps: int, u0, traj=None, stream=None):

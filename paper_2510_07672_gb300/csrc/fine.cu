@@ -91,8 +91,9 @@ __device__ __forceinline__ V* peer_ptr(V* local, int rank) {
     }
 }
 
-template <typename T, int N, int P, int A, int B>
-__global__ void __launch_bounds__(FineShape<T, N, P, A, B>::THREADS, (FineShape<T, N, P, A, B>::THREADS <= 256 ? 2 : 1))
+// MINB: CTAs per SM the register allocation must allow (occupancy target).
+template <typename T, int N, int P, int A, int B, int MINB>
+__global__ void __launch_bounds__(FineShape<T, N, P, A, B>::THREADS, MINB)
 fine_field_kernel(FineArgs args) {
     using Sh = FineShape<T, N, P, A, B>;
     using V = vec2_t<T>;
@@ -337,11 +338,11 @@ fine_field_kernel(FineArgs args) {
 }
 
 // ---------------------------------------------------------------- launch --
-template <typename T, int N, int P, int A, int B>
+template <typename T, int N, int P, int A, int B, int MINB>
 static int launch_fine(const FineArgs& args, cudaStream_t stream) {
     using Sh = FineShape<T, N, P, A, B>;
-    auto kern = fine_field_kernel<T, N, P, A, B>;
-    static bool configured = false;  // attribute set once per process and device 0.. (idempotent)
+    auto kern = fine_field_kernel<T, N, P, A, B, MINB>;
+    static bool configured = false;  // per instantiation, once per process
     if (!configured) {
         ACPR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::SMEM)));
         if (P > 8)
@@ -365,29 +366,79 @@ static int launch_fine(const FineArgs& args, cudaStream_t stream) {
     return AC_OK;
 }
 
-// (precision, n) -> instantiated shape: N = A * B with B | A, P CTAs per field.
+// Launch shapes built for each (precision, n): cluster size P, threads per
+// CTA, occupancy target.  Entry 0 is the default; ac_fine_autotune times them
+// all on the caller's problem and keeps the fastest.
+struct FineVariant {
+    const char* name;
+    int (*launch)(const FineArgs&, cudaStream_t);
+};
+
+#define ACPR_FV(T, N, P, A, B, M) {"P" #P "_A" #A "_B" #B "_occ" #M, &launch_fine<T, N, P, A, B, M>}
+
 template <typename T>
-static int dispatch_fine(int n, const FineArgs& args, cudaStream_t stream) {
-    constexpr bool F32 = sizeof(T) == 4;
-    switch (n) {
-        case 8: return launch_fine<T, 8, 1, 4, 2>(args, stream);
-        case 16: return launch_fine<T, 16, 1, 4, 4>(args, stream);
-        case 32: return launch_fine<T, 32, 1, 8, 4>(args, stream);
-        case 64: return launch_fine<T, 64, 1, 8, 8>(args, stream);
-        case 128:
-            if constexpr (F32) return launch_fine<T, 128, 2, 16, 8>(args, stream);
-            else return launch_fine<T, 128, 4, 16, 8>(args, stream);
-        case 256:
-            if constexpr (F32) return launch_fine<T, 256, 8, 16, 16>(args, stream);
-            else return launch_fine<T, 256, 8, 16, 16>(args, stream);
-        default: break;
+static const FineVariant* fine_variants(int n, int* count) {
+    static const FineVariant v8[] = {ACPR_FV(T, 8, 1, 4, 2, 1)};
+    static const FineVariant v16[] = {ACPR_FV(T, 16, 1, 4, 4, 1)};
+    static const FineVariant v32[] = {ACPR_FV(T, 32, 1, 8, 4, 1)};
+    static const FineVariant v64[] = {ACPR_FV(T, 64, 1, 8, 8, 2), ACPR_FV(T, 64, 2, 8, 8, 3)};
+    if constexpr (sizeof(T) == 4) {
+        static const FineVariant v128[] = {ACPR_FV(T, 128, 2, 16, 8, 2), ACPR_FV(T, 128, 4, 16, 8, 3),
+                                           ACPR_FV(T, 128, 1, 16, 8, 1)};
+        static const FineVariant v256[] = {ACPR_FV(T, 256, 8, 16, 16, 2), ACPR_FV(T, 256, 4, 16, 16, 1),
+                                           ACPR_FV(T, 256, 16, 16, 16, 3), ACPR_FV(T, 256, 16, 16, 16, 4),
+                                           ACPR_FV(T, 256, 8, 16, 16, 1)};
+        static const FineVariant v512[] = {ACPR_FV(T, 512, 16, 32, 16, 1)};
+        switch (n) {
+            case 128: *count = 3; return v128;
+            case 256: *count = 5; return v256;
+            case 512: *count = 1; return v512;
+            default: break;
+        }
+    } else {
+        static const FineVariant v128[] = {ACPR_FV(T, 128, 4, 16, 8, 1), ACPR_FV(T, 128, 2, 16, 8, 1)};
+        static const FineVariant v256[] = {ACPR_FV(T, 256, 8, 16, 16, 2), ACPR_FV(T, 256, 16, 16, 16, 2)};
+        switch (n) {
+            case 128: *count = 2; return v128;
+            case 256: *count = 2; return v256;
+            default: break;
+        }
     }
-    set_error("ac_fine: n=%d not built for %s", n, F32 ? "AC_F32" : "AC_F64");
-    return AC_ERR_UNSUPPORTED;
+    switch (n) {
+        case 8: *count = 1; return v8;
+        case 16: *count = 1; return v16;
+        case 32: *count = 1; return v32;
+        case 64: *count = 2; return v64;
+        default: *count = 0; return nullptr;
+    }
+}
+#undef ACPR_FV
+
+namespace {
+int g_variant[2][11] = {};  // [precision][log2 n]: chosen launch shape
 }
 
-static bool fine_built(int n, int) {
-    return n == 8 || n == 16 || n == 32 || n == 64 || n == 128 || n == 256;
+static const FineVariant* pick_variant(int n, int precision, int* count) {
+    const FineVariant* v = precision == AC_F64 ? fine_variants<double>(n, count) : fine_variants<float>(n, count);
+    return v;
+}
+
+template <typename T>
+static int dispatch_fine(int n, const FineArgs& args, cudaStream_t stream) {
+    int count = 0;
+    const FineVariant* v = fine_variants<T>(n, &count);
+    if (!v || !count) {
+        set_error("ac_fine: n=%d not built for %s", n, sizeof(T) == 8 ? "AC_F64" : "AC_F32");
+        return AC_ERR_UNSUPPORTED;
+    }
+    int idx = g_variant[sizeof(T) == 8 ? AC_F64 : AC_F32][ilog2(n)];
+    if (idx < 0 || idx >= count) idx = 0;
+    return v[idx].launch(args, stream);
+}
+
+static bool fine_built(int n, int precision) {
+    int count = 0;
+    return is_pow2(n) && n <= 1024 && pick_variant(n, precision, &count) != nullptr && count > 0;
 }
 
 static int check_params(const ac_params* p) {
@@ -485,4 +536,64 @@ extern "C" int ac_fine_adjoint(const ac_params* params, int num_fields, int step
     ACPR_CHECK_ARG(states != nullptr, "states is NULL");
     return fine_run(params, 1, num_fields, steps, lam_end, 0, 0, lam_start, 0, 0, nullptr, 1, states, nullptr,
                     reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int ac_fine_variant_count(int n, int precision) {
+    int count = 0;
+    if (!acpr::is_pow2(n) || n > 1024 || (precision != AC_F32 && precision != AC_F64)) return 0;
+    acpr::pick_variant(n, precision, &count);
+    return count;
+}
+
+extern "C" const char* ac_fine_variant_name(int n, int precision, int index) {
+    int count = ac_fine_variant_count(n, precision);
+    if (index < 0 || index >= count) return "";
+    return acpr::pick_variant(n, precision, &count)[index].name;
+}
+
+extern "C" int ac_fine_get_variant(int n, int precision) {
+    if (!ac_fine_variant_count(n, precision)) return -1;
+    return acpr::g_variant[precision][acpr::ilog2(n)];
+}
+
+extern "C" int ac_fine_set_variant(int n, int precision, int index) {
+    using namespace acpr;
+    const int count = ac_fine_variant_count(n, precision);
+    ACPR_CHECK_ARG(count > 0, "n=%d precision %d not built", n, precision);
+    ACPR_CHECK_ARG(index >= 0 && index < count, "variant %d out of range (%d built)", index, count);
+    g_variant[precision][ilog2(n)] = index;
+    return AC_OK;
+}
+
+extern "C" int ac_fine_autotune(const ac_params* params, int num_fields, int steps, const void* u_in, void* u_out,
+                                float* ms_out, acpr_stream stream) {
+    using namespace acpr;
+    int rc = check_params(params);
+    if (rc) return rc;
+    ACPR_CHECK_ARG(num_fields >= 1 && steps >= 1 && u_in && u_out, "bad autotune arguments");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int count = ac_fine_variant_count(params->n, params->precision);
+    cudaEvent_t e0, e1;
+    ACPR_CUDA(cudaEventCreate(&e0));
+    ACPR_CUDA(cudaEventCreate(&e1));
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int v = 0; v < count; ++v) {
+        g_variant[params->precision][ilog2(params->n)] = v;
+        rc = fine_propagate(params, num_fields, steps, u_in, u_out, st);  // warm-up
+        if (rc) break;
+        ACPR_CUDA(cudaEventRecord(e0, st));
+        for (int rep = 0; rep < 2 && !rc; ++rep) rc = fine_propagate(params, num_fields, steps, u_in, u_out, st);
+        ACPR_CUDA(cudaEventRecord(e1, st));
+        ACPR_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        ACPR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        ms *= 0.5f;
+        if (ms_out) ms_out[v] = ms;
+        if (ms < best_ms) { best_ms = ms; best = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g_variant[params->precision][ilog2(params->n)] = best;
+    return rc ? rc : AC_OK;
 }

@@ -23,7 +23,7 @@ def dev(a, dtype):
 
 
 CASES_F64 = [(8, 0), (16, 1), (32, 0), (64, 0), (64, 1), (128, 1)]
-CASES_F32 = [(16, 0), (64, 1), (128, 0), (128, 1), (256, 0), (256, 1)]
+CASES_F32 = [(16, 0), (64, 1), (128, 0), (128, 1), (256, 0), (256, 1), (512, 0), (512, 1)]
 
 
 @pytest.mark.parametrize("n,variant", CASES_F64)
@@ -121,3 +121,41 @@ def test_full_size_sampled():
         ref = O.fine_propagate(p, steps, ics[f].astype(np.float64))
         assert np.abs(out[f] - ref).max() < 2e-5 * np.sqrt(steps)
     assert np.isfinite(out).all()
+
+
+@pytest.mark.parametrize("n,prec", [(64, G.AC_F32), (128, G.AC_F32), (256, G.AC_F32), (128, G.AC_F64),
+                                    (256, G.AC_F64)])
+def test_every_launch_shape_computes_the_same(n, prec):
+    """The launch shapes only re-partition the field over CTAs.  Rows travel in
+    pairs (rows l and l + R/2 of a CTA's R rows), so the pairing, and with it
+    the rounding, follows the partition: every shape agrees with the default to
+    round-off (float32: 1e-5 after 7 steps; float64: 1e-12), and each shape is
+    bitwise reproducible on its own."""
+    dt = torch.float64 if prec == G.AC_F64 else torch.float32
+    names = G.ac_fine_variants(n, prec)
+    assert names
+    u = dev(np.stack([I.random_field(n, seed=s) for s in range(5)]), dt)
+    outs = {}
+    for variant in (0, 1):
+        fp = G.FineParams(n, 2.5 / n, 2.0, 5e-5, variant=variant, precision=prec)
+        for i in range(len(names)):
+            G.ac_fine_set_variant(n, prec, i)
+            outs[(variant, i)] = G.ac_fine_propagate_slices(fp, 7, u)
+        tol = 1e-12 if prec == G.AC_F64 else 1e-5
+        for i in range(1, len(names)):
+            assert (outs[(variant, i)] - outs[(variant, 0)]).abs().max().item() < tol, names[i]
+            G.ac_fine_set_variant(n, prec, i)
+            assert torch.equal(G.ac_fine_propagate_slices(fp, 7, u), outs[(variant, i)]), names[i]
+    G.ac_fine_set_variant(n, prec, 0)
+
+
+def test_autotune_picks_a_shape():
+    n = 256
+    fp = G.FineParams(n, 0.01, 2.0, 5e-5, variant=1, precision=G.AC_F32)
+    u = dev(np.stack([I.random_field(n, seed=s, zero_mean=True) for s in range(64)]), torch.float32)
+    out = torch.empty_like(u)
+    times, idx = G.ac_fine_autotune(fp, 10, u, out)
+    assert len(times) == len(G.ac_fine_variants(n, G.AC_F32))
+    assert all(t > 0 for t in times.values())
+    assert times[G.ac_fine_variants(n, G.AC_F32)[idx]] == min(times.values())
+    G.ac_fine_set_variant(n, G.AC_F32, 0)
