@@ -108,8 +108,10 @@ __device__ __forceinline__ void reg_dft(T (&re)[M], T (&im)[M]) {
 //   line: base of this line's exchange area in shared memory (>= N elements);
 //   j:    this thread's lane within the line.
 // Unnormalised, X_k = sum_n x_n exp(SIGN 2 pi i n k / N).
-// Contains __syncthreads(): every thread of the block must call it.
-template <typename T, int N, int A, int B, int SIGN>
+// Contains __syncthreads(): every thread of the block must call it.  With
+// SYNC_BEFORE = false the caller guarantees that no thread still reads `line`
+// from an earlier use (a block or cluster barrier lies in between).
+template <typename T, int N, int A, int B, int SIGN, bool SYNC_BEFORE = true>
 __device__ __forceinline__ void line_fft(vec2_t<T> (&x)[A], const vec2_t<T>* __restrict__ tw,
                                          vec2_t<T>* line, int j) {
     static_assert(A * B == N && A % B == 0, "N = A * B with B | A");
@@ -128,7 +130,7 @@ __device__ __forceinline__ void line_fft(vec2_t<T> (&x)[A], const vec2_t<T>* __r
         im[k1] = re[k1] * s + im[k1] * c;
         re[k1] = r;
     }
-    __syncthreads();  // previous readers of `line` are done
+    if constexpr (SYNC_BEFORE) __syncthreads();  // previous readers of `line` are done
 #pragma unroll
     for (int k1 = 0; k1 < A; ++k1) {
         vec2_t<T> v;

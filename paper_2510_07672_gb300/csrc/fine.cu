@@ -69,9 +69,15 @@ struct FineShape {
     static constexpr int THREADS = L * B;     // (line, lane) pairs
     static constexpr int PITCH = N + 1;       // complex elements per smem line
     static constexpr size_t BUF = sizeof(vec2_t<T>) * size_t(L) * PITCH;
-    static constexpr size_t SMEM = 2 * BUF + sizeof(vec2_t<T>) * N + sizeof(T) * N + 4 * sizeof(double);
+    // bufR, bufC (DSMEM transpose targets), bufX (line-FFT exchanges), tables
+    static constexpr size_t SMEM = 3 * BUF + sizeof(vec2_t<T>) * N + sizeof(T) * N + 4 * sizeof(double);
     static_assert(R >= 2 && R % 2 == 0, "need at least two rows per CTA");
 };
+
+// Division where float32 round-off of a couple of ulp is harmless (the
+// symbol); float64 keeps the IEEE division.
+__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 
 template <int P>
 __device__ __forceinline__ void cluster_barrier() {
@@ -101,7 +107,8 @@ fine_field_kernel(FineArgs args) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* bufR = reinterpret_cast<V*>(smem_raw);         // row-phase lines
     V* bufC = bufR + L * PITCH;                        // column-phase lines
-    V* tw = bufC + L * PITCH;                          // exp(-2 pi i m / N)
+    V* bufX = bufC + L * PITCH;                        // line-FFT exchanges
+    V* tw = bufX + L * PITCH;                          // exp(-2 pi i m / N)
     T* lam = reinterpret_cast<T*>(tw + N);             // dt eps^2 mu_k
     double* part = reinterpret_cast<double*>(lam + N); // mass partial, adjoint mean
 
@@ -168,6 +175,7 @@ fine_field_kernel(FineArgs args) {
     V x[A];
     V* myR = bufR + line * PITCH;
     V* myC = bufC + line * PITCH;
+    V* myX = bufX + line * PITCH;
 #pragma unroll
     for (int t = 0; t < A; ++t) x[t] = myR[j + B * t];
 
@@ -177,6 +185,11 @@ fine_field_kernel(FineArgs args) {
     const T half = T(0.5);
     const int pair = rank * L + line;  // global row-pair index (row phase)
     const int col = rank * L + line;   // global column index (column phase)
+    // Exchange buffers and barriers per step.  The row FFTs exchange through
+    // bufR after it has been read (forward) or through bufX (inverse), the
+    // column FFTs through bufX, the column-0 split through bufC; each buffer's
+    // previous readers are separated from its next writers by a block or
+    // cluster barrier, so only the barrier after each exchange write remains.
     for (int step = 0; step < args.steps; ++step) {
         if (!args.adjoint) {
             // pointwise right-hand side on both rows of the line
@@ -187,7 +200,10 @@ fine_field_kernel(FineArgs args) {
                 x[t].y = a * ui + dt * (ui - ui * ui * ui);
             }
         }
-        line_fft<T, N, A, B, -1>(x, tw, myR, j);
+        // bufR: its last readers (the rebuild, before the previous inverse
+        // row FFT's barrier) are done; peers write it only after barrier 1
+        if (step == 0) __syncthreads();
+        line_fft<T, N, A, B, -1, false>(x, tw, myR, j);
         // row spectra Z_p[k] -> column min(k, N - k) (k = 0, N/2 -> column 0)
 #pragma unroll
         for (int t = 0; t < A; ++t) {
@@ -218,13 +234,14 @@ fine_field_kernel(FineArgs args) {
             }
             x[t] = v;
         }
-        line_fft<T, N, A, B, -1>(x, tw, myC, j);
+        // bufX: last read in the previous step's inverse FFTs, before barrier 2
+        line_fft<T, N, A, B, -1, false>(x, tw, myX, j);
         // divide by the symbol, with 1/N^2 of the inverse folded in
         if (col != 0) {
             const T lam_l = lam[col];
 #pragma unroll
             for (int t = 0; t < A; ++t) {
-                const T s = inv_nn / (a + (lam[j + B * t] + lam_l));
+                const T s = fast_div(inv_nn, a + (lam[j + B * t] + lam_l));
                 x[t].x *= s;
                 x[t].y *= s;
             }
@@ -233,7 +250,8 @@ fine_field_kernel(FineArgs args) {
             // column 0 carries columns 0 and N/2 as C = F0 + i FN: separate
             // them with C[N - k], scale each by its own symbol, recombine:
             // C'[k] = C[k] (s0 + sN) / 2 + conj(C[N - k]) (s0 - sN) / 2
-            __syncthreads();
+            // (through bufC: its readers, the split, finished before the
+            // column FFT's exchange barrier)
             if (col == 0) {
 #pragma unroll
                 for (int t = 0; t < A; ++t) myC[j + B * t] = x[t];
@@ -247,8 +265,8 @@ fine_field_kernel(FineArgs args) {
                     const V zc = x[t];
                     const V zp = myC[(N - k) & (N - 1)];
                     const T lk = lam[k];
-                    const T s0 = inv_nn / (a + lk);
-                    const T sn = inv_nn / (a + (lk + lam_n));
+                    const T s0 = fast_div(inv_nn, a + lk);
+                    const T sn = fast_div(inv_nn, a + (lk + lam_n));
                     const T sp = half * (s0 + sn), sm = half * (s0 - sn);
                     x[t].x = zc.x * sp + zp.x * sm;
                     x[t].y = zc.y * sp - zp.y * sm;
@@ -266,7 +284,8 @@ fine_field_kernel(FineArgs args) {
                 }
             }
         }
-        line_fft<T, N, A, B, +1>(x, tw, myC, j);
+        // bufX: its readers (forward column FFT) finished before the barrier above
+        line_fft<T, N, A, B, +1, false>(x, tw, myX, j);
         // column values V_r[c] -> owner of row r, slot (row role) and column c
 #pragma unroll
         for (int t = 0; t < A; ++t) {
@@ -296,7 +315,8 @@ fine_field_kernel(FineArgs args) {
             }
             x[t] = z;
         }
-        line_fft<T, N, A, B, +1>(x, tw, myR, j);
+        // bufX: last read in the inverse column FFT, before barrier 2
+        line_fft<T, N, A, B, +1, false>(x, tw, myX, j);
         if (args.adjoint) {
             // lambda_n = a mu + dt f'(u_n) (mu - mean mu), rows r0 (real) and r1 (imag)
             const int n_state = args.steps - 1 - step;
@@ -323,6 +343,7 @@ fine_field_kernel(FineArgs args) {
                 const int row = idx / N, c = idx % N;
                 ts[idx] = reinterpret_cast<const T*>(bufR)[2 * ((row % L) * PITCH + c) + row / L];
             }
+            __syncthreads();  // the next forward row FFT writes bufR without a leading barrier
         }
     }
 
