@@ -280,6 +280,19 @@ int ac_parareal_create(const ac_params* params, const cnn_desc* coarse, int prob
                        int num_slices, int steps_per_slice, const void* u0,
                        ac_parareal** out);
 
+/* As ac_parareal_create for problems that share params and coarse net but
+ * have their own slice counts num_slices[p] and fine steps per slice
+ * steps_per_slice[p] (host arrays of `problems` ints).  The fine solves of all
+ * problems run in one launch per iteration (work items longest first); the
+ * coarse sweep batches, at each slice, the problems that still have it. */
+int ac_parareal_create_uneven(const ac_params* params, const cnn_desc* coarse, int problems,
+                              const int* num_slices, const int* steps_per_slice, const void* u0,
+                              ac_parareal** out);
+
+/* Capture each iteration's device work into a CUDA graph the first time a
+ * (k, active problems) pair is met and replay it afterwards. */
+int ac_parareal_enable_graphs(ac_parareal* state, int on);
+
 /* One iteration of Algorithm 2 on every problem not yet converged.
  * *k_inout = 0 runs the initial coarse sweep U^0_{n+1} = G(U^0_n); k >= 1 runs
  * the fine solves F(U^{k-1}_n), n = k-1..s-1, then the sequential correction
@@ -336,6 +349,13 @@ int ac_parareal_reset_stats(ac_parareal* state);
 /* Number of kernels this library has launched in this process (all entry
  * points, all devices).  Lets a caller count the launches of a region. */
 long long ac_launch_count(void);
+
+/* ac_parareal_solve on `count` handles (e.g. one per grid size) at once:
+ * every iteration is launched on all handles' streams before any is waited
+ * for, so their kernels overlap.  iters_out / rel_l2_out: host arrays with the
+ * handles' problems one after another.  SYNCHRONOUS. */
+int ac_parareal_solve_many(ac_parareal* const* states, int count, const acpr_stream* streams, double tol,
+                           int kmax, int* iters_out, double* rel_l2_out);
 
 void ac_parareal_destroy(ac_parareal* state);
 

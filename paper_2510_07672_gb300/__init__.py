@@ -14,6 +14,6 @@ from .abi import (  # noqa: F401
     ac_fine_variants, ac_fine_set_variant, ac_fine_get_variant, ac_fine_autotune,
     ac_fine_trajectory, ac_fine_adjoint, ac_energy, ac_energy_grad, ac_energy_gradient_ic,
     cnn_packed_bytes, cnn_work_bytes, cnn_pack_weights, cnn_coarse_step,
-    parareal_residual, parareal_residual_noalloc, ac_launch_count, Parareal, CoarseNet, FineParams,
+    parareal_residual, parareal_residual_noalloc, ac_launch_count, parareal_solve_many, Parareal, CoarseNet, FineParams,
     TrainableCoarseNet, mse_loss_grad, coarse_step_function,
 )

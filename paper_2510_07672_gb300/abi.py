@@ -50,7 +50,8 @@ class ac_parareal_stats(C.Structure):
 EXPORTS = ["ac_last_error", "ac_fine_supported", "ac_fine_step", "ac_fine_propagate_slices",
            "cnn_packed_bytes", "cnn_work_bytes", "cnn_pack_weights", "cnn_coarse_step",
            "parareal_residual", "parareal_residual_noalloc", "ac_parareal_create", "parareal_iterate", "ac_parareal_set_active",
-           "ac_parareal_trajectory", "ac_parareal_copy_trajectory", "ac_parareal_solve", "ac_parareal_reset", "ac_parareal_enable_timing",
+           "ac_parareal_trajectory", "ac_parareal_copy_trajectory", "ac_parareal_solve", "ac_parareal_create_uneven", "ac_parareal_enable_graphs",
+           "ac_parareal_solve_many", "ac_parareal_reset", "ac_parareal_enable_timing",
            "ac_parareal_get_stats", "ac_parareal_reset_stats", "ac_launch_count", "ac_parareal_destroy",
            "ac_fine_variant_count", "ac_fine_variant_name", "ac_fine_get_variant", "ac_fine_set_variant",
            "ac_fine_autotune", "ac_fine_trajectory", "ac_fine_adjoint", "ac_energy", "ac_energy_grad",
@@ -92,6 +93,9 @@ def load(build_if_missing: bool = True):
         L.ac_parareal_trajectory.restype = S
         L.ac_parareal_copy_trajectory.argtypes = [S, S, S]
         L.ac_parareal_solve.argtypes = [S, D, I, P(I), P(D), S]
+        L.ac_parareal_create_uneven.argtypes = [P(ac_params), P(cnn_desc), I, P(I), P(I), S, P(S)]
+        L.ac_parareal_enable_graphs.argtypes = [S, I]
+        L.ac_parareal_solve_many.argtypes = [P(S), I, P(S), D, I, P(I), P(D)]
         L.ac_parareal_reset.argtypes = [S, S, S]
         L.ac_parareal_enable_timing.argtypes = [S, I]
         L.ac_parareal_get_stats.argtypes = [S, P(ac_parareal_stats)]
@@ -432,6 +436,25 @@ def cnn_coarse_step(net: CoarseNet, u_in, u_out=None, stream=None):
     return u_out
 
 
+def parareal_solve_many(handles, streams, tol, kmax, allow_unconverged=False):
+    """ac_parareal_solve_many over Parareal handles (one stream each)."""
+    L = load()
+    total = sum(h.problems for h in handles)
+    hs = (C.c_void_p * len(handles))(*[h._h.value for h in handles])
+    ss = (C.c_void_p * len(handles))(*[s.cuda_stream for s in streams])
+    it = (C.c_int * total)()
+    l2 = (C.c_double * total)()
+    rc = L.ac_parareal_solve_many(hs, len(handles), ss, float(tol), int(kmax), it, l2)
+    if rc != AC_OK and not (allow_unconverged and rc == -6):
+        _check(rc)
+    out, i = [], 0
+    for h in handles:
+        out.append((list(it[i:i + h.problems]), list(l2[i:i + h.problems])))
+        h.k = max(h.k, max(it[i:i + h.problems]) + 1)
+        i += h.problems
+    return out
+
+
 def ac_launch_count() -> int:
     return int(load().ac_launch_count())
 
@@ -463,21 +486,33 @@ def parareal_residual_noalloc(U_new, U_old, out, precision=None, stream=None):
 
 
 class Parareal:
-    """Handle on ac_parareal: Algorithm 2 for `problems` independent problems."""
+    """Handle on ac_parareal: Algorithm 2 for `problems` independent problems.
+    `slices` / `steps` may be per-problem sequences (ac_parareal_create_uneven)."""
 
-    def __init__(self, params: FineParams, net: CoarseNet, u0, slices: int, steps: int):
+    def __init__(self, params: FineParams, net: CoarseNet, u0, slices, steps):
         import torch
         self.params, self.net = params, net
         self.problems = u0.shape[0] if u0.dim() == 3 else 1
-        self.s, self.c = int(slices), int(steps)
         self._u0 = u0.contiguous()
         p = params.c()
         d = net.desc()
         h = C.c_void_p()
-        _check(load().ac_parareal_create(C.byref(p), C.byref(d), self.problems, self.s, self.c,
-                                         _dev(self._u0, params.dtype, "u0"), C.byref(h)))
+        if isinstance(slices, int) and isinstance(steps, int):
+            self.s, self.c = int(slices), int(steps)
+            _check(load().ac_parareal_create(C.byref(p), C.byref(d), self.problems, self.s, self.c,
+                                             _dev(self._u0, params.dtype, "u0"), C.byref(h)))
+        else:
+            sl = [int(x) for x in (slices if not isinstance(slices, int) else [slices] * self.problems)]
+            st = [int(x) for x in (steps if not isinstance(steps, int) else [steps] * self.problems)]
+            self.s, self.c = max(sl), st
+            _check(load().ac_parareal_create_uneven(C.byref(p), C.byref(d), self.problems, (C.c_int * len(sl))(*sl),
+                                                    (C.c_int * len(st))(*st), _dev(self._u0, params.dtype, "u0"),
+                                                    C.byref(h)))
         self._h = h
         self.k = 0
+
+    def enable_graphs(self, on=True):
+        _check(load().ac_parareal_enable_graphs(self._h, int(on)))
 
     def iterate(self, stream=None):
         kk = C.c_int(self.k)

@@ -155,13 +155,17 @@ __global__ void conv_hidden_bf16_cc_kernel(const __nv_bfloat16* __restrict__ in,
 
 // Last layer C -> 1 with the residual add in float32.
 template <int C>
+// With zpart != NULL every block also writes the float64 sum of its stack
+// outputs z (before the residual) to zpart[blockIdx.x]; a block never spans
+// two fields (blockDim.x divides n^2).
 __global__ void conv_last_bf16_kernel(const __nv_bfloat16* __restrict__ in, float* __restrict__ out,
                                       const float* __restrict__ W, const float* __restrict__ bias,
                                       const float* __restrict__ u, int batch, int n, int residual,
-                                      BatchIO io) {
-    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+                                      BatchIO io, double* __restrict__ zpart) {
+    const long long pix0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nn = (long long)n * n;
-    if (pix >= nn * batch) return;
+    const bool valid = pix0 < nn * batch;
+    const long long pix = valid ? pix0 : 0;
     const int b = int(pix / nn);
     const int y = int((pix % nn) / n), x = int(pix % n);
     const long long fi = bsel(io.in_map, b), fo = bsel(io.out_map, b);
@@ -178,9 +182,46 @@ __global__ void conv_last_bf16_kernel(const __nv_bfloat16* __restrict__ in, floa
                 acc = fmaf(bf16r(__ldg(W + ((kc * 8 + i) * 9 + t))), __bfloat162float(v8[i]), acc);
         }
     }
-    float z = acc + bias[0];
+    const float zs = acc + bias[0];
+    float z = zs;
     if (residual) z += u[fi * io.in_bs + pix % nn];
-    out[fo * io.out_bs + pix % nn] = z;
+    if (valid) out[fo * io.out_bs + pix % nn] = z;
+    if (zpart) {
+        double v = valid ? double(zs) : 0.0;
+        __shared__ double red[32];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < int((blockDim.x + 31) >> 5); ++w) t += red[w];
+            zpart[blockIdx.x] = t;
+        }
+    }
+}
+
+// mACNN mass shift from the stack-output sums: out += -(sum z) / n^2 per
+// field.  Grid (chunks, batch); each block forms the field's sum from its
+// `bpf` block partials in a fixed order (deterministic), then shifts a chunk.
+constexpr int kMassThreads = 256;
+__global__ void mass_apply_kernel(float* __restrict__ out, const double* __restrict__ zpart, int bpf, int n,
+                                  BatchIO io) {
+    const long long nn = (long long)n * n;
+    const int b = blockIdx.y;
+    __shared__ double red[kMassThreads];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < bpf; i += kMassThreads) s += zpart[(long long)b * bpf + i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kMassThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const float shift = float(-red[0] / double(nn));
+    float* ob = out + bsel(io.out_map, b) * io.out_bs;
+    for (long long i = (long long)blockIdx.x * kMassThreads + threadIdx.x; i < nn;
+         i += (long long)gridDim.x * kMassThreads)
+        ob[i] += shift;
 }
 
 // mACNN mass shift then bound limiter, one block per field (deterministic
@@ -235,9 +276,42 @@ int check_cnn(const cnn_desc* d) {
     return AC_OK;
 }
 
+static int last_threads(int n) { return n * n >= 128 ? 128 : n * n; }
+
 size_t work_bytes_for(const cnn_desc* d, int n, int batch) {
     const size_t act = size_t(batch) * d->channels * n * n * (d->precision == AC_F64 ? 8 : 2);
-    return 2 * act;
+    const size_t zpart = size_t(batch) * (size_t(n) * n / last_threads(n)) * sizeof(double);
+    return 2 * act + zpart;
+}
+
+// Last layer and (if d->mass_fix) the mass shift, for the AC_F32 path.
+template <int C>
+static int last_layer_f32(const cnn_desc* d, int n, int batch, const __nv_bfloat16* a, float* out,
+                          const float* W, const float* Bv, const float* u, const BatchIO& io, double* zpart,
+                          cudaStream_t st) {
+    const int threads = last_threads(n);
+    const long long pixels = (long long)n * n * batch;
+    const unsigned blocks = unsigned((pixels + threads - 1) / threads);
+    conv_last_bf16_kernel<C><<<blocks, threads, 0, st>>>(a, out, W, Bv, u, batch, n, d->residual, io,
+                                                         d->mass_fix ? zpart : nullptr);
+    ACPR_LAUNCH_CHECK();
+    if (d->mass_fix) {
+        const int bpf = int((long long)n * n / threads);
+        const long long chunks = ((long long)n * n + kMassThreads * 8 - 1) / (kMassThreads * 8);
+        mass_apply_kernel<<<dim3(unsigned(chunks), unsigned(batch)), kMassThreads, 0, st>>>(out, zpart, bpf, n, io);
+        ACPR_LAUNCH_CHECK();
+    }
+    return AC_OK;
+}
+
+int last_layer_bf16(const cnn_desc* d, int n, int batch, const __nv_bfloat16* a, float* out, const float* W,
+                    const float* Bv, const float* u, double* zpart, cudaStream_t st) {
+    BatchIO io{nullptr, nullptr, (long long)n * n, (long long)n * n, 1, 1};
+    switch (d->channels) {
+        case 16: return last_layer_f32<16>(d, n, batch, a, out, W, Bv, u, io, zpart, st);
+        case 32: return last_layer_f32<32>(d, n, batch, a, out, W, Bv, u, io, zpart, st);
+        default: return last_layer_f32<64>(d, n, batch, a, out, W, Bv, u, io, zpart, st);
+    }
 }
 
 template <int C>
@@ -266,9 +340,9 @@ static int run_f32(const cnn_desc* d, int n, int batch, const float* u, float* o
         boff += C;
         __nv_bfloat16* t = a0; a0 = a1; a1 = t;
     }
-    conv_last_bf16_kernel<C><<<blocks, threads, 0, st>>>(a0, out, W + woff, Bv + boff, u, batch, n, d->residual, io);
-    ACPR_LAUNCH_CHECK();
-    return AC_OK;
+    double* zpart = reinterpret_cast<double*>(static_cast<unsigned char*>(d->work) +
+                                              2 * act_elems * sizeof(__nv_bfloat16));
+    return last_layer_f32<C>(d, n, batch, a0, out, W + woff, Bv + boff, u, io, zpart, st);
 }
 
 static int run_f64(const cnn_desc* d, int n, int batch, const double* u, double* out, const BatchIO& io,
@@ -335,13 +409,13 @@ int coarse_step_mapped(const cnn_desc* d, int n, int batch, const void* u_in, lo
         }
     }
     if (rc) return rc;
-    if (d->mass_fix || d->limiter) {
+    if ((d->precision == AC_F64 && d->mass_fix) || d->limiter) {
         if (d->precision == AC_F64)
             post_kernel<double><<<batch, 256, 0, st>>>(static_cast<const double*>(u_in), static_cast<double*>(u_out), n,
                                                        d->mass_fix, d->limiter, d->lo, d->hi, io);
         else
             post_kernel<float><<<batch, 256, 0, st>>>(static_cast<const float*>(u_in), static_cast<float*>(u_out), n,
-                                                      d->mass_fix, d->limiter, d->lo, d->hi, io);
+                                                      0, d->limiter, d->lo, d->hi, io);
         ACPR_LAUNCH_CHECK();
     }
     return AC_OK;
@@ -350,13 +424,6 @@ int coarse_step_mapped(const cnn_desc* d, int n, int batch, const void* u_in, lo
 int coarse_step(const cnn_desc* d, int n, int batch, const void* u_in, void* u_out, cudaStream_t st) {
     const long long nn = (long long)n * n;
     return coarse_step_mapped(d, n, batch, u_in, nn, nullptr, u_out, nn, nullptr, st);
-}
-
-int mass_shift_f32(const float* u, float* out, int n, int batch, cudaStream_t st) {
-    BatchIO io{nullptr, nullptr, (long long)n * n, (long long)n * n, 1, 1};
-    post_kernel<float><<<batch, 256, 0, st>>>(u, out, n, 1, 0, 0.0, 0.0, io);
-    ACPR_LAUNCH_CHECK();
-    return AC_OK;
 }
 
 size_t packed_bytes_for(const cnn_desc* d) {

@@ -29,9 +29,10 @@ int coarse_step_mapped(const cnn_desc* d, int n, int batch, const void* u_in, lo
                        const int* in_map, void* u_out, long long out_bs, const int* out_map,
                        cudaStream_t st);
 size_t work_bytes_for(const cnn_desc* d, int n, int batch);
-// mACNN mass shift of the inference path: out += mean(u) - mean(out) per field
-// (float64 sums, fixed order).
-int mass_shift_f32(const float* u, float* out, int n, int batch, cudaStream_t st);
+// Last conv layer (C -> 1, residual) of the AC_F32 path and, with
+// d->mass_fix, the mACNN mass shift; zpart: batch * n^2/128 doubles of scratch.
+int last_layer_bf16(const cnn_desc* d, int n, int batch, const __nv_bfloat16* a, float* out, const float* W,
+                    const float* Bv, const float* u, double* zpart, cudaStream_t st);
 
 // Packed bf16 weights of the hidden C -> C layers, per layer
 // [tap 9][k-chunk C/8][cout C][8 input channels] (the K-major core-matrix

@@ -23,6 +23,7 @@
 //   Wt                bf16 (L-2) x 9*C*C          transposed, flipped hidden weights
 //   partials          f32  kChunks x 9 x (C*C + C)  weight / bias gradient partials
 //   g centred         f32  [B][n][n]               (mass shift only)
+//   z partials        f64  block sums of the last layer (mass shift only)
 #include <cuda_bf16.h>
 
 #include "cnn.cuh"
@@ -36,7 +37,7 @@ __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >
 
 struct TrainLayout {
     size_t a_bytes, z_bytes;    // one layer
-    size_t off_a, off_z, off_dz, off_wt, off_part, off_gc, total;
+    size_t off_a, off_z, off_dz, off_wt, off_part, off_gc, off_zpart, total;
 };
 
 static TrainLayout train_layout(const cnn_desc* d, int n, int batch) {
@@ -52,7 +53,8 @@ static TrainLayout train_layout(const cnn_desc* d, int n, int batch) {
     const size_t wt = size_t(L > 2 ? L - 2 : 0) * 9 * d->channels * d->channels * 2;
     t.off_part = (t.off_wt + wt + 255) / 256 * 256;
     t.off_gc = t.off_part + size_t(kChunks) * 9 * (size_t(d->channels) * d->channels + d->channels) * 4;
-    t.total = t.off_gc + size_t(batch) * n * n * 4;
+    t.off_zpart = t.off_gc + size_t(batch) * n * n * 4;
+    t.total = t.off_zpart + size_t(batch) * n * n * sizeof(double);  // >= batch * n^2/128 partials
     return t;
 }
 
@@ -89,32 +91,6 @@ __global__ void first_fwd_save_kernel(const float* __restrict__ u, __nv_bfloat16
         reinterpret_cast<float4*>(z0 + off)[0] = *reinterpret_cast<const float4*>(z8);
         reinterpret_cast<float4*>(z0 + off)[1] = *reinterpret_cast<const float4*>(z8 + 4);
     }
-}
-
-// Last layer C -> 1 plus the residual (float32 output).
-template <int C>
-__global__ void last_fwd_kernel(const __nv_bfloat16* __restrict__ in, float* __restrict__ out,
-                                const float* __restrict__ W, const float* __restrict__ bias,
-                                const float* __restrict__ u, int batch, int n) {
-    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long nn = (long long)n * n;
-    if (pix >= nn * batch) return;
-    const int b = int(pix / nn);
-    const int y = int((pix % nn) / n), x = int(pix % n);
-    float acc = 0.f;
-    for (int kc = 0; kc < C / 8; ++kc) {
-        const __nv_bfloat16* plane = in + ((long long)b * (C / 8) + kc) * nn * 8;
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const uint4 raw = *reinterpret_cast<const uint4*>(
-                plane + ((long long)wrapi(y + t / 3 - 1, n) * n + wrapi(x + t % 3 - 1, n)) * 8);
-            const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&raw);
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                acc = fmaf(bf16r(__ldg(W + ((kc * 8 + i) * 9 + t))), __bfloat162float(v8[i]), acc);
-        }
-    }
-    out[pix] = u[pix] + (acc + bias[0]);
 }
 
 // ------------------------------------------------------------ backward ----
@@ -339,10 +315,10 @@ static int forward_train(const cnn_desc* d, int n, int batch, const float* u, fl
         woff += size_t(C) * C * 9;
         boff += C;
     }
-    last_fwd_kernel<C><<<blocks, 128, 0, st>>>(A(d->layers - 1), out, W + woff, Bv + boff, u, batch, n);
-    ACPR_LAUNCH_CHECK();
-    if (d->mass_fix) return mass_shift_f32(u, out, n, batch, st);
-    return AC_OK;
+    // the inference path's last layer and mass shift, so that the training
+    // forward equals cnn_coarse_step bit for bit
+    double* zpart = reinterpret_cast<double*>(ws + t.off_zpart);
+    return last_layer_bf16(d, n, batch, A(d->layers - 1), out, W + woff, Bv + boff, u, zpart, st);
 }
 
 template <int C>

@@ -47,6 +47,9 @@ struct FineArgs {
     int per_group;
     long long in_gs, in_off, out_gs, out_off;
     const int* map;
+    // Work list (overrides the mapping above and `steps`): field f reads field
+    // work[f].x of `in`, writes field work[f].y of `out`, runs work[f].z steps.
+    const int4* work;
     int mass;        // 1: hold the (0,0) mode at the entry mean
     // adjoint = 1 runs the transposed steps: lambda_n = a mu + dt f'(u_n) * (mu -
     // [mass] mean mu), mu = A^{-1} lambda_{n+1}, with u_n read from
@@ -120,7 +123,13 @@ fine_field_kernel(FineArgs args) {
     const int field = blockIdx.x / P;
     const size_t NN = size_t(N) * N;
     long long fin, fout;
-    {
+    int nsteps = args.steps;
+    if (args.work) {
+        const int4 w = args.work[field];
+        fin = w.x;
+        fout = w.y;
+        nsteps = w.z;
+    } else {
         const int g = field / args.per_group, i = field % args.per_group;
         const long long pg = args.map ? args.map[g] : g;
         fin = pg * args.in_gs + args.in_off + i;
@@ -190,7 +199,7 @@ fine_field_kernel(FineArgs args) {
     // column FFTs through bufX, the column-0 split through bufC; each buffer's
     // previous readers are separated from its next writers by a block or
     // cluster barrier, so only the barrier after each exchange write remains.
-    for (int step = 0; step < args.steps; ++step) {
+    for (int step = 0; step < nsteps; ++step) {
         if (!args.adjoint) {
             // pointwise right-hand side on both rows of the line
 #pragma unroll
@@ -319,7 +328,7 @@ fine_field_kernel(FineArgs args) {
         line_fft<T, N, A, B, +1, false>(x, tw, myX, j);
         if (args.adjoint) {
             // lambda_n = a mu + dt f'(u_n) (mu - mean mu), rows r0 (real) and r1 (imag)
-            const int n_state = args.steps - 1 - step;
+            const int n_state = nsteps - 1 - step;
             const T* un = static_cast<const T*>(args.states) + (size_t(n_state) * args.num_fields + field) * NN +
                           size_t(rank * R + line) * N;
             const T mbar = args.mass ? T(part[1]) : T(0);
@@ -462,6 +471,8 @@ static bool fine_built(int n, int precision) {
     return is_pow2(n) && n <= 1024 && pick_variant(n, precision, &count) != nullptr && count > 0;
 }
 
+bool fine_supported_internal(int n, int precision) { return is_pow2(n) && fine_built(n, precision); }
+
 static int check_params(const ac_params* p) {
     ACPR_CHECK_ARG(p != nullptr, "ac_params is NULL");
     ACPR_CHECK_ARG(p->precision == AC_F32 || p->precision == AC_F64, "bad precision %d", p->precision);
@@ -487,7 +498,7 @@ int fine_run(const ac_params* p, int groups, int per_group, int steps, const voi
     ACPR_CHECK_ARG((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % 16 == 0,
                    "field pointers must be 16-byte aligned");
     ACPR_CHECK_ARG((long long)groups * per_group < (1LL << 30), "too many fields");
-    FineArgs a;
+    FineArgs a{};
     a.in = in;
     a.out = out;
     a.num_fields = groups * per_group;
@@ -498,6 +509,7 @@ int fine_run(const ac_params* p, int groups, int per_group, int steps, const voi
     a.out_gs = out_gs;
     a.out_off = out_off;
     a.map = map;
+    a.work = nullptr;
     a.adjoint = adjoint;
     a.states = states;
     a.traj = traj;
@@ -515,6 +527,29 @@ int fine_propagate_mapped(const ac_params* p, int groups, int per_group, int ste
                           long long out_off, const int* map, cudaStream_t stream) {
     return fine_run(p, groups, per_group, steps, in, in_gs, in_off, out, out_gs, out_off, map, 0, nullptr,
                     nullptr, stream);
+}
+
+// Work-list launch: `count` fields, field f = (in field, out field, steps)
+// from the device array work[f] (int4 x, y, z).
+int fine_run_work(const ac_params* p, int count, const int4* work, const void* in, void* out, cudaStream_t stream) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    ACPR_CHECK_ARG(count >= 0 && (count == 0 || (work && in && out)), "bad work list");
+    if (!count) return AC_OK;
+    FineArgs a{};
+    a.in = in;
+    a.out = out;
+    a.num_fields = count;
+    a.steps = 0;
+    a.per_group = count;
+    a.work = work;
+    a.mass = p->variant == AC_MASS_CONSERVING;
+    a.a = 1.0 + p->S * p->dt;
+    a.dt = p->dt;
+    const double h = p->length / p->n;
+    a.lam_scale = p->dt * p->eps * p->eps * 4.0 / (h * h);
+    if (p->precision == AC_F64) return dispatch_fine<double>(p->n, a, stream);
+    return dispatch_fine<float>(p->n, a, stream);
 }
 
 int fine_propagate(const ac_params* p, int num_fields, int steps, const void* in, void* out,

@@ -15,7 +15,10 @@
 // The frozen prefix Ub[0..k-2] already equals Ua[0..k-2] (both hold the exact
 // fine values), so step 2 copies one slice only.  The summation order
 // F + (G_new - G_old) keeps U^k_k bitwise equal to the fine result.
+#include <algorithm>
+#include <map>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "cnn.cuh"
@@ -26,6 +29,8 @@ namespace acpr {
 int fine_propagate_mapped(const ac_params* p, int groups, int per_group, int steps, const void* in,
                           long long in_gs, long long in_off, void* out, long long out_gs,
                           long long out_off, const int* map, cudaStream_t stream);
+int fine_run_work(const ac_params* p, int count, const int4* work, const void* in, void* out, cudaStream_t stream);
+bool fine_supported_internal(int n, int precision);
 
 // ------------------------------------------------------------- kernels ----
 constexpr int kResThreads = 256;
@@ -109,6 +114,21 @@ __global__ void correct_kernel(T* __restrict__ Ub, T* __restrict__ Gold, const T
         const T gn = g ? g[(long long)b * nn + i] : gold;
         Ub[(p * (s + 1) + slice + 1) * nn + i] = Fres[(p * s + slice) * nn + i] + (gn - gold);
         if (g) *go = gn;
+    }
+}
+
+// dst field (map[b] * dst_ps + dst_slice) = src field (map[b] * src_ps + src_slice)
+template <typename T>
+__global__ void copy_slice_kernel(T* __restrict__ dst, const T* __restrict__ src, int dst_slice, int src_slice,
+                                  long long dst_ps, long long src_ps, long long nn, int batch,
+                                  const int* __restrict__ map) {
+    const long long total = nn * batch;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int b = int(idx / nn);
+        const long long i = idx % nn;
+        const long long p = map ? map[b] : b;
+        dst[(p * dst_ps + dst_slice) * nn + i] = src[(p * src_ps + src_slice) * nn + i];
     }
 }
 
@@ -233,10 +253,23 @@ int residual_noalloc(int num_slices, int n, int precision, const void* U_new, co
 }  // namespace acpr
 
 // ---------------------------------------------------------------- driver ---
+// Problems of one handle share ac_params and the coarse net; each has its own
+// slice count s_p and steps per slice c_p.  Arrays are laid out with the
+// largest slice count s; slices past s_p are never written and stay zero in
+// both trajectories, so the increments over slices 1..s are those over 1..s_p.
+// Active problems are kept in order of decreasing s_p, so the problems still
+// sweeping at slice n are a prefix of that list.
+struct GraphKey {
+    int k;
+    std::vector<int> active;
+    bool operator<(const GraphKey& o) const { return k != o.k ? k < o.k : active < o.active; }
+};
+
 struct ac_parareal {
     ac_params p;
     cnn_desc g;
-    int problems = 0, s = 0, c = 0;
+    int problems = 0, s = 0;
+    std::vector<int> sp, cp;    // per-problem slices and steps per slice
     size_t esz = 0;
     long long nn = 0;
     void* Ua = nullptr;
@@ -246,16 +279,24 @@ struct ac_parareal {
     void* gtmp = nullptr;   // [problems][nn] coarse output of one sweep step
     void* work = nullptr;   // conv activations
     void* packed = nullptr; // bf16 weights
-    int* d_map = nullptr;   // active problem indices
+    int* d_map = nullptr;   // active problems, decreasing s_p
     int* h_map = nullptr;   // pinned
+    int4* d_fw = nullptr;   // fine work list
+    int4* h_fw = nullptr;   // pinned
     double* d_part = nullptr;
     double* d_res = nullptr;
     double* h_res = nullptr;  // pinned [problems][4]
     std::vector<char> active;
     std::vector<char> synced;  // inactive problem whose trajectory is in both buffers
     int k_next = 0;
+    int m_launched = 0;        // active count of the iteration in flight
+    cudaStream_t stream_launched = nullptr;
     bool timing = false;
+    bool graphs = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t done = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream the graphs are captured on
+    std::map<GraphKey, cudaGraphExec_t> graph_cache;
     ac_parareal_stats stats{};
 };
 
@@ -264,34 +305,30 @@ namespace acpr {
 static void free_state(ac_parareal* st) {
     if (!st) return;
     for (void* ptr : {st->Ua, st->Ub, st->Gold, st->Fres, st->gtmp, st->work, st->packed,
-                      static_cast<void*>(st->d_map), static_cast<void*>(st->d_part), static_cast<void*>(st->d_res)})
+                      static_cast<void*>(st->d_map), static_cast<void*>(st->d_fw), static_cast<void*>(st->d_part),
+                      static_cast<void*>(st->d_res)})
         if (ptr) cudaFree(ptr);
     if (st->h_map) cudaFreeHost(st->h_map);
+    if (st->h_fw) cudaFreeHost(st->h_fw);
     if (st->h_res) cudaFreeHost(st->h_res);
     for (cudaEvent_t e : st->ev)
         if (e) cudaEventDestroy(e);
+    if (st->done) cudaEventDestroy(st->done);
+    for (auto& kv : st->graph_cache) cudaGraphExecDestroy(kv.second);
+    if (st->cap_stream) cudaStreamDestroy(st->cap_stream);
     delete st;
 }
 
-// Upload the active-problem list; returns the count.
-static int upload_map(ac_parareal* st, cudaStream_t stream, int* count) {
-    int m = 0;
-    for (int p = 0; p < st->problems; ++p)
-        if (st->active[p]) st->h_map[m++] = p;
-    *count = m;
-    if (m) ACPR_CUDA(cudaMemcpyAsync(st->d_map, st->h_map, sizeof(int) * m, cudaMemcpyHostToDevice, stream));
-    return AC_OK;
+static unsigned grid_for(long long total, int threads) {
+    const long long want = (total + threads - 1) / threads;
+    return unsigned(want < 152 * 16 ? want : 152 * 16);
 }
 
 template <typename T>
 static int launch_correct(ac_parareal* st, void* Ub, int slice, const void* g, int m, cudaStream_t stream) {
-    const long long total = st->nn * m;
-    const int threads = 256;
-    const long long want = (total + threads - 1) / threads;
-    const unsigned blocks = unsigned(want < 152 * 16 ? want : 152 * 16);
-    correct_kernel<T><<<blocks, threads, 0, stream>>>(static_cast<T*>(Ub), static_cast<T*>(st->Gold),
-                                                      static_cast<const T*>(st->Fres), static_cast<const T*>(g),
-                                                      slice, st->s, st->nn, m, st->d_map);
+    correct_kernel<T><<<grid_for(st->nn * m, 256), 256, 0, stream>>>(
+        static_cast<T*>(Ub), static_cast<T*>(st->Gold), static_cast<const T*>(st->Fres), static_cast<const T*>(g),
+        slice, st->s, st->nn, m, st->d_map);
     ACPR_LAUNCH_CHECK();
     return AC_OK;
 }
@@ -301,109 +338,184 @@ static int correct(ac_parareal* st, void* Ub, int slice, const void* g, int m, c
     return launch_correct<float>(st, Ub, slice, g, m, stream);
 }
 
-static int iterate(ac_parareal* st, int* k_inout, double* l2_out, double* mx_out, cudaStream_t stream) {
-    const int k = *k_inout;
-    ACPR_CHECK_ARG(k == st->k_next, "iteration %d requested, state is at %d", k, st->k_next);
-    ACPR_CHECK_ARG(k <= st->s, "k = %d exceeds the slice count %d", k, st->s);
+static int copy_slice(ac_parareal* st, void* dst, const void* src, int dst_slice, int src_slice, long long dst_ps,
+                      long long src_ps, int m, cudaStream_t stream) {
+    if (st->p.precision == AC_F64)
+        copy_slice_kernel<double><<<grid_for(st->nn * m, 256), 256, 0, stream>>>(
+            static_cast<double*>(dst), static_cast<const double*>(src), dst_slice, src_slice, dst_ps, src_ps, st->nn,
+            m, st->d_map);
+    else
+        copy_slice_kernel<float><<<grid_for(st->nn * m, 256), 256, 0, stream>>>(
+            static_cast<float*>(dst), static_cast<const float*>(src), dst_slice, src_slice, dst_ps, src_ps, st->nn, m,
+            st->d_map);
+    ACPR_LAUNCH_CHECK();
+    return AC_OK;
+}
+
+// Number of active problems (a prefix of h_map) whose slice count exceeds n.
+static int sweeping(const ac_parareal* st, int m, int n) {
+    int c = 0;
+    while (c < m && st->sp[st->h_map[c]] > n) ++c;
+    return c;
+}
+
+// Host-side lists of iteration k: the active problems (decreasing s_p) and
+// the fine work items (decreasing steps, the longest first).  Returns m.
+static int build_lists(ac_parareal* st, int k, int* nwork) {
+    std::vector<int> act;
+    for (int p = 0; p < st->problems; ++p)
+        if (st->active[p]) act.push_back(p);
+    std::stable_sort(act.begin(), act.end(), [&](int a, int b) { return st->sp[a] > st->sp[b]; });
+    for (size_t i = 0; i < act.size(); ++i) st->h_map[i] = act[i];
+    int w = 0;
+    if (k >= 1) {
+        std::vector<int> byc(act);
+        std::stable_sort(byc.begin(), byc.end(), [&](int a, int b) { return st->cp[a] > st->cp[b]; });
+        for (int p : byc)
+            for (int n = k - 1; n < st->sp[p]; ++n)
+                st->h_fw[w++] = make_int4(p * (st->s + 1) + n, p * st->s + n, st->cp[p], 0);
+    }
+    *nwork = w;
+    return int(act.size());
+}
+
+// All device work of iteration k (what a graph captures).
+static int enqueue(ac_parareal* st, int k, int m, int nwork, cudaStream_t stream) {
     const long long nn = st->nn;
     const int s = st->s;
-    const size_t fb = st->esz * nn;  // bytes per field
-    int m = 0;
-    int rc = upload_map(st, stream, &m);
-    if (rc) return rc;
+    const size_t fb = st->esz * nn;
     const bool tm = st->timing;
+    int rc;
     auto mark = [&](int i) -> int {
         if (tm) ACPR_CUDA(cudaEventRecord(st->ev[i], stream));
         return AC_OK;
     };
     if (k == 0) {
-        // U^0_0 = u0 (already in Ua[0]); sequential coarse sweep
+        // U^0_0 = u0 (already in Ua[0]); sequential coarse sweep U^0_{n+1} = G(U^0_n)
         if ((rc = mark(1))) return rc;
         for (int n = 0; n < s; ++n) {
-            rc = coarse_step_mapped(&st->g, st->p.n, m, static_cast<char*>(st->Ua) + n * fb, nn * (s + 1),
-                                    st->d_map, static_cast<char*>(st->Gold) + n * fb, nn * s, st->d_map,
-                                    stream);
+            const int mn = sweeping(st, m, n);
+            if (!mn) break;
+            rc = coarse_step_mapped(&st->g, st->p.n, mn, static_cast<char*>(st->Ua) + n * fb, nn * (s + 1),
+                                    st->d_map, static_cast<char*>(st->Gold) + n * fb, nn * s, st->d_map, stream);
             if (rc) return rc;
-            for (int i = 0; i < m; ++i) {
-                const int p = st->h_map[i];
-                ACPR_CUDA(cudaMemcpyAsync(static_cast<char*>(st->Ua) + (size_t(p) * (s + 1) + n + 1) * fb,
-                                          static_cast<char*>(st->Gold) + (size_t(p) * s + n) * fb, fb,
-                                          cudaMemcpyDeviceToDevice, stream));
-            }
-            st->stats.coarse_calls += 1;
-            st->stats.coarse_cells += (long long)m * nn;
+            if ((rc = copy_slice(st, st->Ua, st->Gold, n + 1, n, s + 1, s, mn, stream))) return rc;
         }
-        if ((rc = mark(2))) return rc;
-        if (tm) {
-            float ms = 0.f;
-            ACPR_CUDA(cudaEventSynchronize(st->ev[2]));
-            ACPR_CUDA(cudaEventElapsedTime(&ms, st->ev[1], st->ev[2]));
-            st->stats.coarse_ms += ms;
-        }
-        st->k_next = 1;
-        *k_inout = 1;
-        return AC_OK;
+        return mark(2);
     }
-    // an inactive problem keeps its last trajectory in both buffers, so that
-    // the buffer swap below never exposes a stale one
-    for (int p = 0; p < st->problems; ++p) {
-        if (st->active[p] || st->synced[p]) continue;
-        ACPR_CUDA(cudaMemcpyAsync(static_cast<char*>(st->Ub) + size_t(p) * (s + 1) * fb,
-                                  static_cast<char*>(st->Ua) + size_t(p) * (s + 1) * fb, fb * (s + 1),
-                                  cudaMemcpyDeviceToDevice, stream));
-        st->synced[p] = 1;
-    }
-    if (m == 0) {
-        std::swap(st->Ua, st->Ub);
-        st->k_next = k + 1;
-        *k_inout = k + 1;
-        return AC_OK;
-    }
-    // 1. fine solves of slices k-1 .. s-1 of every active problem (one launch)
+    // 1. fine solves of slices k-1 .. s_p-1 of every active problem (one launch)
     if ((rc = mark(0))) return rc;
-    rc = fine_propagate_mapped(&st->p, m, s - k + 1, st->c, st->Ua, s + 1, k - 1, st->Fres, s, k - 1,
-                               st->d_map, stream);
+    rc = fine_run_work(&st->p, nwork, st->d_fw, st->Ua, st->Fres, stream);
     if (rc) return rc;
-    st->stats.fine_launches += 1;
-    st->stats.fine_cell_steps += (long long)m * (s - k + 1) * st->c * nn;
     if ((rc = mark(1))) return rc;
     // 2. newest frozen slice and the exact slice k
-    for (int i = 0; i < m; ++i) {
-        const int p = st->h_map[i];
-        ACPR_CUDA(cudaMemcpyAsync(static_cast<char*>(st->Ub) + (size_t(p) * (s + 1) + k - 1) * fb,
-                                  static_cast<char*>(st->Ua) + (size_t(p) * (s + 1) + k - 1) * fb, fb,
-                                  cudaMemcpyDeviceToDevice, stream));
-    }
-    rc = correct(st, st->Ub, k - 1, nullptr, m, stream);
-    if (rc) return rc;
+    if ((rc = copy_slice(st, st->Ub, st->Ua, k - 1, k - 1, s + 1, s + 1, m, stream))) return rc;
+    if ((rc = correct(st, st->Ub, k - 1, nullptr, m, stream))) return rc;
     // 3. sequential correction sweep
     for (int n = k; n < s; ++n) {
-        rc = coarse_step_mapped(&st->g, st->p.n, m, static_cast<char*>(st->Ub) + n * fb, nn * (s + 1),
-                                st->d_map, st->gtmp, nn, nullptr, stream);
+        const int mn = sweeping(st, m, n);
+        if (!mn) break;
+        rc = coarse_step_mapped(&st->g, st->p.n, mn, static_cast<char*>(st->Ub) + n * fb, nn * (s + 1), st->d_map,
+                                st->gtmp, nn, nullptr, stream);
         if (rc) return rc;
-        rc = correct(st, st->Ub, n, st->gtmp, m, stream);
-        if (rc) return rc;
-        st->stats.coarse_calls += 1;
-        st->stats.coarse_cells += (long long)m * nn;
+        if ((rc = correct(st, st->Ub, n, st->gtmp, mn, stream))) return rc;
     }
     if ((rc = mark(2))) return rc;
     // 4. increments over slices 1..s
     rc = increment(st->p.precision, st->Ub, st->Ua, nn * (s + 1), nn * (s + 1), nn, nn * s, st->d_map, m,
                    st->d_part, st->d_res, stream);
     if (rc) return rc;
-    if ((rc = mark(3))) return rc;
-    ACPR_CUDA(cudaMemcpyAsync(st->h_res, st->d_res, sizeof(double) * 4 * m, cudaMemcpyDeviceToHost, stream));
-    ACPR_CUDA(cudaStreamSynchronize(stream));
-    st->stats.iterations += 1;
-    if (tm) {
+    return mark(3);
+}
+
+static void account(ac_parareal* st, int k, int m, int nwork) {
+    if (k >= 1) {
+        st->stats.fine_launches += 1;
+        for (int i = 0; i < nwork; ++i) st->stats.fine_cell_steps += (long long)st->h_fw[i].z * st->nn;
+    }
+    for (int n = k; n < st->s; ++n) {
+        const int mn = sweeping(st, m, n);
+        if (!mn) break;
+        st->stats.coarse_calls += 1;
+        st->stats.coarse_cells += (long long)mn * st->nn;
+    }
+}
+
+// Launch iteration k (asynchronous); finish() completes it.
+static int launch(ac_parareal* st, int k, cudaStream_t stream) {
+    ACPR_CHECK_ARG(k == st->k_next, "iteration %d requested, state is at %d", k, st->k_next);
+    ACPR_CHECK_ARG(k <= st->s, "k = %d exceeds the slice count %d", k, st->s);
+    const size_t fb = st->esz * st->nn;
+    int nwork = 0;
+    const int m = build_lists(st, k, &nwork);
+    st->m_launched = m;
+    st->stream_launched = stream;
+    if (k >= 1) {
+        // an inactive problem keeps its last trajectory in both buffers, so
+        // that the buffer swap never exposes a stale one
+        for (int p = 0; p < st->problems; ++p) {
+            if (st->active[p] || st->synced[p]) continue;
+            ACPR_CUDA(cudaMemcpyAsync(static_cast<char*>(st->Ub) + size_t(p) * (st->s + 1) * fb,
+                                      static_cast<char*>(st->Ua) + size_t(p) * (st->s + 1) * fb, fb * (st->s + 1),
+                                      cudaMemcpyDeviceToDevice, stream));
+            st->synced[p] = 1;
+        }
+    }
+    if (m == 0) return AC_OK;
+    ACPR_CUDA(cudaMemcpyAsync(st->d_map, st->h_map, sizeof(int) * m, cudaMemcpyHostToDevice, stream));
+    if (nwork) ACPR_CUDA(cudaMemcpyAsync(st->d_fw, st->h_fw, sizeof(int4) * nwork, cudaMemcpyHostToDevice, stream));
+    int rc;
+    if (st->graphs) {
+        GraphKey key{k, std::vector<int>(st->h_map, st->h_map + m)};
+        auto it = st->graph_cache.find(key);
+        if (it == st->graph_cache.end()) {
+            // capture on a private stream (the caller's may be the legacy
+            // default stream, which cannot be captured); nothing runs here
+            if (!st->cap_stream) ACPR_CUDA(cudaStreamCreateWithFlags(&st->cap_stream, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            ACPR_CUDA(cudaStreamBeginCapture(st->cap_stream, cudaStreamCaptureModeRelaxed));
+            rc = enqueue(st, k, m, nwork, st->cap_stream);
+            cudaError_t ec = cudaStreamEndCapture(st->cap_stream, &graph);
+            if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+            ACPR_CUDA(ec);
+            cudaGraphExec_t exec = nullptr;
+            cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            ACPR_CUDA(ei);
+            it = st->graph_cache.emplace(key, exec).first;
+        }
+        ACPR_CUDA(cudaGraphLaunch(it->second, stream));
+    } else {
+        if ((rc = enqueue(st, k, m, nwork, stream))) return rc;
+    }
+    account(st, k, m, nwork);
+    if (k >= 1)
+        ACPR_CUDA(cudaMemcpyAsync(st->h_res, st->d_res, sizeof(double) * 4 * m, cudaMemcpyDeviceToHost, stream));
+    ACPR_CUDA(cudaEventRecord(st->done, stream));
+    return AC_OK;
+}
+
+static int finish(ac_parareal* st, int k, double* l2_out, double* mx_out) {
+    const int m = st->m_launched;
+    if (m) ACPR_CUDA(cudaEventSynchronize(st->done));
+    int rc = tc_check_status(st->stream_launched);
+    if (rc) return rc;
+    if (st->timing && m) {
         float a = 0.f, b = 0.f, c = 0.f;
-        ACPR_CUDA(cudaEventElapsedTime(&a, st->ev[0], st->ev[1]));
-        ACPR_CUDA(cudaEventElapsedTime(&b, st->ev[1], st->ev[2]));
-        ACPR_CUDA(cudaEventElapsedTime(&c, st->ev[2], st->ev[3]));
+        if (k == 0) {
+            ACPR_CUDA(cudaEventElapsedTime(&b, st->ev[1], st->ev[2]));
+        } else {
+            ACPR_CUDA(cudaEventElapsedTime(&a, st->ev[0], st->ev[1]));
+            ACPR_CUDA(cudaEventElapsedTime(&b, st->ev[1], st->ev[2]));
+            ACPR_CUDA(cudaEventElapsedTime(&c, st->ev[2], st->ev[3]));
+        }
         st->stats.fine_ms += a;
         st->stats.coarse_ms += b;
         st->stats.increment_ms += c;
     }
+    st->k_next = k + 1;
+    if (k == 0) return AC_OK;
+    st->stats.iterations += 1;
     bool nonfinite = false;
     for (int i = 0; i < m; ++i) {
         const int p = st->h_map[i];
@@ -412,12 +524,91 @@ static int iterate(ac_parareal* st, int* k_inout, double* l2_out, double* mx_out
         if (!std::isfinite(st->h_res[4 * i]) || !std::isfinite(st->h_res[4 * i + 1])) nonfinite = true;
     }
     std::swap(st->Ua, st->Ub);
-    st->k_next = k + 1;
-    *k_inout = k + 1;
     if (nonfinite) {
         set_error("parareal_iterate: non-finite increment at k = %d", k);
         return AC_ERR_NONFINITE;
     }
+    return AC_OK;
+}
+
+static int iterate(ac_parareal* st, int* k_inout, double* l2_out, double* mx_out, cudaStream_t stream) {
+    const int k = *k_inout;
+    int rc = launch(st, k, stream);
+    if (rc) return rc;
+    rc = finish(st, k, l2_out, mx_out);
+    *k_inout = st->k_next;
+    return rc;
+}
+
+static int create(const ac_params* params, const cnn_desc* coarse, int problems, const int* slices,
+                  const int* steps, const void* u0, ac_parareal** out) {
+    ACPR_CHECK_ARG(out != nullptr, "out is NULL");
+    *out = nullptr;
+    ACPR_CHECK_ARG(params && coarse && u0 && slices && steps, "null argument");
+    ACPR_CHECK_ARG(problems >= 1, "need at least one problem");
+    int smax = 0;
+    for (int p = 0; p < problems; ++p) {
+        ACPR_CHECK_ARG(slices[p] >= 1 && steps[p] >= 0, "problem %d: bad slice count or steps", p);
+        smax = std::max(smax, slices[p]);
+    }
+    ACPR_CHECK_ARG(coarse->precision == params->precision, "coarse and fine precision differ");
+    int rc = check_cnn(coarse);
+    if (rc) return rc;
+    if (!fine_supported_internal(params->n, params->precision)) {
+        set_error("ac_parareal_create: n=%d not supported", params->n);
+        return AC_ERR_UNSUPPORTED;
+    }
+    ac_parareal* st = new ac_parareal();
+    st->p = *params;
+    st->g = *coarse;
+    st->problems = problems;
+    st->s = smax;
+    st->sp.assign(slices, slices + problems);
+    st->cp.assign(steps, steps + problems);
+    st->esz = elem_size(params->precision);
+    st->nn = (long long)params->n * params->n;
+    st->active.assign(problems, 1);
+    st->synced.assign(problems, 0);
+    const size_t fb = st->esz * st->nn;
+    const size_t traj = fb * size_t(problems) * (smax + 1);
+    const size_t slc = fb * size_t(problems) * smax;
+    auto alloc = [&](void** p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
+    bool ok = alloc(&st->Ua, traj) && alloc(&st->Ub, traj) && alloc(&st->Gold, slc) && alloc(&st->Fres, slc) &&
+              alloc(&st->gtmp, fb * problems);
+    const size_t wb = work_bytes_for(coarse, params->n, problems);
+    ok = ok && alloc(&st->work, wb);
+    const size_t pb = cnn_packed_bytes(coarse);
+    if (ok && pb) ok = alloc(&st->packed, pb);
+    ok = ok && alloc(reinterpret_cast<void**>(&st->d_map), sizeof(int) * problems) &&
+         alloc(reinterpret_cast<void**>(&st->d_fw), sizeof(int4) * size_t(problems) * smax) &&
+         alloc(reinterpret_cast<void**>(&st->d_part), sizeof(double) * 3 * kResBlocksPerProblem * problems) &&
+         alloc(reinterpret_cast<void**>(&st->d_res), sizeof(double) * 4 * problems);
+    ok = ok && cudaMallocHost(&st->h_map, sizeof(int) * problems) == cudaSuccess &&
+         cudaMallocHost(&st->h_fw, sizeof(int4) * size_t(problems) * smax) == cudaSuccess &&
+         cudaMallocHost(&st->h_res, sizeof(double) * 4 * problems) == cudaSuccess &&
+         cudaEventCreateWithFlags(&st->done, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_state(st);
+        set_error("ac_parareal_create: device allocation failed");
+        return AC_ERR_NOMEM;
+    }
+    st->g.work = st->work;
+    st->g.work_bytes = wb;
+    st->g.packed = st->packed;
+    if (pb) {
+        rc = cnn_pack_weights(&st->g, nullptr);
+        if (rc) { free_state(st); return rc; }
+    }
+    // zero trajectories (slices past s_p stay zero), then U[p][0] = u0[p]
+    if (cudaMemset(st->Ua, 0, traj) != cudaSuccess || cudaMemset(st->Ub, 0, traj) != cudaSuccess ||
+        cudaMemcpy2D(st->Ua, fb * (smax + 1), u0, fb, fb, problems, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        set_error("ac_parareal_create: initialisation failed: %s", cudaGetErrorString(cudaGetLastError()));
+        free_state(st);
+        return AC_ERR_CUDA;
+    }
+    *out = st;
     return AC_OK;
 }
 
@@ -435,67 +626,18 @@ extern "C" int parareal_residual_noalloc(int num_slices, int n, int precision, c
                                   reinterpret_cast<cudaStream_t>(stream));
 }
 
-extern "C" int ac_parareal_create(const ac_params* params, const cnn_desc* coarse, int problems,
-                                  int num_slices, int steps_per_slice, const void* u0, ac_parareal** out) {
+extern "C" int ac_parareal_create(const ac_params* params, const cnn_desc* coarse, int problems, int num_slices,
+                                  int steps_per_slice, const void* u0, ac_parareal** out) {
     using namespace acpr;
-    ACPR_CHECK_ARG(out != nullptr, "out is NULL");
-    *out = nullptr;
-    ACPR_CHECK_ARG(params && coarse && u0, "null argument");
-    ACPR_CHECK_ARG(problems >= 1 && num_slices >= 1 && steps_per_slice >= 0, "bad counts");
-    ACPR_CHECK_ARG(coarse->precision == params->precision, "coarse and fine precision differ");
-    int rc = check_cnn(coarse);
-    if (rc) return rc;
-    if (!ac_fine_supported(params->n, params->precision)) {
-        set_error("ac_parareal_create: n=%d not supported", params->n);
-        return AC_ERR_UNSUPPORTED;
-    }
-    ac_parareal* st = new ac_parareal();
-    st->p = *params;
-    st->g = *coarse;
-    st->problems = problems;
-    st->s = num_slices;
-    st->c = steps_per_slice;
-    st->esz = elem_size(params->precision);
-    st->nn = (long long)params->n * params->n;
-    st->active.assign(problems, 1);
-    st->synced.assign(problems, 0);
-    const size_t fb = st->esz * st->nn;
-    const size_t traj = fb * size_t(problems) * (num_slices + 1);
-    const size_t slc = fb * size_t(problems) * num_slices;
-    auto alloc = [&](void** p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
-    bool ok = alloc(&st->Ua, traj) && alloc(&st->Ub, traj) && alloc(&st->Gold, slc) && alloc(&st->Fres, slc) &&
-              alloc(&st->gtmp, fb * problems);
-    const size_t wb = work_bytes_for(coarse, params->n, problems);
-    ok = ok && alloc(&st->work, wb);
-    const size_t pb = cnn_packed_bytes(coarse);
-    if (ok && pb) ok = alloc(&st->packed, pb);
-    ok = ok && alloc(reinterpret_cast<void**>(&st->d_map), sizeof(int) * problems) &&
-         alloc(reinterpret_cast<void**>(&st->d_part), sizeof(double) * 3 * kResBlocksPerProblem * problems) &&
-         alloc(reinterpret_cast<void**>(&st->d_res), sizeof(double) * 4 * problems);
-    ok = ok && cudaMallocHost(&st->h_map, sizeof(int) * problems) == cudaSuccess &&
-         cudaMallocHost(&st->h_res, sizeof(double) * 4 * problems) == cudaSuccess;
-    if (!ok) {
-        cudaGetLastError();
-        free_state(st);
-        set_error("ac_parareal_create: device allocation failed");
-        return AC_ERR_NOMEM;
-    }
-    st->g.work = st->work;
-    st->g.work_bytes = wb;
-    st->g.packed = st->packed;
-    if (pb) {
-        rc = cnn_pack_weights(&st->g, nullptr);
-        if (rc) { free_state(st); return rc; }
-    }
-    // U0[p][0] = u0[p]
-    if (cudaMemcpy2D(st->Ua, fb * (num_slices + 1), u0, fb, fb, problems, cudaMemcpyDeviceToDevice) != cudaSuccess ||
-        cudaDeviceSynchronize() != cudaSuccess) {
-        set_error("ac_parareal_create: copy of u0 failed: %s", cudaGetErrorString(cudaGetLastError()));
-        free_state(st);
-        return AC_ERR_CUDA;
-    }
-    *out = st;
-    return AC_OK;
+    ACPR_CHECK_ARG(problems >= 1 && problems < (1 << 24), "bad problem count");
+    std::vector<int> sl(problems, num_slices), st(problems, steps_per_slice);
+    return create(params, coarse, problems, sl.data(), st.data(), u0, out);
+}
+
+extern "C" int ac_parareal_create_uneven(const ac_params* params, const cnn_desc* coarse, int problems,
+                                         const int* num_slices, const int* steps_per_slice, const void* u0,
+                                         ac_parareal** out) {
+    return acpr::create(params, coarse, problems, num_slices, steps_per_slice, u0, out);
 }
 
 extern "C" int parareal_iterate(ac_parareal* state, int* k_inout, double* rel_l2_out, double* max_abs_out,
@@ -525,48 +667,92 @@ extern "C" int ac_parareal_copy_trajectory(const ac_parareal* state, void* dst, 
     return AC_OK;
 }
 
+// Iterations of several handles at once: each iteration is launched on every
+// handle's stream before any is waited for, so different grid sizes overlap.
+static int solve_many(ac_parareal* const* states, int count, const cudaStream_t* streams, double tol, int kmax,
+                      int* iters_out, double* rel_l2_out) {
+    using namespace acpr;
+    std::vector<std::vector<double>> l2(count), mx(count);
+    std::vector<int> base(count, 0);
+    int total = 0;
+    for (int h = 0; h < count; ++h) {
+        ACPR_CHECK_ARG(states[h], "null state %d", h);
+        base[h] = total;
+        total += states[h]->problems;
+        l2[h].assign(states[h]->problems, 0.0);
+        mx[h].assign(states[h]->problems, 0.0);
+    }
+    for (int i = 0; i < total; ++i) { iters_out[i] = 0; rel_l2_out[i] = 0.0; }
+    int rc;
+    for (int h = 0; h < count; ++h)
+        if (states[h]->k_next == 0 && (rc = launch(states[h], 0, streams[h]))) return rc;
+    for (int h = 0; h < count; ++h)
+        if (states[h]->k_next == 0 && (rc = finish(states[h], 0, nullptr, nullptr))) return rc;
+    std::vector<char> busy(count, 1);
+    bool any = true, saw_nonfinite = false;
+    while (any) {
+        any = false;
+        std::vector<int> kk(count, -1);
+        for (int h = 0; h < count; ++h) {
+            ac_parareal* st = states[h];
+            const int klim = std::min(kmax, st->s);
+            bool act = false;
+            for (int p = 0; p < st->problems; ++p) act = act || st->active[p];
+            if (!busy[h] || !act || st->k_next > klim) { busy[h] = 0; continue; }
+            kk[h] = st->k_next;
+            if ((rc = launch(st, kk[h], streams[h]))) return rc;
+        }
+        for (int h = 0; h < count; ++h) {
+            if (kk[h] < 0) continue;
+            ac_parareal* st = states[h];
+            rc = finish(st, kk[h], l2[h].data(), mx[h].data());
+            if (rc == AC_ERR_NONFINITE) saw_nonfinite = true;
+            else if (rc) return rc;
+            for (int p = 0; p < st->problems; ++p) {
+                if (!st->active[p]) continue;
+                iters_out[base[h] + p] = kk[h];
+                rel_l2_out[base[h] + p] = l2[h][p];
+                // converged on the tolerance, or exact because k reached s_p
+                if (l2[h][p] < tol || kk[h] >= st->sp[p]) st->active[p] = 0;
+                else any = true;
+            }
+        }
+        bool left = false;
+        for (int h = 0; h < count; ++h) {
+            if (kk[h] < 0) continue;
+            const int klim = std::min(kmax, states[h]->s);
+            for (int p = 0; p < states[h]->problems; ++p)
+                if (states[h]->active[p] && states[h]->k_next <= klim) left = true;
+        }
+        any = left;
+    }
+    for (int h = 0; h < count; ++h)
+        for (int p = 0; p < states[h]->problems; ++p)
+            if (states[h]->active[p]) {
+                set_error("ac_parareal_solve: not converged within kmax = %d%s", kmax,
+                          saw_nonfinite ? " (non-finite increments met)" : "");
+                return AC_ERR_NOT_CONVERGED;
+            }
+    return AC_OK;
+}
+
 extern "C" int ac_parareal_solve(ac_parareal* state, double tol, int kmax, int* iters_out, double* rel_l2_out,
                                  acpr_stream stream) {
     using namespace acpr;
     ACPR_CHECK_ARG(state && iters_out && rel_l2_out, "null argument");
     ACPR_CHECK_ARG(kmax >= 1, "kmax must be >= 1");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const int P = state->problems;
-    std::vector<double> l2(P, 0.0), mx(P, 0.0);
-    for (int p = 0; p < P; ++p) { iters_out[p] = 0; rel_l2_out[p] = 0.0; }
-    int k = state->k_next;
-    int rc = AC_OK;
-    if (k == 0) {
-        rc = iterate(state, &k, nullptr, nullptr, st);
-        if (rc) return rc;
-    }
-    const int klim = kmax < state->s ? kmax : state->s;
-    bool any = true;
-    bool saw_nonfinite = false;
-    while (k <= klim && any) {
-        const int kk = k;
-        rc = iterate(state, &k, l2.data(), mx.data(), st);
-        // A non-finite increment means a diverging iterate beyond the exact
-        // prefix; slices <= k stay fine-solver values, so keep iterating: the
-        // loop still ends with the exact trajectory at k = s.
-        if (rc == AC_ERR_NONFINITE) saw_nonfinite = true;
-        else if (rc) return rc;
-        any = false;
-        for (int p = 0; p < P; ++p) {
-            if (!state->active[p]) continue;
-            iters_out[p] = kk;
-            rel_l2_out[p] = l2[p];
-            // converged on the tolerance, or exact because k reached s
-            if (l2[p] < tol || kk == state->s) state->active[p] = 0;
-            else any = true;
-        }
-    }
-    if (any) {
-        set_error("ac_parareal_solve: not converged within kmax = %d%s", kmax,
-                  saw_nonfinite ? " (non-finite increments met)" : "");
-        return AC_ERR_NOT_CONVERGED;
-    }
-    return AC_OK;
+    return solve_many(&state, 1, &st, tol, kmax, iters_out, rel_l2_out);
+}
+
+extern "C" int ac_parareal_solve_many(ac_parareal* const* states, int count, const acpr_stream* streams, double tol,
+                                      int kmax, int* iters_out, double* rel_l2_out) {
+    using namespace acpr;
+    ACPR_CHECK_ARG(states && streams && iters_out && rel_l2_out && count >= 1, "null argument");
+    ACPR_CHECK_ARG(kmax >= 1, "kmax must be >= 1");
+    std::vector<cudaStream_t> sv(count);
+    for (int h = 0; h < count; ++h) sv[h] = reinterpret_cast<cudaStream_t>(streams[h]);
+    return solve_many(states, count, sv.data(), tol, kmax, iters_out, rel_l2_out);
 }
 
 extern "C" int ac_parareal_reset(ac_parareal* state, const void* u0, acpr_stream stream) {
@@ -586,7 +772,18 @@ extern "C" int ac_parareal_enable_timing(ac_parareal* state, int on) {
     ACPR_CHECK_ARG(state, "null state");
     if (on && !state->ev[0])
         for (cudaEvent_t& e : state->ev) ACPR_CUDA(cudaEventCreate(&e));
+    if (bool(on) != state->timing) {
+        for (auto& kv : state->graph_cache) cudaGraphExecDestroy(kv.second);
+        state->graph_cache.clear();  // captured graphs hold (or lack) the timing events
+    }
     state->timing = on != 0;
+    return AC_OK;
+}
+
+extern "C" int ac_parareal_enable_graphs(ac_parareal* state, int on) {
+    using namespace acpr;
+    ACPR_CHECK_ARG(state, "null state");
+    state->graphs = on != 0;
     return AC_OK;
 }
 
