@@ -155,6 +155,82 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def run_uneven(args):
+    """64 independent classic problems of uneven grid (128/256/512), slice count
+    (16..64) and steps per slice (50..400), eps = 2.5 h: one handle per grid
+    size, all solved together on three streams, each iteration a CUDA graph.
+    Prints one JSON line (not the benchmark line)."""
+    import torch
+    import paper_2510_07672_gb300 as G
+    probs = I.uneven_problems()
+    classes = sorted({p["n"] for p in probs})
+    Wc = I.cnn_weights(6, 32, seed=0)
+    net = G.CoarseNet(6, 32, Wc[0].astype(np.float32), Wc[1].astype(np.float32), act=1, precision=G.AC_F32)
+    handles, streams, groups = [], [], []
+    for n in classes:
+        grp = [p for p in probs if p["n"] == n]
+        fp = G.FineParams(n, 2.5 / n, 2.0, 5e-5, variant=G.AC_CLASSIC, precision=G.AC_F32)
+        u0 = torch.tensor(np.stack([I.random_field(n, seed=p["seed"]) for p in grp]), dtype=torch.float32,
+                          device="cuda")
+        h = G.Parareal(fp, net, u0, [p["slices"] for p in grp], [p["steps"] for p in grp])
+        h.enable_graphs(not args.no_graphs)
+        h.enable_timing(True)
+        handles.append(h)
+        streams.append(torch.cuda.Stream())
+        groups.append((fp, grp, u0))
+
+    def solve():
+        for h, (fp, grp, u0) in zip(handles, groups):
+            h.reset(u0)
+        return G.parareal_solve_many(handles, streams, tol=1e-6, kmax=64)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        out = solve()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    cells = sum(p["slices"] * p["steps"] * p["n"] ** 2 for p in probs)
+    # sequential fine solves of the same problems: per grid size and slice j, one
+    # work-list launch advancing every problem with s_p > j by its c_p steps
+    seqs = []
+    for fp, grp, u0 in groups:
+        S = max(p["slices"] for p in grp)
+        traj = torch.zeros((len(grp), S + 1, fp.n, fp.n), dtype=torch.float32, device="cuda")
+        traj[:, 0] = u0
+        works = []
+        for j in range(S):
+            items = sorted(([i * (S + 1) + j, i * (S + 1) + j + 1, p["steps"], 0] for i, p in enumerate(grp)
+                            if p["slices"] > j), key=lambda w: -w[2])
+            works.append(torch.tensor(items, dtype=torch.int32, device="cuda"))
+        seqs.append((fp, traj, works))
+
+    def sequential():
+        for (fp, traj, works), st in zip(seqs, streams):
+            with torch.cuda.stream(st):
+                for w in works:
+                    G.ac_fine_propagate_work(fp, w, traj, traj, stream=st)
+
+    sequential()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sequential()
+    torch.cuda.synchronize()
+    seq_ms = (time.perf_counter() - t0) * 1e3
+    its = [i for o in out for i in o[0]]
+    st = [h.stats() for h in handles]
+    fine_ms = sum(x["fine_ms"] for x in st) / (args.steps + args.warmup)
+    print(json.dumps({
+        "metric": METRIC, "workload": "uneven-64-classic-f32", "value": cells / (ms * 1e-3), "unit": UNIT,
+        "ms_per_solve": ms, "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / ms,
+        "iterations_mean": float(np.mean(its)), "problems": len(probs),
+        "grid_classes": {str(n): sum(1 for p in probs if p["n"] == n) for n in classes},
+        "fine_ms_per_solve_summed_over_streams": fine_ms, "steps": args.steps, "warmup": args.warmup,
+        "coarse_weights": "untrained N(0, 0.01^2)", "cuda_graphs": not args.no_graphs}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -163,6 +239,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--weights", default="trained", help="'trained' (the committed G), 'untrained', or a .npz path")
+    ap.add_argument("--workload", default="mass256", choices=["mass256", "uneven"],
+                    help="mass256: the benchmark line; uneven: 64 classic problems of uneven size (batching)")
+    ap.add_argument("--no-graphs", action="store_true")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -170,6 +249,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "uneven":
+        run_uneven(args)
         return
 
     # host-side oracle sample first (before any GPU work in this process)
@@ -205,6 +287,7 @@ def main():
     u0 = torch.tensor(ics, device=dev)
     pr = G.Parareal(fp, net, u0, WL.slices, WL.steps)
     pr.enable_timing(True)
+    pr.enable_graphs(not args.no_graphs)
     stream = torch.cuda.current_stream()
 
     def solve():
@@ -304,7 +387,7 @@ def main():
                        "steps_per_slice": WL.steps, "variant": "mass-conserving", "conv": "1-32x6-1 gelu bf16, mACNN mass shift",
                        "tol": WL.tol, "coarse_weights": wsrc,
                        "l2": "state larger than L2 (trajectories, stored G and F values: 0.54 GB)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "cuda_graphs": not args.no_graphs},
             "iterations": its, "final_rel_l2": l2,
             "sequential_ms": seq_ms, "parareal_ms": ms,
             "speedup_vs_sequential": seq_ms / ms,

@@ -134,6 +134,15 @@ int ac_fine_step(const ac_params* params, int batch, const void* u_in, void* u_o
 int ac_fine_propagate_slices(const ac_params* params, int num_fields, int steps_per_slice,
                              const void* u_starts, void* u_ends, acpr_stream stream);
 
+/* Fine propagation of a work list: item i (device int32[count][4], 16-byte
+ * aligned) = {in field, out field, steps, unused} advances field `in field`
+ * of u_in by `steps` fine steps into field `out field` of u_out (fields of
+ * n*n values counted from the base pointers).  Items run in parallel, the
+ * first ones first: list long items first.  u_in and u_out may be the same
+ * buffer when no item's output is another item's input. */
+int ac_fine_propagate_work(const ac_params* params, int count, const void* work, const void* u_in,
+                           void* u_out, acpr_stream stream);
+
 /* The fine steps of ac_fine_propagate_slices, also storing every state:
  * traj[s][f] = u^s of field f for s = 0..steps (device [steps+1][num_fields]
  * [n][n]); u0: device [num_fields][n][n]. */

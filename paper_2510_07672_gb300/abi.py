@@ -54,7 +54,7 @@ EXPORTS = ["ac_last_error", "ac_fine_supported", "ac_fine_step", "ac_fine_propag
            "ac_parareal_solve_many", "ac_parareal_reset", "ac_parareal_enable_timing",
            "ac_parareal_get_stats", "ac_parareal_reset_stats", "ac_launch_count", "ac_parareal_destroy",
            "ac_fine_variant_count", "ac_fine_variant_name", "ac_fine_get_variant", "ac_fine_set_variant",
-           "ac_fine_autotune", "ac_fine_trajectory", "ac_fine_adjoint", "ac_energy", "ac_energy_grad",
+           "ac_fine_autotune", "ac_fine_propagate_work", "ac_fine_trajectory", "ac_fine_adjoint", "ac_energy", "ac_energy_grad",
            "ac_energy_gradient_workspace", "ac_energy_gradient_ic",
            "cnn_train_bytes", "cnn_forward_train", "cnn_backward", "cnn_adam_step", "mse_loss_grad"]
 
@@ -108,6 +108,7 @@ def load(build_if_missing: bool = True):
         L.ac_fine_set_variant.argtypes = [I, I, I]
         L.ac_fine_autotune.argtypes = [P(ac_params), I, I, S, S, P(C.c_float), S]
         L.ac_fine_trajectory.argtypes = [P(ac_params), I, I, S, S, S]
+        L.ac_fine_propagate_work.argtypes = [P(ac_params), I, S, S, S, S]
         L.ac_fine_adjoint.argtypes = [P(ac_params), I, I, S, S, S, S]
         L.ac_energy.argtypes = [P(ac_params), I, S, S, S]
         L.ac_energy_grad.argtypes = [P(ac_params), I, S, S, S]
@@ -215,6 +216,17 @@ def ac_fine_autotune(params: FineParams, steps: int, u_in, u_out, stream=None):
                               _dev(u_out, params.dtype, "u_out"), ms, _stream(stream)))
     names = ac_fine_variants(params.n, params.precision)
     return {names[i]: ms[i] for i in range(cnt)}, ac_fine_get_variant(params.n, params.precision)
+
+
+def ac_fine_propagate_work(params: FineParams, work, u_in, u_out, stream=None):
+    """work: int32 CUDA tensor [count][4] = (in field, out field, steps, 0)."""
+    import torch
+    count = work.shape[0]
+    p = params.c()
+    _check(load().ac_fine_propagate_work(C.byref(p), count, _dev(work, torch.int32, "work"),
+                                         _dev(u_in, params.dtype, "u_in"), _dev(u_out, params.dtype, "u_out"),
+                                         _stream(stream)))
+    return u_out
 
 
 def ac_fine_trajectory(params: FineParams, steps: int, u0, traj=None, stream=None):

@@ -535,6 +535,7 @@ int fine_run_work(const ac_params* p, int count, const int4* work, const void* i
     int rc = check_params(p);
     if (rc) return rc;
     ACPR_CHECK_ARG(count >= 0 && (count == 0 || (work && in && out)), "bad work list");
+    ACPR_CHECK_ARG(reinterpret_cast<uintptr_t>(work) % 16 == 0, "work list must be 16-byte aligned");
     if (!count) return AC_OK;
     FineArgs a{};
     a.in = in;
@@ -652,4 +653,10 @@ extern "C" int ac_fine_autotune(const ac_params* params, int num_fields, int ste
     cudaEventDestroy(e1);
     g_variant[params->precision][ilog2(params->n)] = best;
     return rc ? rc : AC_OK;
+}
+
+extern "C" int ac_fine_propagate_work(const ac_params* params, int count, const void* work, const void* u_in,
+                                      void* u_out, acpr_stream stream) {
+    return acpr::fine_run_work(params, count, static_cast<const int4*>(work), u_in, u_out,
+                               reinterpret_cast<cudaStream_t>(stream));
 }
