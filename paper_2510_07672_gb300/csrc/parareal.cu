@@ -386,8 +386,13 @@ static int enqueue(ac_parareal* st, int k, int m, int nwork, cudaStream_t stream
     const size_t fb = st->esz * nn;
     const bool tm = st->timing;
     int rc;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (tm) ACPR_CUDA(cudaStreamIsCapturing(stream, &cap));
     auto mark = [&](int i) -> int {
-        if (tm) ACPR_CUDA(cudaEventRecord(st->ev[i], stream));
+        // inside a capture only an "external" record becomes an event node
+        if (tm) ACPR_CUDA(cudaEventRecordWithFlags(st->ev[i], stream,
+                                                   cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                                        : cudaEventRecordDefault));
         return AC_OK;
     };
     if (k == 0) {

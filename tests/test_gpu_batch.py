@@ -59,6 +59,7 @@ def test_graph_replay_matches_direct_launches():
     for graphs in (False, True, True):  # the second graph run replays cached graphs
         pr = G.Parareal(fp, net, u0, 6, 25)
         pr.enable_graphs(graphs)
+        pr.enable_timing(True)
         incs = []
         pr.iterate()
         for k in range(1, 7):
@@ -72,6 +73,8 @@ def test_graph_replay_matches_direct_launches():
                 l2, _ = pr.iterate()
                 assert l2 == incs[k - 1]
             assert torch.equal(pr.trajectory(), res[-1][0])
+            st = pr.stats()
+            assert st["fine_ms"] > 0 and st["coarse_ms"] > 0 and st["increment_ms"] > 0
     assert torch.equal(res[0][0], res[1][0])
     assert res[0][1] == res[1][1]
 
