@@ -356,7 +356,8 @@ int ac_parareal_get_stats(const ac_parareal* state, ac_parareal_stats* out);
 int ac_parareal_reset_stats(ac_parareal* state);
 
 /* Number of kernels this library has launched in this process (all entry
- * points, all devices).  Lets a caller count the launches of a region. */
+ * points, all devices; a replayed CUDA graph adds its kernel nodes).  Lets a
+ * caller count the launches of a region. */
 long long ac_launch_count(void);
 
 /* ac_parareal_solve on `count` handles (e.g. one per grid size) at once:

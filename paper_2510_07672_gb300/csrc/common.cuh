@@ -34,6 +34,7 @@ void set_error(const char* fmt, ...);
 
 // Kernels launched by the library (ac_launch_count()).
 void count_launch();
+void count_launch_add(long long n);
 
 // Check a kernel launch (configuration errors are reported synchronously) and
 // count it.

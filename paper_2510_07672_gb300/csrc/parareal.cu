@@ -296,7 +296,7 @@ struct ac_parareal {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t done = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream the graphs are captured on
-    std::map<GraphKey, cudaGraphExec_t> graph_cache;
+    std::map<GraphKey, std::pair<cudaGraphExec_t, int>> graph_cache;  // exec, kernel nodes
     ac_parareal_stats stats{};
 };
 
@@ -314,7 +314,7 @@ static void free_state(ac_parareal* st) {
     for (cudaEvent_t e : st->ev)
         if (e) cudaEventDestroy(e);
     if (st->done) cudaEventDestroy(st->done);
-    for (auto& kv : st->graph_cache) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : st->graph_cache) cudaGraphExecDestroy(kv.second.first);
     if (st->cap_stream) cudaStreamDestroy(st->cap_stream);
     delete st;
 }
@@ -483,13 +483,27 @@ static int launch(ac_parareal* st, int k, cudaStream_t stream) {
             cudaError_t ec = cudaStreamEndCapture(st->cap_stream, &graph);
             if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
             ACPR_CUDA(ec);
+            // kernel nodes, so that replays count towards ac_launch_count()
+            size_t nodes = 0;
+            int kernels = 0;
+            if (cudaGraphGetNodes(graph, nullptr, &nodes) == cudaSuccess && nodes) {
+                std::vector<cudaGraphNode_t> list(nodes);
+                if (cudaGraphGetNodes(graph, list.data(), &nodes) == cudaSuccess)
+                    for (size_t i = 0; i < nodes; ++i) {
+                        cudaGraphNodeType t;
+                        if (cudaGraphNodeGetType(list[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+                    }
+            }
             cudaGraphExec_t exec = nullptr;
             cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
             cudaGraphDestroy(graph);
             ACPR_CUDA(ei);
-            it = st->graph_cache.emplace(key, exec).first;
+            // capture counted the kernels as launches already; undo that
+            count_launch_add(-kernels);
+            it = st->graph_cache.emplace(key, std::make_pair(exec, kernels)).first;
         }
-        ACPR_CUDA(cudaGraphLaunch(it->second, stream));
+        ACPR_CUDA(cudaGraphLaunch(it->second.first, stream));
+        count_launch_add(it->second.second);
     } else {
         if ((rc = enqueue(st, k, m, nwork, stream))) return rc;
     }
@@ -778,7 +792,7 @@ extern "C" int ac_parareal_enable_timing(ac_parareal* state, int on) {
     if (on && !state->ev[0])
         for (cudaEvent_t& e : state->ev) ACPR_CUDA(cudaEventCreate(&e));
     if (bool(on) != state->timing) {
-        for (auto& kv : state->graph_cache) cudaGraphExecDestroy(kv.second);
+        for (auto& kv : state->graph_cache) cudaGraphExecDestroy(kv.second.first);
         state->graph_cache.clear();  // captured graphs hold (or lack) the timing events
     }
     state->timing = on != 0;

@@ -68,11 +68,13 @@ def test_graph_replay_matches_direct_launches():
         res.append((pr.trajectory(), incs))
         if graphs:
             pr.reset(u0)
+            n0 = G.ac_launch_count()
             pr.iterate()
             for k in range(1, 7):
                 l2, _ = pr.iterate()
                 assert l2 == incs[k - 1]
             assert torch.equal(pr.trajectory(), res[-1][0])
+            assert G.ac_launch_count() - n0 > 6 * 7  # replays count their kernels
             st = pr.stats()
             assert st["fine_ms"] > 0 and st["coarse_ms"] > 0 and st["increment_ms"] > 0
     assert torch.equal(res[0][0], res[1][0])
