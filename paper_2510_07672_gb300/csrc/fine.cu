@@ -466,8 +466,14 @@ static int dispatch_fine(int n, const FineArgs& args, cudaStream_t stream) {
     return v[idx].launch(args, stream);
 }
 
+bool fine_big_supported(int n, int precision);
+int fine_big_run(const ac_params* p, int groups, int per_group, int steps, const void* in, long long in_gs,
+                 long long in_off, void* out, long long out_gs, long long out_off, const int* map, void* ws,
+                 cudaStream_t st);
+
 static bool fine_built(int n, int precision) {
     int count = 0;
+    if (fine_big_supported(n, precision)) return true;
     return is_pow2(n) && n <= 1024 && pick_variant(n, precision, &count) != nullptr && count > 0;
 }
 
@@ -498,6 +504,14 @@ int fine_run(const ac_params* p, int groups, int per_group, int steps, const voi
     ACPR_CHECK_ARG((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % 16 == 0,
                    "field pointers must be 16-byte aligned");
     ACPR_CHECK_ARG((long long)groups * per_group < (1LL << 30), "too many fields");
+    if (fine_big_supported(p->n, p->precision)) {
+        if (adjoint || traj || states) {
+            set_error("ac_fine: n=%d supports plain propagation only (no trajectory or adjoint mode)", p->n);
+            return AC_ERR_UNSUPPORTED;
+        }
+        return fine_big_run(p, groups, per_group, steps, in, in_gs, in_off, out, out_gs, out_off, map, nullptr,
+                            stream);
+    }
     FineArgs a{};
     a.in = in;
     a.out = out;
@@ -536,6 +550,10 @@ int fine_run_work(const ac_params* p, int count, const int4* work, const void* i
     if (rc) return rc;
     ACPR_CHECK_ARG(count >= 0 && (count == 0 || (work && in && out)), "bad work list");
     ACPR_CHECK_ARG(reinterpret_cast<uintptr_t>(work) % 16 == 0, "work list must be 16-byte aligned");
+    if (fine_big_supported(p->n, p->precision)) {
+        set_error("ac_fine: n=%d has no work-list launch (uniform steps only)", p->n);
+        return AC_ERR_UNSUPPORTED;
+    }
     if (!count) return AC_OK;
     FineArgs a{};
     a.in = in;

@@ -270,6 +270,7 @@ struct ac_parareal {
     cnn_desc g;
     int problems = 0, s = 0;
     std::vector<int> sp, cp;    // per-problem slices and steps per slice
+    bool uniform = true;        // every problem has the same slices and steps
     size_t esz = 0;
     long long nn = 0;
     void* Ua = nullptr;
@@ -410,7 +411,13 @@ static int enqueue(ac_parareal* st, int k, int m, int nwork, cudaStream_t stream
     }
     // 1. fine solves of slices k-1 .. s_p-1 of every active problem (one launch)
     if ((rc = mark(0))) return rc;
-    rc = fine_run_work(&st->p, nwork, st->d_fw, st->Ua, st->Fres, stream);
+    if (st->uniform && st->p.n >= 1024) {
+        // large fields: the two-pass path runs uniform launches only
+        rc = fine_propagate_mapped(&st->p, m, s - k + 1, st->cp[0], st->Ua, s + 1, k - 1, st->Fres, s, k - 1,
+                                   st->d_map, stream);
+    } else {
+        rc = fine_run_work(&st->p, nwork, st->d_fw, st->Ua, st->Fres, stream);
+    }
     if (rc) return rc;
     if ((rc = mark(1))) return rc;
     // 2. newest frozen slice and the exact slice k
@@ -584,6 +591,13 @@ static int create(const ac_params* params, const cnn_desc* coarse, int problems,
     st->s = smax;
     st->sp.assign(slices, slices + problems);
     st->cp.assign(steps, steps + problems);
+    for (int p = 1; p < problems; ++p)
+        if (slices[p] != slices[0] || steps[p] != steps[0]) st->uniform = false;
+    if (params->n >= 1024 && !st->uniform) {
+        delete st;
+        set_error("ac_parareal: n=%d needs equal slice counts and steps for all problems", params->n);
+        return AC_ERR_UNSUPPORTED;
+    }
     st->esz = elem_size(params->precision);
     st->nn = (long long)params->n * params->n;
     st->active.assign(problems, 1);

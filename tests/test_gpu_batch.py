@@ -97,3 +97,19 @@ def test_solve_many_sizes_on_streams():
     for h, ref in zip(handles, singles):
         assert torch.equal(h.trajectory(), ref)
     assert [len(o[0]) for o in out] == [2, 1]
+
+
+def test_parareal_1024_exact_at_k_equals_s():
+    """One 1024^2 problem (the two-pass fine path inside Parareal): at k = s the
+    trajectory is the sequential fine solve bit for bit."""
+    n, s, c = 1024, 3, 4
+    fp = G.FineParams(n, 0.004, 2.0, 2e-5, precision=G.AC_F32)
+    net = make_net(C=16, L=3)
+    u0 = fields(n, [11])
+    pr = G.Parareal(fp, net, u0, s, c)
+    its, _ = pr.solve(tol=0.0, kmax=s)
+    assert its == [s]
+    seq = [u0]
+    for j in range(s):
+        seq.append(G.ac_fine_propagate_slices(fp, c, seq[-1]))
+    assert torch.equal(pr.trajectory()[0], torch.cat(seq))

@@ -23,7 +23,7 @@ def dev(a, dtype):
 
 
 CASES_F64 = [(8, 0), (16, 1), (32, 0), (64, 0), (64, 1), (128, 1)]
-CASES_F32 = [(16, 0), (64, 1), (128, 0), (128, 1), (256, 0), (256, 1), (512, 0), (512, 1)]
+CASES_F32 = [(16, 0), (64, 1), (128, 0), (128, 1), (256, 0), (256, 1), (512, 0), (512, 1), (1024, 0), (1024, 1)]
 
 
 @pytest.mark.parametrize("n,variant", CASES_F64)
@@ -159,3 +159,20 @@ def test_autotune_picks_a_shape():
     assert all(t > 0 for t in times.values())
     assert times[G.ac_fine_variants(n, G.AC_F32)[idx]] == min(times.values())
     G.ac_fine_set_variant(n, G.AC_F32, 0)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_propagate_1024_two_pass(variant):
+    """1024^2 fields run the two-pass path through L2/HBM; three fields (mapped
+    launch), 6 steps, against the oracle, plus mass conservation."""
+    n, steps = 1024, 6
+    u = np.stack([I.random_field(n, seed=60 + i, zero_mean=bool(variant)) for i in range(3)]).astype(np.float32)
+    fp = G.FineParams(n, 0.004, 2.0, 2e-5, variant=variant, precision=G.AC_F32)
+    got = G.ac_fine_propagate_slices(fp, steps, dev(u, torch.float32)).double().cpu().numpy()
+    p = O.params(n, 0.004, 2.0, 2e-5, variant)
+    ref = O.fine_propagate(p, steps, u[2].astype(np.float64))
+    assert np.abs(got[2] - ref).max() < 2e-5 * np.sqrt(steps)
+    if variant:
+        assert abs(got[0].mean() - u[0].astype(np.float64).mean()) < 1e-7
+    zero = G.ac_fine_propagate_slices(fp, 0, dev(u, torch.float32)).cpu().numpy()
+    assert np.array_equal(zero, u)
