@@ -1,6 +1,7 @@
 // fft_reg.cuh -- small complex DFTs held entirely in one thread's registers,
 // and the two-pass (four-step) 1D transform of length N = A * B that a group of
-// B threads performs on one line of a field with one shared-memory exchange.
+// B lanes of one warp performs on one line of a field with one shared-memory
+// exchange.
 //
 // Layout invariant ("stride layout"): thread j of a line holds element
 // j + B * t in slot t, t = 0..A-1, both before and after a 1D transform (the
@@ -101,20 +102,34 @@ __device__ __forceinline__ void reg_dft(T (&re)[M], T (&im)[M]) {
     dit_stages<T, M, SIGN, 2>(re, im);
 }
 
-// One line transform of length N = A * B by the B threads of that line.
+// Shared-memory position of element e = k1 * B + n2 of a line's exchange area:
+// one pad slot after every B elements, so that the pass-2 reads (B lanes
+// reading elements B apart) fall in distinct banks.
+template <int B>
+__host__ __device__ constexpr int xpos(int k1, int n2) { return k1 * (B + 1) + n2; }
+
+// Exchange-area length (complex elements) a line needs.
+template <int N, int B>
+__host__ __device__ constexpr int xlen() { return N + N / B; }
+
+// One line transform of length N = A * B by the B lanes of that line, which
+// are B consecutive lanes of one warp (B divides 32).
 //   x:    this thread's A elements (stride layout), transformed in place.
-//   tw:   shared table exp(-2 pi i m / N), m = 0..N-1 (the inverse uses the
-//         conjugates); every lane of a warp reads the same entry (broadcast).
-//   line: base of this line's exchange area in shared memory (>= N elements);
-//   j:    this thread's lane within the line.
-// Unnormalised, X_k = sum_n x_n exp(SIGN 2 pi i n k / N).
-// Contains __syncthreads(): every thread of the block must call it.  With
-// SYNC_BEFORE = false the caller guarantees that no thread still reads `line`
-// from an earlier use (a block or cluster barrier lies in between).
-template <typename T, int N, int A, int B, int SIGN, bool SYNC_BEFORE = true>
+//   tw:   shared table, entry k1 * B + j = exp(-2 pi i ((j k1) mod N) / N)
+//         (the inverse uses the conjugates): the B lanes of a line read B
+//         consecutive entries.
+//   line: base of this line's exchange area in shared memory (>= xlen<N, B>()
+//         elements), read and written by this line's lanes only;
+//   j:    this thread's lane within the line;
+//   wmask: the warp's lanes that run this code (all lanes of every line in
+//         the warp).
+// Unnormalised, X_k = sum_n x_n exp(SIGN 2 pi i n k / N).  Only warp-level
+// barriers: the lanes that exchange data share a warp.
+template <typename T, int N, int A, int B, int SIGN>
 __device__ __forceinline__ void line_fft(vec2_t<T> (&x)[A], const vec2_t<T>* __restrict__ tw,
-                                         vec2_t<T>* line, int j) {
+                                         vec2_t<T>* line, int j, unsigned wmask) {
     static_assert(A * B == N && A % B == 0, "N = A * B with B | A");
+    static_assert(B <= 32 && 32 % B == 0, "a line's lanes must fit in one warp");
     T re[A], im[A];
 #pragma unroll
     for (int t = 0; t < A; ++t) { re[t] = x[t].x; im[t] = x[t].y; }
@@ -123,22 +138,22 @@ __device__ __forceinline__ void line_fft(vec2_t<T> (&x)[A], const vec2_t<T>* __r
     // twiddle exp(SIGN 2 pi i j k1 / N)
 #pragma unroll
     for (int k1 = 1; k1 < A; ++k1) {
-        const vec2_t<T> w = tw[(j * k1) & (N - 1)];
+        const vec2_t<T> w = tw[k1 * B + j];
         const T c = w.x;
         const T s = SIGN < 0 ? w.y : -w.y;
         const T r = re[k1] * c - im[k1] * s;
         im[k1] = re[k1] * s + im[k1] * c;
         re[k1] = r;
     }
-    if constexpr (SYNC_BEFORE) __syncthreads();  // previous readers of `line` are done
+    __syncwarp(wmask);  // this line's earlier readers of `line` are done
 #pragma unroll
     for (int k1 = 0; k1 < A; ++k1) {
         vec2_t<T> v;
         v.x = re[k1];
         v.y = im[k1];
-        line[k1 * B + j] = v;
+        line[xpos<B>(k1, j)] = v;
     }
-    __syncthreads();
+    __syncwarp(wmask);
     // pass 2: for k1 = j + B m, a B-point DFT over n2
 #pragma unroll
     for (int m = 0; m < A / B; ++m) {
@@ -146,7 +161,7 @@ __device__ __forceinline__ void line_fft(vec2_t<T> (&x)[A], const vec2_t<T>* __r
         T br[B], bi[B];
 #pragma unroll
         for (int n2 = 0; n2 < B; ++n2) {
-            const vec2_t<T> v = line[k1 * B + n2];
+            const vec2_t<T> v = line[xpos<B>(k1, n2)];
             br[n2] = v.x;
             bi[n2] = v.y;
         }

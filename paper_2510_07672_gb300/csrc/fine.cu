@@ -64,17 +64,39 @@ struct FineArgs {
     double lam_scale;  // dt eps^2 (4 / h^2)
 };
 
+// Smallest value >= len that is congruent to B modulo 16 (B < 16); B = 16
+// (one line per half-warp) takes len + 1.
+__host__ __device__ constexpr int exchange_pitch(int len, int B) {
+    return B >= 16 ? len + 1 : len + (((B - len) % 16) + 16) % 16;
+}
+
+// Smallest odd multiple of 16/B that is >= L (B <= 16).
+__host__ __device__ constexpr int transpose_pitch(int L, int B) {
+    return ((L / (16 / B)) | 1) * (16 / B) >= L ? ((L / (16 / B)) | 1) * (16 / B)
+                                                 : ((L / (16 / B)) + 2 | 1) * (16 / B);
+}
+
 template <typename T, int N, int P, int A, int B>
 struct FineShape {
     static constexpr int R = N / P;           // rows per CTA
     static constexpr int L = R / 2;           // lines per CTA (row pairs, then columns)
     static constexpr int HALF = N / 2;
     static constexpr int THREADS = L * B;     // (line, lane) pairs
-    static constexpr int PITCH = N + 1;       // complex elements per smem line
-    static constexpr size_t BUF = sizeof(vec2_t<T>) * size_t(L) * PITCH;
-    // bufR, bufC (DSMEM transpose targets), bufX (line-FFT exchanges), tables
-    static constexpr size_t SMEM = 3 * BUF + sizeof(vec2_t<T>) * N + sizeof(T) * N + 4 * sizeof(double);
+    // bufX: one padded exchange area per line.  A half-warp holds 16/B lines;
+    // with XP = B (mod 16) their areas start 2B banks apart and the exchange
+    // writes and reads of those lines fall in distinct banks.
+    static constexpr int XP = exchange_pitch(xlen<N, B>(), B);
+    // bufR, bufC (transpose targets): position-major, element (pos, line) at
+    // pos * TP + line.  A sender's B lanes write B consecutive lines at one
+    // position (one contiguous run in the peer's memory); a reader's half-warp
+    // (16/B lines, B positions each, TP elements apart) hits distinct banks
+    // when TP is an odd multiple of 16/B.
+    static constexpr int TP = transpose_pitch(L, B);
+    static constexpr size_t BUFT = sizeof(vec2_t<T>) * size_t(N) * TP;
+    static constexpr size_t BUFX = sizeof(vec2_t<T>) * size_t(L) * XP;
+    static constexpr size_t SMEM = 2 * BUFT + BUFX + sizeof(vec2_t<T>) * N + sizeof(T) * N + 4 * sizeof(double);
     static_assert(R >= 2 && R % 2 == 0, "need at least two rows per CTA");
+    static_assert(B <= 16 && TP >= L, "transpose layout");
 };
 
 // Division where float32 round-off of a couple of ulp is harmless (the
@@ -106,18 +128,21 @@ __global__ void __launch_bounds__(FineShape<T, N, P, A, B>::THREADS, MINB)
 fine_field_kernel(FineArgs args) {
     using Sh = FineShape<T, N, P, A, B>;
     using V = vec2_t<T>;
-    constexpr int R = Sh::R, L = Sh::L, HALF = Sh::HALF, PITCH = Sh::PITCH;
+    constexpr int R = Sh::R, L = Sh::L, HALF = Sh::HALF, TP = Sh::TP, XP = Sh::XP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* bufR = reinterpret_cast<V*>(smem_raw);         // row-phase lines
-    V* bufC = bufR + L * PITCH;                        // column-phase lines
-    V* bufX = bufC + L * PITCH;                        // line-FFT exchanges
-    V* tw = bufX + L * PITCH;                          // exp(-2 pi i m / N)
+    V* bufR = reinterpret_cast<V*>(smem_raw);         // row phase: [pos][line]
+    V* bufC = bufR + N * TP;                           // column phase: [pos][line]
+    V* bufX = bufC + N * TP;                           // line-FFT exchanges
+    V* tw = bufX + L * XP;                             // line_fft twiddle table
     T* lam = reinterpret_cast<T*>(tw + N);             // dt eps^2 mu_k
     double* part = reinterpret_cast<double*>(lam + N); // mass partial, adjoint mean
 
     const int tid = threadIdx.x;
-    const int j = tid / L;       // lane within a line
-    const int line = tid % L;    // local line index
+    // the B lanes of a line are consecutive lanes of one warp, so the line
+    // FFTs' exchanges need warp barriers only
+    const int j = tid % B;       // lane within a line
+    const int line = tid / B;    // local line index
+    constexpr unsigned WMASK = Sh::THREADS >= 32 ? 0xffffffffu : ((1u << Sh::THREADS) - 1u);
     int rank = 0;
     if constexpr (P > 1) rank = int(cg::this_cluster().block_rank());
     const int field = blockIdx.x / P;
@@ -140,7 +165,7 @@ fine_field_kernel(FineArgs args) {
 
     for (int k = tid; k < N; k += Sh::THREADS) {
         double sn, cs;
-        sincospi(-2.0 * double(k) / N, &sn, &cs);
+        sincospi(-2.0 * double(((k % B) * (k / B)) & (N - 1)) / N, &sn, &cs);
         tw[k].x = T(cs);
         tw[k].y = T(sn);
         const double s = sinpi(double(k) / N);
@@ -155,7 +180,7 @@ fine_field_kernel(FineArgs args) {
         const int row = idx / N, c = idx % N;
         const T v = in[idx];
         msum += double(v);
-        reinterpret_cast<T*>(bufR)[2 * ((row % L) * PITCH + c) + row / L] = v;
+        reinterpret_cast<T*>(bufR)[2 * (c * TP + row % L) + row / L] = v;
         if (traj0) traj0[idx] = v;
     }
     double mean = 0.0;
@@ -182,11 +207,11 @@ fine_field_kernel(FineArgs args) {
     __syncthreads();
 
     V x[A];
-    V* myR = bufR + line * PITCH;
-    V* myC = bufC + line * PITCH;
-    V* myX = bufX + line * PITCH;
+    V* myR = bufR + line;  // element pos of this line at myR[pos * TP]
+    V* myC = bufC + line;
+    V* myX = bufX + line * XP;
 #pragma unroll
-    for (int t = 0; t < A; ++t) x[t] = myR[j + B * t];
+    for (int t = 0; t < A; ++t) x[t] = myR[(j + B * t) * TP];
 
     const T a = T(args.a);
     const T dt = T(args.dt);
@@ -194,11 +219,11 @@ fine_field_kernel(FineArgs args) {
     const T half = T(0.5);
     const int pair = rank * L + line;  // global row-pair index (row phase)
     const int col = rank * L + line;   // global column index (column phase)
-    // Exchange buffers and barriers per step.  The row FFTs exchange through
-    // bufR after it has been read (forward) or through bufX (inverse), the
-    // column FFTs through bufX, the column-0 split through bufC; each buffer's
-    // previous readers are separated from its next writers by a block or
-    // cluster barrier, so only the barrier after each exchange write remains.
+    // Exchange buffers and barriers per step.  Every line FFT, and the
+    // column-0 separation, exchanges through the line's own area of bufX,
+    // which only the line's lanes (one warp) touch: warp barriers order it.
+    // bufR and bufC are only transpose targets (and the load/store staging),
+    // ordered by the two cluster barriers.
     for (int step = 0; step < nsteps; ++step) {
         if (!args.adjoint) {
             // pointwise right-hand side on both rows of the line
@@ -209,10 +234,7 @@ fine_field_kernel(FineArgs args) {
                 x[t].y = a * ui + dt * (ui - ui * ui * ui);
             }
         }
-        // bufR: its last readers (the rebuild, before the previous inverse
-        // row FFT's barrier) are done; peers write it only after barrier 1
-        if (step == 0) __syncthreads();
-        line_fft<T, N, A, B, -1, false>(x, tw, myR, j);
+        line_fft<T, N, A, B, -1>(x, tw, myX, j, WMASK);
         // row spectra Z_p[k] -> column min(k, N - k) (k = 0, N/2 -> column 0)
 #pragma unroll
         for (int t = 0; t < A; ++t) {
@@ -220,7 +242,7 @@ fine_field_kernel(FineArgs args) {
             const int c = (k == HALF) ? 0 : (k < HALF ? k : N - k);
             const int slot = (k == 0 || k < HALF) ? 0 : 1;
             V* dst = peer_ptr<P>(bufC, c / L);
-            dst[(c % L) * PITCH + slot * HALF + pair] = x[t];
+            dst[(slot * HALF + pair) * TP + c % L] = x[t];
         }
         cluster_barrier<P>();
         // split each row pair into its two rows' half spectra
@@ -229,7 +251,7 @@ fine_field_kernel(FineArgs args) {
             const int r = j + B * t;
             const int lr = r % R;
             const int pp = (r / R) * L + (lr % L);
-            const V za = myC[pp], zb = myC[HALF + pp];
+            const V za = myC[pp * TP], zb = myC[(HALF + pp) * TP];
             V v;
             if (col == 0) {  // packed DC and Nyquist columns
                 if (lr < L) { v.x = za.x; v.y = zb.x; }
@@ -243,8 +265,7 @@ fine_field_kernel(FineArgs args) {
             }
             x[t] = v;
         }
-        // bufX: last read in the previous step's inverse FFTs, before barrier 2
-        line_fft<T, N, A, B, -1, false>(x, tw, myX, j);
+        line_fft<T, N, A, B, -1>(x, tw, myX, j, WMASK);
         // divide by the symbol, with 1/N^2 of the inverse folded in
         if (col != 0) {
             const T lam_l = lam[col];
@@ -259,20 +280,20 @@ fine_field_kernel(FineArgs args) {
             // column 0 carries columns 0 and N/2 as C = F0 + i FN: separate
             // them with C[N - k], scale each by its own symbol, recombine:
             // C'[k] = C[k] (s0 + sN) / 2 + conj(C[N - k]) (s0 - sN) / 2
-            // (through bufC: its readers, the split, finished before the
-            // column FFT's exchange barrier)
+            // (through this line's area of bufX, after the FFT's reads)
+            __syncwarp(WMASK);
             if (col == 0) {
 #pragma unroll
-                for (int t = 0; t < A; ++t) myC[j + B * t] = x[t];
+                for (int t = 0; t < A; ++t) myX[j + B * t] = x[t];
             }
-            __syncthreads();
+            __syncwarp(WMASK);
             if (col == 0) {
                 const T lam_n = lam[HALF];
 #pragma unroll
                 for (int t = 0; t < A; ++t) {
                     const int k = j + B * t;
                     const V zc = x[t];
-                    const V zp = myC[(N - k) & (N - 1)];
+                    const V zp = myX[(N - k) & (N - 1)];
                     const T lk = lam[k];
                     const T s0 = fast_div(inv_nn, a + lk);
                     const T sn = fast_div(inv_nn, a + (lk + lam_n));
@@ -293,15 +314,14 @@ fine_field_kernel(FineArgs args) {
                 }
             }
         }
-        // bufX: its readers (forward column FFT) finished before the barrier above
-        line_fft<T, N, A, B, +1, false>(x, tw, myX, j);
+        line_fft<T, N, A, B, +1>(x, tw, myX, j, WMASK);
         // column values V_r[c] -> owner of row r, slot (row role) and column c
 #pragma unroll
         for (int t = 0; t < A; ++t) {
             const int r = j + B * t;
             const int lr = r % R;
             V* dst = peer_ptr<P>(bufR, r / R);
-            dst[(lr % L) * PITCH + (lr / L) * HALF + col] = x[t];
+            dst[((lr / L) * HALF + col) * TP + lr % L] = x[t];
         }
         cluster_barrier<P>();
         // rebuild each pair's full row spectrum from the half spectra
@@ -310,22 +330,21 @@ fine_field_kernel(FineArgs args) {
             const int k = j + B * t;
             V z;
             if (k == 0 || k == HALF) {
-                const V va = myR[0], vb = myR[HALF];
+                const V va = myR[0], vb = myR[HALF * TP];
                 if (k == 0) { z.x = va.x; z.y = vb.x; }
                 else        { z.x = va.y; z.y = vb.y; }
             } else if (k < HALF) {  // Va + i Vb
-                const V va = myR[k], vb = myR[HALF + k];
+                const V va = myR[k * TP], vb = myR[(HALF + k) * TP];
                 z.x = va.x - vb.y;
                 z.y = va.y + vb.x;
             } else {                // conj(Va) + i conj(Vb) at N - k
-                const V va = myR[N - k], vb = myR[HALF + N - k];
+                const V va = myR[(N - k) * TP], vb = myR[(HALF + N - k) * TP];
                 z.x = va.x + vb.y;
                 z.y = vb.x - va.y;
             }
             x[t] = z;
         }
-        // bufX: last read in the inverse column FFT, before barrier 2
-        line_fft<T, N, A, B, +1, false>(x, tw, myX, j);
+        line_fft<T, N, A, B, +1>(x, tw, myX, j, WMASK);
         if (args.adjoint) {
             // lambda_n = a mu + dt f'(u_n) (mu - mean mu), rows r0 (real) and r1 (imag)
             const int n_state = nsteps - 1 - step;
@@ -344,26 +363,25 @@ fine_field_kernel(FineArgs args) {
         if (args.traj) {
             __syncthreads();
 #pragma unroll
-            for (int t = 0; t < A; ++t) myR[j + B * t] = x[t];
+            for (int t = 0; t < A; ++t) myR[(j + B * t) * TP] = x[t];
             __syncthreads();
             T* ts = static_cast<T*>(args.traj) + (size_t(step + 1) * traj_step) + size_t(field) * NN +
                     size_t(rank) * R * N;
             for (int idx = tid; idx < R * N; idx += Sh::THREADS) {
                 const int row = idx / N, c = idx % N;
-                ts[idx] = reinterpret_cast<const T*>(bufR)[2 * ((row % L) * PITCH + c) + row / L];
+                ts[idx] = reinterpret_cast<const T*>(bufR)[2 * (c * TP + row % L) + row / L];
             }
-            __syncthreads();  // the next forward row FFT writes bufR without a leading barrier
         }
     }
 
     // store rows, coalesced, through bufR
     __syncthreads();
 #pragma unroll
-    for (int t = 0; t < A; ++t) myR[j + B * t] = x[t];
+    for (int t = 0; t < A; ++t) myR[(j + B * t) * TP] = x[t];
     __syncthreads();
     for (int idx = tid; idx < R * N; idx += Sh::THREADS) {
         const int row = idx / N, c = idx % N;
-        out[idx] = reinterpret_cast<const T*>(bufR)[2 * ((row % L) * PITCH + c) + row / L];
+        out[idx] = reinterpret_cast<const T*>(bufR)[2 * (c * TP + row % L) + row / L];
     }
 }
 
@@ -416,18 +434,17 @@ static const FineVariant* fine_variants(int n, int* count) {
         static const FineVariant v128[] = {ACPR_FV(T, 128, 2, 16, 8, 2), ACPR_FV(T, 128, 4, 16, 8, 3),
                                            ACPR_FV(T, 128, 1, 16, 8, 1)};
         static const FineVariant v256[] = {ACPR_FV(T, 256, 8, 16, 16, 2), ACPR_FV(T, 256, 4, 16, 16, 1),
-                                           ACPR_FV(T, 256, 16, 16, 16, 3), ACPR_FV(T, 256, 16, 16, 16, 4),
-                                           ACPR_FV(T, 256, 8, 16, 16, 1)};
+                                           ACPR_FV(T, 256, 16, 16, 16, 3), ACPR_FV(T, 256, 8, 16, 16, 1)};
         static const FineVariant v512[] = {ACPR_FV(T, 512, 16, 32, 16, 1)};
         switch (n) {
             case 128: *count = 3; return v128;
-            case 256: *count = 5; return v256;
+            case 256: *count = 4; return v256;
             case 512: *count = 1; return v512;
             default: break;
         }
     } else {
         static const FineVariant v128[] = {ACPR_FV(T, 128, 4, 16, 8, 1), ACPR_FV(T, 128, 2, 16, 8, 1)};
-        static const FineVariant v256[] = {ACPR_FV(T, 256, 8, 16, 16, 2), ACPR_FV(T, 256, 16, 16, 16, 2)};
+        static const FineVariant v256[] = {ACPR_FV(T, 256, 8, 16, 16, 1), ACPR_FV(T, 256, 16, 16, 16, 2)};
         switch (n) {
             case 128: *count = 2; return v128;
             case 256: *count = 2; return v256;
