@@ -399,7 +399,7 @@ int coarse_step_mapped(const cnn_desc* d, int n, int batch, const void* u_in, lo
     if (d->precision == AC_F64) {
         rc = run_f64(d, n, batch, static_cast<const double*>(u_in), static_cast<double*>(u_out), io, st);
     } else {
-        ACPR_CHECK_ARG(d->packed != nullptr, "AC_F32 conv needs the packed weight buffer");
+        ACPR_CHECK_ARG(d->packed != nullptr || d->layers == 2, "AC_F32 conv needs the packed weight buffer");
         const float* ui = static_cast<const float*>(u_in);
         float* uo = static_cast<float*>(u_out);
         switch (d->channels) {

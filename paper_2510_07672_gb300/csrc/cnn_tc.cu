@@ -18,6 +18,7 @@
 // TMEM with tcgen05.ld, adds the float32 bias, applies the activation, rounds
 // to bf16 and stores 16-byte channel chunks.  All waits are bounded; a timeout
 // sets a device flag that tc_check_status() reports as AC_ERR_TIMEOUT.
+// Fields with n >= 128 take the persistent, warp-specialised kernel below.
 #include "cnn.cuh"
 #include "tc_ptx.cuh"
 
@@ -227,9 +228,361 @@ conv_hidden_tc_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __res
     if (warp == 0) tc::tmem_dealloc(tmem, uint32_t(ncols));
 }
 
+// ------------------------------------------------------------ persistent --
+// Persistent, warp-specialised form of the same GEMM for n >= 128 (n a
+// multiple of 128), one CTA per SM.  Work unit = (field f, column block cb,
+// row block yb): TY output rows y0 = yb TY .. y0 + TY - 1, each cut into MG
+// M-tiles of 128 consecutive positions, columns [cb CW, cb CW + CW),
+// CW = 128 MG.  Units are ordered (f, cb, yb) and CTA c takes a contiguous
+// range of them, so consecutive units of a CTA mostly slide down TY rows and
+// need TY new input rows.
+//   warp 0 (lane 0), producer: input row segments (the CW columns of a row
+//     plus one wrapped pixel on each side, all C/8 chunk planes) into a ring
+//     of RING slots by cp.async.bulk, each completing on full[slot];
+//   warp 1 (lane 0), MMA issuer: for tap (dy, dx) the A operand of output row
+//     y0 + r, M-tile m, is slot(row y0 + r - 1 + dy) read from pixel
+//     m*128 + dx, so an M-tile never leaves its slot.  The TY * MG
+//     accumulators of a unit fill one of two TMEM stages of 256 columns.
+//     Descriptors are formed by integer adds on their start-address field, so
+//     issuing an MMA costs a few instructions.  tcgen05.commit marks the stage
+//     full and releases (empty[slot]) the input rows no later unit reads;
+//   warps 2..17, epilogue: tcgen05.ld of the stage, bias + activation (or the
+//     act' product), bf16 16-byte stores; then the stage is marked empty.
+// Loads of later rows, MMAs of the next unit and the epilogue of the current
+// one overlap.  Every output is the same sum in the same order (tap, then
+// K-step) as in the one-shot kernel, so both produce the same bits.  Every
+// wait is bounded and also stops once another role has given up (abort flag
+// in shared memory); before exit the CTA drains its in-flight copies and MMAs
+// and frees TMEM.
+constexpr int kPEpiWarps = 16;
+constexpr int kPThreads = 32 * (2 + kPEpiWarps);
+constexpr int kPStages = 2;
+constexpr int kPStageCols = 256;
+constexpr int kPMaxRing = 16;
+
+struct PShape {
+    int MG = 0, CW = 0, TY = 0, RING = 0;
+    uint32_t slot_bytes = 0;
+    size_t smem = 0;
+};
+
+static PShape p_shape(int n, int C) {
+    PShape s;
+    if (n < 128 || n % 128) return s;
+    // C = 64 keeps one M-tile per row so that a ring slot stays small
+    s.MG = (C >= 64 || n < 256) ? 1 : 2;
+    s.CW = 128 * s.MG;
+    s.TY = kPStageCols / (s.MG * C);
+    if (s.TY < 1 || n % s.TY) return PShape{};
+    s.slot_bytes = uint32_t(C / 8) * uint32_t(s.CW + 2) * 16u;
+    const size_t wbytes = size_t(9) * C * C * 2;
+    const size_t ctrl = 1024;
+    const size_t avail = size_t(227) * 1024 - wbytes - ctrl;
+    int ring = int(avail / s.slot_bytes);
+    if (ring > kPMaxRing) ring = kPMaxRing;
+    if (ring > 2 * s.TY + 2) ring = 2 * s.TY + 2;  // one unit of prefetch is enough
+    if (ring < s.TY + 2) return PShape{};
+    s.RING = ring;
+    s.smem = wbytes + size_t(ring) * s.slot_bytes + ctrl;
+    // more than half an SM's shared memory: at most one such CTA per SM, so
+    // the CTAs' TMEM stages (all 512 columns) never contend
+    if (s.smem < size_t(116) * 1024) s.smem = size_t(116) * 1024;
+    return s;
+}
+
+struct PCtl {
+    uint64_t full[kPMaxRing];
+    uint64_t empty[kPMaxRing];
+    uint64_t accf[kPStages];
+    uint64_t acce[kPStages];
+    uint64_t wbar;  // the weight copy
+    uint64_t fin;   // completion of every MMA the CTA issued
+    uint32_t tmem;
+    int abort;
+    alignas(16) float bias[64];
+};
+
+__device__ __forceinline__ bool p_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    for (long long i = 0; i < kTcSpin; ++i) {
+        if (tc::mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        __nanosleep(32);
+    }
+    *abort_flag = 1;
+    atomicExch(&g_tc_timeout, 3);
+    return false;
+}
+
+template <int C, int MG>
+__global__ void __launch_bounds__(kPThreads, 1)
+conv_hidden_tc_persistent(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ out,
+                          const __nv_bfloat16* __restrict__ wpk, const float* __restrict__ bias, int n,
+                          int batch, int RING, uint32_t slot_bytes, int act, int mode, float* __restrict__ zio) {
+    constexpr int KC = C / 8;
+    constexpr int TY = kPStageCols / (MG * C);
+    constexpr int NACC = TY * MG;
+    constexpr int CW = 128 * MG;
+    constexpr uint32_t WBYTES = 9u * C * C * 2u;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* w_tile = smem;
+    unsigned char* ring = smem + WBYTES;
+    PCtl* ctl = reinterpret_cast<PCtl*>(ring + size_t(RING) * slot_bytes);
+    volatile int* abort_flag = &ctl->abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int NB = n / CW;
+    const int NYB = n / TY;
+    const uint32_t plane_b = uint32_t(CW + 2) * 16u;
+    const size_t nn = size_t(n) * n;
+    const long long total = (long long)batch * NB * NYB;
+    const long long u0 = total * blockIdx.x / gridDim.x;
+    const long long u1 = total * (blockIdx.x + 1) / gridDim.x;
+
+    if (tid == 0) {
+        for (int i = 0; i < RING; ++i) {
+            tc::mbar_init(&ctl->full[i], 1);
+            tc::mbar_init(&ctl->empty[i], 1);
+        }
+        for (int i = 0; i < kPStages; ++i) {
+            tc::mbar_init(&ctl->accf[i], 1);
+            tc::mbar_init(&ctl->acce[i], kPEpiWarps);
+        }
+        tc::mbar_init(&ctl->wbar, 1);
+        tc::mbar_init(&ctl->fin, 1);
+        ctl->abort = 0;
+        tc::fence_mbar_init();
+    }
+    if (tid < C) ctl->bias[tid] = (mode == kFwd) ? bias[tid] : 0.f;
+    __syncthreads();
+    if (warp == 1) tc::tmem_alloc(&ctl->tmem, uint32_t(kPStages * kPStageCols));
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = ctl->tmem;
+
+    if (warp == 0 && lane == 0) {
+        // ---- producer
+        tc::mbar_arrive_expect_tx(&ctl->wbar, WBYTES);
+        tc::bulk_g2s(w_tile, wpk, WBYTES, &ctl->wbar);
+        long long s = 0;
+        bool ok = true;
+        for (long long u = u0; u < u1 && ok; ++u) {
+            const int yb = int(u % NYB);
+            const long long t = u / NYB;
+            const int cb = int(t % NB);
+            const long long f = t / NB;
+            const int y0 = yb * TY;
+            const bool start = (u == u0) || (yb == 0);
+            // input rows y0 - 1 .. y0 + TY (segment start) or y0 + 1 .. y0 + TY
+            for (int r = start ? -1 : 1; r <= TY && ok; ++r) {
+                int yin = y0 + r;
+                yin = yin < 0 ? yin + n : (yin >= n ? yin - n : yin);
+                const int slot = int(s % RING);
+                const long long k = s / RING;
+                if (k >= 1 && !p_wait(&ctl->empty[slot], uint32_t((k - 1) & 1), abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc::mbar_arrive_expect_tx(&ctl->full[slot], uint32_t(KC) * plane_b);
+                const int x0 = cb * CW;
+                const int xl = x0 == 0 ? n - 1 : x0 - 1;
+                const int xr = x0 + CW == n ? 0 : x0 + CW;
+                for (int kc = 0; kc < KC; ++kc) {
+                    const __nv_bfloat16* src = in + ((size_t(f) * KC + kc) * nn + size_t(yin) * n) * 8;
+                    unsigned char* dst = ring + size_t(slot) * slot_bytes + size_t(kc) * plane_b;
+                    tc::bulk_g2s(dst + 16, src + size_t(x0) * 8, uint32_t(CW) * 16u, &ctl->full[slot]);
+                    tc::bulk_g2s(dst, src + size_t(xl) * 8, 16u, &ctl->full[slot]);
+                    tc::bulk_g2s(dst + size_t(CW + 1) * 16, src + size_t(xr) * 8, 16u, &ctl->full[slot]);
+                }
+                ++s;
+            }
+        }
+        // drain: every issued copy lands before the CTA may exit
+        const long long first = s > RING ? s - RING : 0;
+        for (long long x = first; x < s; ++x)
+            tc::mbar_wait_bounded(&ctl->full[x % RING], uint32_t((x / RING) & 1), kTcSpin);
+        tc::mbar_wait_bounded(&ctl->wbar, 0, kTcSpin);
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        bool ok = p_wait(&ctl->wbar, 0, abort_flag);
+        const uint32_t idesc = tc::idesc_bf16_f32(128, C);
+        const uint64_t a_hi = tc::smem_desc(0, plane_b, 128);
+        const uint64_t b_hi = tc::smem_desc(0, C * 16, 128);
+        // start-address fields count 16-byte units; one pixel (8 channels) is one unit
+        const uint32_t ring_u = tc::smem_u32(ring) >> 4, w_u = tc::smem_u32(w_tile) >> 4;
+        const uint32_t slot_u = slot_bytes >> 4, plane_u = plane_b >> 4;
+        int a = 0, snext = 0;  // load index of the unit's first input row (a CTA's loads are few)
+        int i = 0;
+        for (long long u = u0; u < u1 && ok; ++u, ++i) {
+            const int yb = int(u % NYB);
+            const bool start = (u == u0) || (yb == 0);
+            if (start) {
+                a = snext;
+                snext += TY + 2;
+            } else {
+                a += TY;
+                snext += TY;
+            }
+            const int stage = i & 1;
+            const int kk = i >> 1;
+            if (kk >= 1 && !p_wait(&ctl->acce[stage], uint32_t((kk - 1) & 1), abort_flag)) break;
+            const int aslot = a % RING;
+            for (int d = 0; d < TY + 2 && ok; ++d)
+                ok = p_wait(&ctl->full[(a + d) % RING], uint32_t(((a + d) / RING) & 1), abort_flag);
+            if (!ok) break;
+            tc::fence_after_sync();
+            const uint32_t dbase = tmem + uint32_t(stage * kPStageCols);
+#pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap % 3;
+                // start of each output row's input row for this tap
+                uint32_t row_u[TY];
+#pragma unroll
+                for (int r = 0; r < TY; ++r) {
+                    int sl = aslot + r + dy;
+                    sl = sl >= RING ? sl - RING : sl;
+                    row_u[r] = ring_u + uint32_t(sl) * slot_u + uint32_t(dx);
+                }
+#pragma unroll
+                for (int ks = 0; ks < C / 16; ++ks) {
+                    const uint64_t bd = b_hi | uint64_t(w_u + uint32_t((tap * KC + 2 * ks) * C));
+#pragma unroll
+                    for (int acc = 0; acc < NACC; ++acc) {
+                        const int r = acc / MG, m = acc % MG;
+                        const uint64_t ad =
+                            a_hi | uint64_t(row_u[r] + uint32_t(2 * ks) * plane_u + uint32_t(m * 128));
+                        tc::mma_bf16(dbase + uint32_t(acc * C), ad, bd, idesc, (tap | ks) != 0);
+                    }
+                }
+            }
+            tc::mma_commit(&ctl->accf[stage]);
+            const bool cont = (u + 1 < u1) && (yb != NYB - 1);
+            const int nrel = cont ? TY : TY + 2;
+            for (int d = 0; d < nrel; ++d) tc::mma_commit(&ctl->empty[(a + d) % RING]);
+        }
+        // every MMA issued so far completes before TMEM is freed
+        tc::mma_commit(&ctl->fin);
+        tc::mbar_wait_bounded(&ctl->fin, 0, kTcSpin);
+    } else if (warp >= 2) {
+        // ---- epilogue: kPEpiWarps warps in kPEpiWarps / 4 groups; a warp
+        // reads TMEM lanes 32 (warp % 4) .. + 31 (positions of an M-tile) and
+        // its group's (accumulator, chunk) pairs j = grp, grp + NG, ...; the
+        // TMEM load of the next pair is in flight while the current one is
+        // stored.
+        constexpr int NG = kPEpiWarps / 4;
+        constexpr int NPAIRS = NACC * KC;
+        const int grp = (warp - 2) >> 2;
+        const int q = warp & 3;
+        const float4* bias4 = reinterpret_cast<const float4*>(ctl->bias);
+        int i = 0;
+        for (long long u = u0; u < u1; ++u, ++i) {
+            const int yb = int(u % NYB);
+            const long long t = u / NYB;
+            const int cb = int(t % NB);
+            const long long f = t / NB;
+            const int stage = i & 1;
+            if (!p_wait(&ctl->accf[stage], uint32_t((i >> 1) & 1), abort_flag)) break;
+            tc::fence_after_sync();
+            const size_t base =
+                (size_t(f) * KC * nn + size_t(yb * TY) * n + size_t(cb * CW + q * 32 + lane)) * 8;
+            const uint32_t trow = tmem + (uint32_t(q * 32) << 16) + uint32_t(stage * kPStageCols);
+            uint32_t v[8], w[8];
+            // pair j: accumulator j / KC (row r = acc / MG, M-tile m = acc % MG), chunk j % KC
+            if (grp < NPAIRS) tc::tmem_ld8(trow + uint32_t((grp / KC) * C + (grp % KC) * 8), v);
+            tc::tmem_wait_ld();
+            for (int j = grp; j < NPAIRS; j += NG) {
+                const int jn = j + NG;
+                if (jn < NPAIRS) tc::tmem_ld8(trow + uint32_t((jn / KC) * C + (jn % KC) * 8), w);
+                const int acc = j / KC, kc = j % KC;
+                const int r = acc / MG, m = acc % MG;
+                const size_t off = base + (size_t(kc) * nn + size_t(r) * n + size_t(m) * 128) * 8;
+                uint32_t packed[4];
+                if (mode == kFwd) {
+                    const float4 b0 = bias4[kc * 2], b1 = bias4[kc * 2 + 1];
+                    __align__(16) float z8[8] = {__uint_as_float(v[0]) + b0.x, __uint_as_float(v[1]) + b0.y,
+                                                 __uint_as_float(v[2]) + b0.z, __uint_as_float(v[3]) + b0.w,
+                                                 __uint_as_float(v[4]) + b1.x, __uint_as_float(v[5]) + b1.y,
+                                                 __uint_as_float(v[6]) + b1.z, __uint_as_float(v[7]) + b1.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(act_apply<float>(act, z8[2 * e]),
+                                                                       act_apply<float>(act, z8[2 * e + 1]));
+                        packed[e] = *reinterpret_cast<const uint32_t*>(&h);
+                    }
+                    if (zio) {
+                        reinterpret_cast<float4*>(zio + off)[0] = *reinterpret_cast<const float4*>(z8);
+                        reinterpret_cast<float4*>(zio + off)[1] = *reinterpret_cast<const float4*>(z8 + 4);
+                    }
+                } else {
+                    const float4 za = reinterpret_cast<const float4*>(zio + off)[0];
+                    const float4 zb = reinterpret_cast<const float4*>(zio + off)[1];
+                    const float zz[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const __nv_bfloat162 h =
+                            __floats2bfloat162_rn(__uint_as_float(v[2 * e]) * act_grad<float>(act, zz[2 * e]),
+                                                  __uint_as_float(v[2 * e + 1]) * act_grad<float>(act, zz[2 * e + 1]));
+                        packed[e] = *reinterpret_cast<const uint32_t*>(&h);
+                    }
+                }
+                *reinterpret_cast<uint4*>(out + off) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = w[e];
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&ctl->acce[stage]);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tmem, uint32_t(kPStages * kPStageCols));
+}
+
+static int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 1;
+    }
+    return sms;
+}
+
+template <int C, int MG>
+static int launch_persistent_mg(const PShape& s, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
+                                const __nv_bfloat16* w, const float* bias, int act, int mode, float* zio,
+                                cudaStream_t st) {
+    auto kern = conv_hidden_tc_persistent<C, MG>;
+    static bool configured = false;
+    if (!configured) {
+        ACPR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(227 * 1024)));
+        configured = true;
+    }
+    const long long units = (long long)batch * (n / s.CW) * (n / s.TY);
+    const int grid = int(units < num_sms() ? units : num_sms());
+    kern<<<grid, kPThreads, s.smem, st>>>(in, out, w, bias, n, batch, s.RING, s.slot_bytes, act, mode, zio);
+    ACPR_LAUNCH_CHECK();
+    return AC_OK;
+}
+
+template <int C>
+static int launch_persistent(const PShape& s, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
+                             const __nv_bfloat16* w, const float* bias, int act, int mode, float* zio,
+                             cudaStream_t st) {
+    if (s.MG == 1) return launch_persistent_mg<C, 1>(s, n, batch, in, out, w, bias, act, mode, zio, st);
+    if constexpr (C < 64) return launch_persistent_mg<C, 2>(s, n, batch, in, out, w, bias, act, mode, zio, st);
+    set_error("conv: no persistent kernel for C=%d, MG=%d", C, s.MG);
+    return AC_ERR_UNSUPPORTED;
+}
+
 template <int C>
 static int launch_hidden(int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out, const __nv_bfloat16* w,
                          const float* bias, int act, int mode, float* zio, cudaStream_t st) {
+    if (batch <= 0) return AC_OK;
+    const PShape ps = p_shape(n, C);
+    if (ps.RING) return launch_persistent<C>(ps, n, batch, in, out, w, bias, act, mode, zio, st);
     const TcShape s = pick_shape(n, C);
     if (s.TY == 0) return AC_ERR_UNSUPPORTED;
     auto kern = conv_hidden_tc_kernel<C>;

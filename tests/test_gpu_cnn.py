@@ -70,3 +70,34 @@ def test_cnn_deterministic():
     bb = G.cnn_coarse_step(net, u)
     assert torch.equal(a, bb)
     assert torch.equal(a[0], a[3])
+
+
+def test_cnn_bf16_partition_independent():
+    """The persistent tensor-core kernel (n >= 128) splits row blocks over
+    CTAs by the batch size; a field's result must not depend on the split."""
+    n, L, C = 256, 6, 32
+    w, b = I.cnn_weights(L, C, seed=4, sigma=0.05)
+    net = G.CoarseNet(L, C, w.astype(np.float32), b.astype(np.float32), act=1, precision=G.AC_F32)
+    u = torch.tensor(np.stack([I.random_field(n, seed=s) for s in range(5)]), dtype=torch.float32, device="cuda")
+    many = G.cnn_coarse_step(net, u)
+    for i in (0, 3):
+        assert torch.equal(G.cnn_coarse_step(net, u[i:i + 1].contiguous())[0], many[i])
+
+
+@pytest.mark.parametrize("n,L,C", [(128, 4, 32), (128, 3, 64), (512, 4, 16), (256, 3, 64), (256, 4, 32)])
+def test_cnn_bf16_persistent_shapes(n, L, C):
+    """Every persistent-kernel shape (one or two M-tiles per row, 2 to 8 rows
+    per work unit, one or two column blocks) against the oracle's
+    bf16-emulating mode, with weights large enough (sigma 0.05) that the
+    stack's output depends on its input."""
+    w, b = I.cnn_weights(L, C, seed=6, sigma=0.05)
+    u = np.stack([I.random_field(n, seed=s) for s in range(2)]).astype(np.float32)
+    w32, b32 = w.astype(np.float32), b.astype(np.float32)
+    net = G.CoarseNet(L, C, w32, b32, act=1, precision=G.AC_F32)
+    got = G.cnn_coarse_step(net, torch.tensor(u, device="cuda")).double().cpu().numpy()
+    ref = O.cnn_forward(O.CnnSpec(L, C, w32.astype(np.float64), b32.astype(np.float64), act=1, bf16=1),
+                        u.astype(np.float64))
+    err = np.abs(got - ref)
+    scale = max(np.abs(ref - u).max(), 1e-3)
+    assert err.max() < 2e-2 * scale + 1e-6
+    assert np.median(err) < 1e-3 * scale + 1e-7
