@@ -231,6 +231,20 @@ def run_uneven(args):
         "coarse_weights": "untrained N(0, 0.01^2)", "cuda_graphs": not args.no_graphs}), flush=True)
 
 
+# DRAM bytes (read + write) the fine kernel moved per field-slice in one ncu
+# capture of the 256^2 launch shape (512 fields x 20 steps: 134.3 MB read,
+# 87.7 MB written); a slice is read once and written once whatever its step
+# count, so a launch's traffic scales with the field-slices it processes.
+FINE_DRAM_BYTES_PER_FIELD_SLICE_256 = (134.330112e6 + 87.662080e6) / 512
+
+
+def fine_traffic_per_launch(st, wl):
+    if wl.n != 256 or not st.get("fine_launches"):
+        return None
+    slices = st["fine_cell_steps"] / (wl.n * wl.n * wl.steps)
+    return FINE_DRAM_BYTES_PER_FIELD_SLICE_256 * slices / st["fine_launches"]
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,7 +411,8 @@ def main():
             "conv_tflops": conv_tflops,
             "roofline": {"bound": "alu", "kernel": "fine_field_kernel", "achieved": fine_tflops,
                          "peak": peak, "unit": "TFLOP/s", "frac": fine_tflops / peak,
-                         "traffic": None,
+                         "traffic": fine_traffic_per_launch(st, WL),
+                         "traffic_unit": "bytes per launch (ncu DRAM bytes per field-slice x field-slices per launch)",
                          "peak_source": f"FP32 lanes x 2 x sm_max_mhz {sm_mhz:.0f} from {src} peaks",
                          "flops_per_cell_step": fpc},
             "cpu_baseline": cpu,

@@ -98,7 +98,10 @@ typedef struct {
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* ac_last_error(void);
 
-/* 1 if the fine-step kernels are built for this (n, precision), else 0. */
+/* 1 if the fine-step kernels are built for this (n, precision), else 0:
+ * n = 8 .. 512 (float32) and 8 .. 256 (float64) on one thread-block cluster
+ * per field; n = 1024 float32 through two passes per step over L2/HBM (fine
+ * step and slice propagation only, not the adjoint or trajectory modes). */
 int ac_fine_supported(int n, int precision);
 
 /* Launch shapes of the fine kernel built for (n, precision) -- cluster size,
@@ -127,7 +130,8 @@ int ac_fine_step(const ac_params* params, int batch, const void* u_in, void* u_o
 /* The fine propagator F(t_n, t_{n+1}, U_n) of Eq. (fine_operator): for every
  * one of `num_fields` independent fields, `steps_per_slice` fine steps
  * (Algorithm 2: the parallel fine solves of all slices).  The field stays on
- * chip for all steps; HBM is touched once on entry and once on exit.  In the
+ * chip for all steps (n <= 512; at n = 1024 each step is two passes through
+ * L2/HBM); HBM is touched once on entry and once on exit.  In the
  * mass-conserving variant the spectrum's mean mode is held at the field's
  * float64 mean taken on entry, so mass is conserved to rounding.
  * u_starts, u_ends: device [num_fields][n][n]; they may not overlap. */
