@@ -77,15 +77,22 @@ __global__ void conv_f64_kernel(const double* __restrict__ in, double* __restric
 
 // ------------------------------------------------------------ bf16 / f32 --
 // First layer: float32 field -> bf16 chunked activations (K = 9 on CUDA cores).
+// The bf16-rounded weights and the biases are staged in shared memory once per
+// block (every thread reads the same entry: broadcast).
 template <int C>
 __global__ void conv_first_bf16_kernel(const float* __restrict__ u, __nv_bfloat16* __restrict__ act,
                                        const float* __restrict__ W, const float* __restrict__ bias,
                                        int batch, int n, int act_kind, BatchIO io) {
+    __shared__ float ws[C * 9], bs[C];
+    for (int i = threadIdx.x; i < C * 9; i += blockDim.x) ws[i] = bf16r(W[i]);
+    for (int i = threadIdx.x; i < C; i += blockDim.x) bs[i] = bias[i];
+    __syncthreads();
     const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nn = (long long)n * n;
     if (pix >= nn * batch) return;
-    const int b = int(pix / nn);
-    const int y = int((pix % nn) / n), x = int(pix % n);
+    const int lg = __ffs(n) - 1;  // n is a power of two
+    const int b = int(pix >> (2 * lg));
+    const int y = int(pix >> lg) & (n - 1), x = int(pix) & (n - 1);
     const float* f = u + bsel(io.in_map, b) * io.in_bs;
     float v[9];
 #pragma unroll
@@ -100,11 +107,11 @@ __global__ void conv_first_bf16_kernel(const float* __restrict__ u, __nv_bfloat1
             const int o = kc * 8 + i;
             float s = 0.f;
 #pragma unroll
-            for (int t = 0; t < 9; ++t) s = fmaf(bf16r(W[o * 9 + t]), v[t], s);
-            s += bias[o];
+            for (int t = 0; t < 9; ++t) s = fmaf(ws[o * 9 + t], v[t], s);
+            s += bs[o];
             o8[i] = __float2bfloat16_rn(act_apply<float>(act_kind, s));
         }
-        *reinterpret_cast<uint4*>(act + ((((long long)b * (C / 8) + kc) * nn) + pix % nn) * 8) =
+        *reinterpret_cast<uint4*>(act + ((((long long)b * (C / 8) + kc) * nn) + (pix & (nn - 1))) * 8) =
             *reinterpret_cast<const uint4*>(o8);
     }
 }
@@ -153,51 +160,93 @@ __global__ void conv_hidden_bf16_cc_kernel(const __nv_bfloat16* __restrict__ in,
     }
 }
 
-// Last layer C -> 1 with the residual add in float32.
-template <int C>
+// Last layer C -> 1 with the residual add in float32.  A block covers
+// ppb = last_pixels(n) consecutive pixels of one field: nr = ppb / w rows of
+// w = min(n, 256) columns starting at (y0, x0).  It first stages the input
+// rows y0 - 1 .. y0 + nr (wrapped) over columns x0 - 1 .. x0 + w (wrapped), all
+// C/8 chunk planes, and the bf16-rounded weights in shared memory, then one
+// thread per pixel sums over (chunk, tap, channel) in that order.
 // With zpart != NULL every block also writes the float64 sum of its stack
-// outputs z (before the residual) to zpart[blockIdx.x]; a block never spans
-// two fields (blockDim.x divides n^2).
-__global__ void conv_last_bf16_kernel(const __nv_bfloat16* __restrict__ in, float* __restrict__ out,
-                                      const float* __restrict__ W, const float* __restrict__ bias,
-                                      const float* __restrict__ u, int batch, int n, int residual,
-                                      BatchIO io, double* __restrict__ zpart) {
-    const long long pix0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// outputs z (before the residual) to zpart[blockIdx.x], one warp adding the
+// block's values in a fixed order (float64 arithmetic is scarce on this GPU:
+// about one add per pixel, not one per thread and shuffle step).
+constexpr int kLastThreads = 256;
+template <int C>
+__global__ void __launch_bounds__(kLastThreads)
+conv_last_bf16_kernel(const __nv_bfloat16* __restrict__ in, float* __restrict__ out, const float* __restrict__ W,
+                      const float* __restrict__ bias, const float* __restrict__ u, int batch, int n, int residual,
+                      BatchIO io, double* __restrict__ zpart) {
+    constexpr int KC = C / 8;
+    extern __shared__ __align__(16) unsigned char lsm[];
+    float* ws = reinterpret_cast<float*>(lsm);                       // [kc][tap][8]
+    float* zsh = ws + C * 9;                                          // [ppb]
+    uint4* tile = reinterpret_cast<uint4*>(zsh + kLastThreads);       // [nr + 2][KC][w + 2]
     const long long nn = (long long)n * n;
-    const bool valid = pix0 < nn * batch;
-    const long long pix = valid ? pix0 : 0;
-    const int b = int(pix / nn);
-    const int y = int((pix % nn) / n), x = int(pix % n);
-    const long long fi = bsel(io.in_map, b), fo = bsel(io.out_map, b);
-    float acc = 0.f;
-    for (int kc = 0; kc < C / 8; ++kc) {
-        const __nv_bfloat16* plane = in + ((long long)b * (C / 8) + kc) * nn * 8;
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const int yy = wrap(y + t / 3 - 1, n), xx = wrap(x + t % 3 - 1, n);
-            const uint4 raw = *reinterpret_cast<const uint4*>(plane + ((long long)yy * n + xx) * 8);
-            const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&raw);
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                acc = fmaf(bf16r(__ldg(W + ((kc * 8 + i) * 9 + t))), __bfloat162float(v8[i]), acc);
+    const int ppb = int(nn < kLastThreads ? nn : kLastThreads);
+    const int w = n < kLastThreads ? n : kLastThreads;
+    const int nr = ppb / w;
+    const long long p0 = (long long)blockIdx.x * ppb;
+    const int b = int(p0 / nn);
+    const int q0 = int(p0 % nn);
+    const int y0 = q0 / n, x0 = q0 % n;
+    for (int i = threadIdx.x; i < C * 9; i += blockDim.x) {
+        const int e = i % 8, t = (i / 8) % 9, kc = i / 72;
+        ws[i] = bf16r(W[(kc * 8 + e) * 9 + t]);
+    }
+    const __nv_bfloat16* ib = in + (long long)b * KC * nn * 8;
+    const int tw = w + 2;
+    for (int r = 0; r < nr + 2; ++r) {
+        const int yy = wrap(y0 - 1 + r, n);
+        for (int kc = 0; kc < KC; ++kc) {
+            const uint4* src = reinterpret_cast<const uint4*>(ib + ((long long)kc * nn + (long long)yy * n) * 8);
+            uint4* dst = tile + (r * KC + kc) * tw;
+            for (int xx = threadIdx.x; xx < tw; xx += blockDim.x) dst[xx] = src[wrap(x0 - 1 + xx, n)];
         }
     }
-    const float zs = acc + bias[0];
-    float z = zs;
-    if (residual) z += u[fi * io.in_bs + pix % nn];
-    if (valid) out[fo * io.out_bs + pix % nn] = z;
+    __syncthreads();
+    const int tp = threadIdx.x;
+    const bool valid = tp < ppb;
+    float zs = 0.f;
+    if (valid) {
+        const int ry = tp / w, cx = tp % w;
+        float acc = 0.f;
+        for (int kc = 0; kc < KC; ++kc) {
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const uint4 raw = tile[((ry + t / 3) * KC + kc) * tw + cx + t % 3];
+                const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&raw);
+                const float4 w0 = reinterpret_cast<const float4*>(ws)[(kc * 9 + t) * 2];
+                const float4 w1 = reinterpret_cast<const float4*>(ws)[(kc * 9 + t) * 2 + 1];
+                const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                for (int e = 0; e < 8; ++e) acc = fmaf(wv[e], __bfloat162float(v8[e]), acc);
+            }
+        }
+        zs = acc + bias[0];
+        const long long q = (long long)(y0 + ry) * n + x0 + cx;
+        float z = zs;
+        if (residual) z += u[bsel(io.in_map, b) * io.in_bs + q];
+        out[bsel(io.out_map, b) * io.out_bs + q] = z;
+    }
     if (zpart) {
-        double v = valid ? double(zs) : 0.0;
-        __shared__ double red[32];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        zsh[tp] = valid ? zs : 0.f;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < int((blockDim.x + 31) >> 5); ++w) t += red[w];
-            zpart[blockIdx.x] = t;
+        if (tp < 32) {
+            double v = 0.0;
+            for (int i = tp; i < ppb; i += 32) v += double(zsh[i]);
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (tp == 0) zpart[blockIdx.x] = v;
         }
     }
+}
+
+template <int C>
+static size_t last_smem(int n) {
+    const long long nn = (long long)n * n;
+    const int ppb = int(nn < kLastThreads ? nn : kLastThreads);
+    const int w = n < kLastThreads ? n : kLastThreads;
+    const int nr = ppb / w;
+    return sizeof(float) * (C * 9 + kLastThreads) + sizeof(uint4) * size_t(nr + 2) * (C / 8) * (w + 2);
 }
 
 // mACNN mass shift from the stack-output sums: out += -(sum z) / n^2 per
@@ -276,11 +325,13 @@ int check_cnn(const cnn_desc* d) {
     return AC_OK;
 }
 
-static int last_threads(int n) { return n * n >= 128 ? 128 : n * n; }
+// Pixels per block of the last layer (a power of two dividing n^2, so a block
+// never spans two fields).
+static int last_pixels(int n) { return n * n >= kLastThreads ? kLastThreads : n * n; }
 
 size_t work_bytes_for(const cnn_desc* d, int n, int batch) {
     const size_t act = size_t(batch) * d->channels * n * n * (d->precision == AC_F64 ? 8 : 2);
-    const size_t zpart = size_t(batch) * (size_t(n) * n / last_threads(n)) * sizeof(double);
+    const size_t zpart = size_t(batch) * (size_t(n) * n / last_pixels(n)) * sizeof(double);
     return 2 * act + zpart;
 }
 
@@ -289,14 +340,21 @@ template <int C>
 static int last_layer_f32(const cnn_desc* d, int n, int batch, const __nv_bfloat16* a, float* out,
                           const float* W, const float* Bv, const float* u, const BatchIO& io, double* zpart,
                           cudaStream_t st) {
-    const int threads = last_threads(n);
+    const int ppb = last_pixels(n);
     const long long pixels = (long long)n * n * batch;
-    const unsigned blocks = unsigned((pixels + threads - 1) / threads);
-    conv_last_bf16_kernel<C><<<blocks, threads, 0, st>>>(a, out, W, Bv, u, batch, n, d->residual, io,
-                                                         d->mass_fix ? zpart : nullptr);
+    const unsigned blocks = unsigned(pixels / ppb);
+    const size_t smem = last_smem<C>(n);
+    static bool configured = false;
+    if (!configured) {
+        ACPR_CUDA(cudaFuncSetAttribute(conv_last_bf16_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(last_smem<C>(256))));
+        configured = true;
+    }
+    conv_last_bf16_kernel<C><<<blocks, kLastThreads, smem, st>>>(a, out, W, Bv, u, batch, n, d->residual, io,
+                                                                 d->mass_fix ? zpart : nullptr);
     ACPR_LAUNCH_CHECK();
     if (d->mass_fix) {
-        const int bpf = int((long long)n * n / threads);
+        const int bpf = int((long long)n * n / ppb);
         const long long chunks = ((long long)n * n + kMassThreads * 8 - 1) / (kMassThreads * 8);
         mass_apply_kernel<<<dim3(unsigned(chunks), unsigned(batch)), kMassThreads, 0, st>>>(out, zpart, bpf, n, io);
         ACPR_LAUNCH_CHECK();

@@ -54,7 +54,7 @@ static TrainLayout train_layout(const cnn_desc* d, int n, int batch) {
     t.off_part = (t.off_wt + wt + 255) / 256 * 256;
     t.off_gc = t.off_part + size_t(kChunks) * 9 * (size_t(d->channels) * d->channels + d->channels) * 4;
     t.off_zpart = t.off_gc + size_t(batch) * n * n * 4;
-    t.total = t.off_zpart + size_t(batch) * n * n * sizeof(double);  // >= batch * n^2/128 partials
+    t.total = t.off_zpart + size_t(batch) * n * n * sizeof(double);  // >= the last layer's block partials
     return t;
 }
 

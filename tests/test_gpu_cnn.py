@@ -101,3 +101,30 @@ def test_cnn_bf16_persistent_shapes(n, L, C):
     scale = max(np.abs(ref - u).max(), 1e-3)
     assert err.max() < 2e-2 * scale + 1e-6
     assert np.median(err) < 1e-3 * scale + 1e-7
+
+
+def test_gelu_activation_error_bound():
+    """float32 GELU x Phi(x) with Phi from Abramowitz & Stegun 7.1.26 (error
+    <= 1.5e-7 in erfc).  A 1 -> 16 -> 1 stack without residual whose first
+    layer copies bf16(u) into channel 0 and whose last layer reads channel 0
+    back gives out = bf16(GELU(bf16(u))).  It must be the correctly rounded
+    bf16 of the exact GELU, or a neighbouring bf16 value where the exact value
+    lies within the approximation's error of a rounding midpoint."""
+    from math import erf, sqrt
+    n, L, C = 64, 2, 16
+    w = np.zeros(C * 9 + C * 9)
+    w[4] = 1.0                      # layer 1, out channel 0, centre tap
+    w[C * 9 + 4] = 1.0              # layer 2, in channel 0, centre tap
+    b = np.zeros(C + 1)
+    net = G.CoarseNet(L, C, w.astype(np.float32), b.astype(np.float32), act=1, precision=G.AC_F32, residual=0)
+    u = np.linspace(-7.0, 5.0, n * n).reshape(1, n, n).astype(np.float32)
+    got = G.cnn_coarse_step(net, torch.tensor(u, device="cuda")).cpu().numpy().astype(np.float64)
+    ub = torch.tensor(u).to(torch.bfloat16).double().numpy()
+    exact = np.vectorize(lambda x: 0.5 * x * (1.0 + erf(x / sqrt(2.0))))(ub)
+    ref = torch.tensor(exact).to(torch.bfloat16).double().numpy()
+    ulp = np.maximum(np.abs(ref), 1e-30) * 2.0 ** -7
+    err = np.abs(got - ref)
+    exact_hit = err <= 1e-7 + 1e-6 * np.abs(ref)
+    assert np.all(exact_hit | (err <= ulp * 1.01))
+    # one-step flips are rare (about 1% of this ramp, measured)
+    assert np.mean(exact_hit) > 0.98
