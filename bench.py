@@ -231,6 +231,44 @@ def run_uneven(args):
         "coarse_weights": "untrained N(0, 0.01^2)", "cuda_graphs": not args.no_graphs}), flush=True)
 
 
+def run_train(args):
+    """The differentiation workload: training iterations of the 1 -> 64 x 8
+    GELU bf16 coarse net on 256^2 fields -- a 4-step unrolled MSE against fine
+    trajectories with 100 fine steps between snapshots, backward through the
+    chain, Adam -- with batches of 16 windows drawn from 512 trajectories of
+    the classic model (eps = 0.01, dt = 5e-5, S = 2) from seeded U(-0.9, 0.9)
+    initial data.  Prints one JSON line (not the benchmark line)."""
+    import torch
+    import paper_2510_07672_gb300 as G
+    from paper_2510_07672_gb300.train import make_trajectories, train_coarse
+    n, C, L, unroll, batch, R, snaps = 256, 64, 8, 4, 16, 512, 6
+    fp = G.FineParams(n, 0.01, 2.0, 5e-5, variant=G.AC_CLASSIC, precision=G.AC_F32)
+    ics = torch.tensor(np.stack([I.random_field(n, seed=s) for s in range(R)]), dtype=torch.float32,
+                       device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    traj = make_trajectories(fp, ics, snaps, 100)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    w, b = I.cnn_weights(L, C, seed=0)
+    net = G.TrainableCoarseNet(L, C, w.astype(np.float32), b.astype(np.float32), act=G.AC_ACT_GELU)
+    train_coarse(net, traj, max(args.warmup, 1), batch, unroll, 1e-3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = train_coarse(net, traj, args.steps, batch, unroll, 1e-3, seed=1)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    fwd = batch * unroll * n * n * 2 * 9 * (C + (L - 2) * C * C + C)
+    print(json.dumps({
+        "metric": "coarse-net training iteration (4-step unrolled MSE, backward, Adam)",
+        "workload": "train-c64l8-gelu-bf16-256sq-b16-u4", "ms_per_iteration": ms,
+        "windows_per_s": batch / (ms * 1e-3), "tflops_est": 3 * fwd / (ms * 1e-3) / 1e12,
+        "flops_note": "3 x forward conv flops (forward, input and weight gradients)",
+        "trajectories": R, "snapshots": snaps, "trajectory_generation_s": gen_s,
+        "loss_first": losses[0], "loss_last": losses[-1], "steps": args.steps, "warmup": args.warmup,
+        "timing": "wall clock per iteration, one host read of the loss per iteration included"}), flush=True)
+
+
 # DRAM bytes (read + write) the fine kernel moved per field-slice in one ncu
 # capture of the 256^2 launch shape (512 fields x 20 steps: 134.3 MB read,
 # 87.7 MB written); a slice is read once and written once whatever its step
@@ -253,8 +291,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--weights", default="trained", help="'trained' (the committed G), 'untrained', or a .npz path")
-    ap.add_argument("--workload", default="mass256", choices=["mass256", "uneven"],
-                    help="mass256: the benchmark line; uneven: 64 classic problems of uneven size (batching)")
+    ap.add_argument("--workload", default="mass256", choices=["mass256", "uneven", "train"],
+                    help="mass256: the benchmark line; uneven: 64 classic problems of uneven size (batching); "
+                         "train: coarse-net training iterations (C = 64, 8 layers)")
     ap.add_argument("--no-graphs", action="store_true")
     args = ap.parse_args()
 
@@ -266,6 +305,9 @@ def main():
         return
     if args.workload == "uneven":
         run_uneven(args)
+        return
+    if args.workload == "train":
+        run_train(args)
         return
 
     # host-side oracle sample first (before any GPU work in this process)

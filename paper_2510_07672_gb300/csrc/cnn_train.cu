@@ -176,6 +176,27 @@ __global__ void first_dgrad_kernel(const float* __restrict__ g, const __nv_bfloa
 // dz: bf16 chunked, or (COUT == 1) the float32 output gradient rounded to bf16.
 // Block rows of 64 pixels are staged in shared memory; thread (o, c-group)
 // accumulates a strip of input channels.
+// Each thread owns a TO x TC block of (output, input) channel pairs and, per
+// staged pixel, reads TO dz values and TC activations (vector loads) for its
+// TO * TC fused multiply-adds; every pair still sums its pixels in order.
+template <int PER> struct WgTile;
+template <> struct WgTile<1> { static constexpr int TO = 1, TC = 1; };
+template <> struct WgTile<4> { static constexpr int TO = 2, TC = 2; };
+template <> struct WgTile<16> { static constexpr int TO = 4, TC = 4; };
+
+template <int K>
+__device__ __forceinline__ void lds_vec(const float* p, float (&v)[K]) {
+    if constexpr (K == 4) {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else if constexpr (K == 2) {
+        const float2 t = *reinterpret_cast<const float2*>(p);
+        v[0] = t.x; v[1] = t.y;
+    } else {
+        v[0] = *p;
+    }
+}
+
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(kWgThreads)
 wgrad_kernel(const void* __restrict__ a_src, const void* __restrict__ dz_src, float* __restrict__ part,
@@ -183,20 +204,30 @@ wgrad_kernel(const void* __restrict__ a_src, const void* __restrict__ dz_src, fl
     constexpr int TP = 64;                       // pixels per staged strip
     constexpr int PAIRS = CIN * COUT;
     constexpr int PER = (PAIRS + kWgThreads - 1) / kWgThreads;
-    __shared__ float s_a[TP][CIN + 1];
-    __shared__ float s_dz[TP][COUT + 1];
+    constexpr int TO = WgTile<PER>::TO, TC = WgTile<PER>::TC;
+    constexpr int NCB = CIN / TC;                // input-channel blocks
+    constexpr int NTH = (COUT / TO) * NCB;       // threads that own pairs
+    constexpr int PA = CIN >= 4 ? CIN + 4 : CIN + 1;    // row pitches (16-byte rows for vector loads)
+    constexpr int PD = COUT >= 4 ? COUT + 4 : COUT + 1;
+    __shared__ __align__(16) float s_a[TP][PA];
+    __shared__ __align__(16) float s_dz[TP][PD];
     const int tap = blockIdx.x % 9;
     const int chunk = blockIdx.x / 9;
     const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const int lg = __ffs(n) - 1;                 // n is a power of two
     const long long nn = (long long)n * n;
     const long long total = nn * batch;
     const long long per_chunk = (total + kChunks - 1) / kChunks;
     const long long p0 = chunk * per_chunk;
     const long long p1 = p0 + per_chunk < total ? p0 + per_chunk : total;
-    float acc[PER];
+    const int ob = threadIdx.x / NCB, cb = threadIdx.x % NCB;
+    const bool owner = threadIdx.x < NTH;
+    float acc[TO][TC];
     float bacc = 0.f;
 #pragma unroll
-    for (int k = 0; k < PER; ++k) acc[k] = 0.f;
+    for (int i = 0; i < TO; ++i)
+#pragma unroll
+        for (int k = 0; k < TC; ++k) acc[i][k] = 0.f;
     for (long long base = p0; base < p1; base += TP) {
         __syncthreads();
         for (int idx = threadIdx.x; idx < TP * CIN; idx += kWgThreads) {
@@ -204,8 +235,8 @@ wgrad_kernel(const void* __restrict__ a_src, const void* __restrict__ dz_src, fl
             const long long p = base + pi;
             float v = 0.f;
             if (p < p1) {
-                const int b = int(p / nn);
-                const int y = wrapi(int((p % nn) / n) + dy, n), x = wrapi(int(p % n) + dx, n);
+                const int b = int(p >> (2 * lg));
+                const int y = wrapi((int(p >> lg) & (n - 1)) + dy, n), x = wrapi((int(p) & (n - 1)) + dx, n);
                 const long long q = (long long)y * n + x;
                 if constexpr (CIN == 1) {
                     v = bf16r(static_cast<const float*>(a_src)[(long long)b * nn + q]);
@@ -221,8 +252,8 @@ wgrad_kernel(const void* __restrict__ a_src, const void* __restrict__ dz_src, fl
             const long long p = base + pi;
             float v = 0.f;
             if (p < p1) {
-                const int b = int(p / nn);
-                const long long q = p % nn;
+                const int b = int(p >> (2 * lg));
+                const long long q = p & (nn - 1);
                 if constexpr (COUT == 1) {
                     v = bf16r(static_cast<const float*>(dz_src)[(long long)b * nn + q]);
                 } else {
@@ -233,28 +264,30 @@ wgrad_kernel(const void* __restrict__ a_src, const void* __restrict__ dz_src, fl
             s_dz[pi][o] = v;
         }
         __syncthreads();
+        if (owner) {
+#pragma unroll 4
+            for (int pi = 0; pi < TP; ++pi) {
+                float dv[TO], av[TC];
+                lds_vec<TO>(&s_dz[pi][ob * TO], dv);
+                lds_vec<TC>(&s_a[pi][cb * TC], av);
 #pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int pr = threadIdx.x + k * kWgThreads;
-            if (pr < PAIRS) {
-                const int o = pr / CIN, c = pr % CIN;
-                float s = acc[k];
-                for (int pi = 0; pi < TP; ++pi) s = fmaf(s_dz[pi][o], s_a[pi][c], s);
-                acc[k] = s;
+                for (int i = 0; i < TO; ++i)
+#pragma unroll
+                    for (int k = 0; k < TC; ++k) acc[i][k] = fmaf(dv[i], av[k], acc[i][k]);
             }
         }
         if (tap == 0 && threadIdx.x < COUT)
             for (int pi = 0; pi < TP; ++pi) bacc += s_dz[pi][threadIdx.x];
     }
     float* out = part + ((long long)chunk * 9 + tap) * (C * C + C);
+    if (owner) {
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int pr = threadIdx.x + k * kWgThreads;
-        if (pr < PAIRS) out[pr] = acc[k];
+        for (int i = 0; i < TO; ++i)
+#pragma unroll
+            for (int k = 0; k < TC; ++k) out[(ob * TO + i) * CIN + cb * TC + k] = acc[i][k];
     }
     if (tap == 0 && threadIdx.x < COUT) out[C * C + threadIdx.x] = bacc;
 }
-
 // Fixed-order sum of the chunk partials into the float32 gradients
 // (W[o][c][tap] layout of the masters; overwrite or accumulate).
 __global__ void wgrad_reduce_kernel(const float* __restrict__ part, float* __restrict__ gw, float* __restrict__ gb,
