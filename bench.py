@@ -298,6 +298,26 @@ def run_train(args):
 FINE_DRAM_BYTES_PER_FIELD_SLICE_256 = (134.330112e6 + 87.662080e6) / 512
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over the ranks (a job's time is its slowest rank's); every
+    rank gets it.  device: where the reduction tensor lives (cuda for NCCL,
+    cpu for gloo)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(cells_per_rank: float, ms: float, world: int) -> float:
+    """Whole-job throughput of `world` replicas that each deliver
+    cells_per_rank in a step, over the slowest rank's step time (weak
+    scaling: the work per GPU is fixed)."""
+    return world * cells_per_rank / (ms * 1e-3)
+
+
 def cost_model(st, seq_ms, its, steps):
     """The cost model of Sec. 3.4 with the measured unit costs: t_num = one
     fine step of one slice (all problems), from the sequential solve; t_nn =
@@ -418,16 +438,12 @@ def main():
         e1.record(stream)
         barrier()
     launches = G.ac_launch_count() - n_launch0
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
     st = pr.stats()
     clocks = clk.summary()
 
     cells = WL.problems * WL.slices * WL.steps * WL.n * WL.n  # delivered per solve per rank
-    value = world * cells / (ms * 1e-3)
+    value = job_rate(cells, ms, world)
 
     # sequential float32 fine solve of the same problems, same kernel
     seq_in = u0.clone()
@@ -469,11 +485,7 @@ def main():
     for _ in range(args.steps):
         e2e_step()
     barrier()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, world, dev)
 
     if rank == 0:
         peaks, src = measured_peaks()
@@ -508,7 +520,7 @@ def main():
             "cpu_baseline": cpu,
             "cpu_baseline_1core": cpu1,
             "cost_model": cost_model(st, seq_ms, its, args.steps),
-            "e2e": {"value": world * cells / (e2e_ms * 1e-3), "unit": UNIT,
+            "e2e": {"value": job_rate(cells, e2e_ms, world), "unit": UNIT,
                     "h2d_bytes_per_step": int(host_u0.numel() * 4), "d2h_bytes_per_step": int(host_out.numel() * 4)},
             "gpu_launches": int(launches),
             "clocks": clocks,
