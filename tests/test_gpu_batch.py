@@ -1,4 +1,4 @@
-"""GPU tests of batching (SURVEY a7): problems of uneven slice counts and
+"""GPU tests of batching: problems of uneven slice counts and
 steps in one handle, CUDA-graph replay of the iterations, several grid sizes
 solved together on separate streams, and the fine-kernel autotuner.
 
