@@ -291,6 +291,43 @@ def run_train(args):
         "timing": "wall clock per iteration, one host read of the loss per iteration included"}), flush=True)
 
 
+def run_adjoint(args):
+    """The adjoint workload: dE_h(u^2000)/du^0 of one 256^2 classic field
+    (eps = 0.01, dt = 5e-5, S = 2) by the checkpointed adjoint (a checkpoint
+    every 32 steps), float32 and float64, against the 2000-step forward solve
+    of the same field.  Prints one JSON line (not the benchmark line)."""
+    import torch
+    import paper_2510_07672_gb300 as G
+    n, steps, every = 256, 2000, 32
+    out = {"metric": "energy gradient through 2000 fine steps (checkpointed adjoint)",
+           "workload": "adjoint-256sq-2000-steps-ckpt32", "steps": args.steps, "warmup": args.warmup}
+    for prec, dt_, name in ((G.AC_F32, torch.float32, "f32"), (G.AC_F64, torch.float64, "f64")):
+        fp = G.FineParams(n, 0.01, 2.0, 5e-5, variant=G.AC_CLASSIC, precision=prec)
+        u0 = torch.tensor(I.random_field(n, seed=0)[None], dtype=dt_, device="cuda")
+        fwd_out = torch.empty_like(u0)
+
+        def timed(fn):
+            for _ in range(max(args.warmup, 1)):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / args.steps
+
+        fwd_ms = timed(lambda: G.ac_fine_propagate_slices(fp, steps, u0, fwd_out))
+        grad_ms = timed(lambda: G.ac_energy_gradient_ic(fp, steps, u0, checkpoint_every=every))
+        out[name] = {"forward_ms": fwd_ms, "gradient_ms": grad_ms, "ratio": grad_ms / fwd_ms,
+                     "forward_cell_steps_per_s": steps * n * n / (fwd_ms * 1e-3)}
+    out["note"] = ("one field per call (the entry point's shape): one 8-CTA cluster of the GPU's 152 SMs "
+                   "works; the gradient runs the forward pass, a recompute of each segment and the adjoint "
+                   "steps, about 3x the forward work")
+    print(json.dumps(out), flush=True)
+
+
 # DRAM bytes (read + write) the fine kernel moved per field-slice in one ncu
 # capture of the 256^2 launch shape (512 fields x 20 steps: 134.3 MB read,
 # 87.7 MB written); a slice is read once and written once whatever its step
@@ -353,9 +390,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--weights", default="trained", help="'trained' (the committed G), 'untrained', or a .npz path")
-    ap.add_argument("--workload", default="mass256", choices=["mass256", "uneven", "train"],
+    ap.add_argument("--workload", default="mass256", choices=["mass256", "uneven", "train", "adjoint"],
                     help="mass256: the benchmark line; uneven: 64 classic problems of uneven size (batching); "
-                         "train: coarse-net training iterations (C = 64, 8 layers)")
+                         "train: coarse-net training iterations (C = 64, 8 layers); "
+                         "adjoint: checkpointed energy gradient through 2000 steps")
     ap.add_argument("--no-graphs", action="store_true")
     args = ap.parse_args()
 
@@ -370,6 +408,9 @@ def main():
         return
     if args.workload == "train":
         run_train(args)
+        return
+    if args.workload == "adjoint":
+        run_adjoint(args)
         return
 
     # host-side oracle sample first (before any GPU work in this process)
