@@ -79,6 +79,8 @@ struct BigArgs {
     void* Z;          // [fields][N/2][N] complex
     void* V;          // [fields][N][N/2] complex
     const double* mean;  // [fields] entry means (mass-conserving)
+    const void* tw;   // [N] exp(-2 pi i k / N), float64-rounded once per call
+    const void* lam;  // [N] dt eps^2 (4/h^2) sin^2(pi k / N)
     int mass;
     double a, dt, lam_scale;
 };
@@ -103,12 +105,7 @@ big_rows_kernel(BigArgs args, int mode) {
     const int blocks_per_field = HALF / kBigWarps;
     const int f = blockIdx.x / blocks_per_field;
     const int p = (blockIdx.x % blocks_per_field) * kBigWarps + w;  // row pair: rows 2p, 2p+1
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        double sn, cs;
-        sincospi(-2.0 * double(k) / N, &sn, &cs);
-        tw[k].x = T(cs);
-        tw[k].y = T(sn);
-    }
+    for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = static_cast<const V2*>(args.tw)[k];
     __syncthreads();
     V2* buf = bufs + w * PB;
     const size_t NN = size_t(N) * N;
@@ -182,12 +179,8 @@ big_cols_kernel(BigArgs args) {
     const int c0 = (blockIdx.x % blocks_per_field) * kBigWarps;
     const int col = c0 + w;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        double sn, cs;
-        sincospi(-2.0 * double(k) / N, &sn, &cs);
-        tw[k].x = T(cs);
-        tw[k].y = T(sn);
-        const double s = sinpi(double(k) / N);
-        lam[k] = T(args.lam_scale * s * s);
+        tw[k] = static_cast<const V2*>(args.tw)[k];
+        lam[k] = static_cast<const T*>(args.lam)[k];
     }
     __syncthreads();
     V2* buf = bufs + w * PB;
@@ -195,13 +188,26 @@ big_cols_kernel(BigArgs args) {
     const V2* Z = static_cast<const V2*>(args.Z) + size_t(f) * NN / 2;
     const T half = T(0.5);
     V2 x[A];
+    // stage, for every row pair, the block's kBigWarps columns and their
+    // partner columns (N - c; N/2 for c = 0) with row-contiguous loads:
+    // in[pp][s], s < kBigWarps: Z[pp][c0 + s]; s >= kBigWarps: the partner of
+    // c0 + s - kBigWarps (pitch 2 kBigWarps + 1: the split's reads of 16 row
+    // pairs at one column fall in distinct banks)
+    constexpr int SP = 2 * kBigWarps + 1;
+    V2* in = bufs;  // [HALF][SP], before the transform buffers are used
+    for (int idx = threadIdx.x; idx < HALF * 2 * kBigWarps; idx += blockDim.x) {
+        const int pp = idx / (2 * kBigWarps), sl = idx % (2 * kBigWarps);
+        const int cc = c0 + (sl % kBigWarps);
+        const int cz = sl < kBigWarps ? cc : (cc == 0 ? HALF : N - cc);
+        in[pp * SP + sl] = Z[size_t(pp) * N + cz];
+    }
+    __syncthreads();
     // split each row pair into its two rows' half spectra (column col)
-    const int cpart = col == 0 ? HALF : N - col;
 #pragma unroll
     for (int t = 0; t < A; ++t) {
         const int r = j + B * t;
         const int pp = r >> 1;
-        const V2 za = Z[size_t(pp) * N + col], zb = Z[size_t(pp) * N + cpart];
+        const V2 za = in[pp * SP + w], zb = in[pp * SP + kBigWarps + w];
         V2 v;
         if (col == 0) {
             if ((r & 1) == 0) { v.x = za.x; v.y = zb.x; }
@@ -215,6 +221,7 @@ big_cols_kernel(BigArgs args) {
         }
         x[t] = v;
     }
+    __syncthreads();  // the staged rows are read before the transform buffers overwrite them
     warp_line_fft<T, N, A, B, -1>(x, tw, buf, j);
     const T a = T(args.a);
     const T inv_nn = T(1.0 / double(NN));
@@ -262,6 +269,20 @@ big_cols_kernel(BigArgs args) {
     for (int idx = threadIdx.x; idx < N * kBigWarps; idx += blockDim.x) {
         const int r = idx / kBigWarps, cc = idx % kBigWarps;
         Vf[size_t(r) * HALF + c0 + cc] = stage[r * (kBigWarps + 1) + cc];
+    }
+}
+
+// The twiddle and symbol tables of one call, in float64 then rounded (float64
+// arithmetic is scarce on this GPU: once per call, not once per block).
+template <typename T, int N>
+__global__ void big_tables_kernel(vec2_t<T>* __restrict__ tw, T* __restrict__ lam, double lam_scale) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        double sn, cs;
+        sincospi(-2.0 * double(k) / N, &sn, &cs);
+        tw[k].x = T(cs);
+        tw[k].y = T(sn);
+        const double s = sinpi(double(k) / N);
+        lam[k] = T(lam_scale * s * s);
     }
 }
 
@@ -318,7 +339,8 @@ static int big_workspace(size_t bytes, void** out) {
 bool fine_big_supported(int n, int precision) { return n == 1024 && precision == AC_F32; }
 
 size_t fine_big_workspace_bytes(int n, int fields) {
-    return size_t(n) * n * sizeof(float2) * fields + fields * sizeof(double) + 256;
+    // Z and V spectra, the means, then the tables (16-byte aligned)
+    return size_t(n) * n * sizeof(float2) * fields + fields * sizeof(double) + 256 + size_t(n) * 12;
 }
 
 // The two-pass fine propagation of `fields` fields (mapping as in BigArgs).
@@ -355,17 +377,28 @@ int fine_big_run(const ac_params* p, int groups, int per_group, int steps, const
     a.V = base + zbytes;
     double* mean = reinterpret_cast<double*>(base + 2 * zbytes);
     a.mean = mean;
+    const size_t toff = (2 * zbytes + size_t(fields) * sizeof(double) + 255) / 256 * 256;
+    vec2_t<T>* tw_tab = reinterpret_cast<vec2_t<T>*>(base + toff);
+    T* lam_tab = reinterpret_cast<T*>(tw_tab + N);
+    a.tw = tw_tab;
+    a.lam = lam_tab;
     a.mass = p->variant == AC_MASS_CONSERVING;
     a.a = 1.0 + p->S * p->dt;
     a.dt = p->dt;
     const double h = p->length / p->n;
     a.lam_scale = p->dt * p->eps * p->eps * 4.0 / (h * h);
+    big_tables_kernel<T, N><<<(N + 255) / 256, 256, 0, st>>>(tw_tab, lam_tab, a.lam_scale);
+    ACPR_LAUNCH_CHECK();
     if (a.mass) {
         big_mean_kernel<T><<<fields, 1024, 0, st>>>(a, (long long)NN, mean);
         ACPR_LAUNCH_CHECK();
     }
-    constexpr size_t kBufs = size_t(kBigWarps) * A * 33 > size_t(N) * (kBigWarps + 1) ? size_t(kBigWarps) * A * 33
-                                                                                     : size_t(N) * (kBigWarps + 1);
+    // the columns kernel's shared area serves, one after the other, the
+    // staged input columns, the warps' transform buffers and the output staging
+    constexpr size_t kIn = size_t(N / 2) * (2 * kBigWarps + 1);
+    constexpr size_t kXf = size_t(kBigWarps) * A * 33;
+    constexpr size_t kOut = size_t(N) * (kBigWarps + 1);
+    constexpr size_t kBufs = kIn > kXf ? (kIn > kOut ? kIn : kOut) : (kXf > kOut ? kXf : kOut);
     const size_t smem_rows = sizeof(vec2_t<T>) * (N + size_t(kBigWarps) * A * 33);
     const size_t smem_cols = sizeof(vec2_t<T>) * (N + kBufs) + sizeof(T) * N;
     static bool configured = false;

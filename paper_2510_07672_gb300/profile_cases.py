@@ -2,6 +2,7 @@
 
     python -m paper_2510_07672_gb300.profile_cases fine   # ac_fine_propagate_slices, 512 x 256^2, 20 steps
     python -m paper_2510_07672_gb300.profile_cases conv   # cnn_coarse_step, 16 x 256^2, 1-32x6-1 gelu bf16
+    python -m paper_2510_07672_gb300.profile_cases big    # ac_fine_propagate_slices, 16 x 1024^2, 2 steps
 
 Each case runs its call twice (a warm-up launch, then the one to capture) and
 exits 0, so `ncu -s <warm-up launches> -c 1` captures a warm launch.  Inputs
@@ -39,8 +40,16 @@ def main(case: str) -> None:
         u = torch.tensor(W.ics(), dtype=torch.float32, device="cuda")
         for _ in range(2):
             G.cnn_coarse_step(net, u)
+    elif case == "big":
+        n = 1024
+        u = torch.tensor(np.stack([I.random_field(n, seed=s) for s in range(16)]), dtype=torch.float32,
+                         device="cuda")
+        fp = G.FineParams(n, 0.004, 2.0, 2e-5, variant=G.AC_CLASSIC, precision=G.AC_F32)
+        out = torch.empty_like(u)
+        for _ in range(2):
+            G.ac_fine_propagate_slices(fp, 2, u, out)
     else:
-        raise SystemExit(f"unknown case {case!r} (fine | conv)")
+        raise SystemExit(f"unknown case {case!r} (fine | conv | big)")
     torch.cuda.synchronize()
     print(f"{case}: ok")
 
