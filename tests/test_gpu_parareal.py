@@ -103,3 +103,43 @@ def test_mass_f32_solve_matches_oracle_iterates():
         assert ref["iters"] == its[p]
         assert np.abs(U[p] - ref["U"]).max() < 2e-5 * np.sqrt(c)
         assert l2[p] < 2 * ref["res_l2"][-1] + 2e-6
+
+
+def test_full_size_mass256_in_the_bench_configuration():
+    """The benchmarked workload at full size, configured as bench.py times it
+    (16 mass-conserving 256^2 problems, 32 slices x 200 steps, the committed
+    trained G with the mass shift, every iteration a CUDA graph).  Every
+    problem stops below the 1e-6 increment or at k = s; at k = s the
+    trajectory is the sequential fine solve bit for bit (Sec. 3.3 exactness:
+    the fine kernel computes each field alone, so the batched sequential
+    solve is the same function); sampled slices are checked against the
+    float64 oracle's fine propagation, 2e-5 * sqrt(steps) per slice."""
+    import os
+    W = I.MASS_F32_256
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    z = np.load(os.path.join(root, "paper_2510_07672_gb300", "weights", "mass256_c32l6_gelu.npz"))
+    net = G.CoarseNet(W.layers, W.channels, z["w"].astype(np.float32), z["b"].astype(np.float32), act=W.act,
+                      precision=G.AC_F32, mass_fix=W.mass_fix)
+    fp = G.FineParams(W.n, W.eps, W.S, W.dt, variant=W.variant, precision=G.AC_F32)
+    ics = W.ics().astype(np.float32)
+    u0 = torch.tensor(ics, device="cuda")
+    pr = G.Parareal(fp, net, u0, W.slices, W.steps)
+    pr.enable_graphs(True)
+    its, l2 = pr.solve(tol=W.tol, kmax=W.kmax)
+    U = pr.trajectory()
+    assert all(r < W.tol or k == W.slices for k, r in zip(its, l2))
+    # sequential fine solve of all problems, slice after slice
+    seq = [u0]
+    for _ in range(W.slices):
+        seq.append(G.ac_fine_propagate_slices(fp, W.steps, seq[-1]))
+    seq = torch.stack(seq, dim=1)
+    for p, k in enumerate(its):
+        if k == W.slices:
+            assert torch.equal(U[p], seq[p])
+        else:
+            assert torch.equal(U[p, :k + 1], seq[p, :k + 1])  # U^k_j is exact for j <= k
+    # sampled slices against the oracle (one slice of 200 float64 steps each)
+    p_o = O.params(W.n, W.eps, W.S, W.dt, W.variant)
+    for p, j in ((0, 0), (7, 13), (15, 31)):
+        ref = O.fine_propagate(p_o, W.steps, U[p, j].double().cpu().numpy())
+        assert np.abs(U[p, j + 1].double().cpu().numpy() - ref).max() < 2e-5 * np.sqrt(W.steps)
