@@ -58,6 +58,10 @@ def lib():
             L.or_dft2d_naive_ri.argtypes = [dp, dp, C.c_int, C.c_int]
             L.or_fine_step.argtypes = [C.POINTER(Params), dp, dp]
             L.or_fine_propagate.argtypes = [C.POINTER(Params), C.c_int, dp, dp]
+            L.or_cn_step.argtypes = [C.POINTER(Params), dp, dp, C.c_double, C.c_int]
+            L.or_cn_step.restype = C.c_int
+            L.or_cn_propagate.argtypes = [C.POINTER(Params), C.c_int, dp, dp, C.c_double, C.c_int]
+            L.or_cn_propagate.restype = C.c_long
             L.or_solve_A.argtypes = [C.POINTER(Params), dp, dp]
             L.or_energy.argtypes = [C.POINTER(Params), dp]
             L.or_energy.restype = C.c_double
@@ -134,6 +138,23 @@ def fine_propagate(p: Params, steps: int, u) -> np.ndarray:
     out = np.empty_like(u)
     lib().or_fine_propagate(C.byref(p), int(steps), _dp(u), _dp(out))
     return out
+
+
+def cn_step(p: Params, u, tol: float = 1e-13, maxit: int = 50):
+    """One Crank-Nicolson step with Picard iteration (Sec. 3.1); returns
+    (U', iterations).  S in p is unused by this scheme."""
+    u = _f64(u)
+    out = np.empty_like(u)
+    it = lib().or_cn_step(C.byref(p), _dp(u), _dp(out), float(tol), int(maxit))
+    return out, int(it)
+
+
+def cn_propagate(p: Params, steps: int, u, tol: float = 1e-13, maxit: int = 50):
+    """`steps` Crank-Nicolson steps; returns (U, total Picard iterations)."""
+    u = _f64(u)
+    out = np.empty_like(u)
+    it = lib().or_cn_propagate(C.byref(p), int(steps), _dp(u), _dp(out), float(tol), int(maxit))
+    return out, int(it)
 
 
 def solve_A(p: Params, r) -> np.ndarray:

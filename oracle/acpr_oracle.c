@@ -14,6 +14,8 @@
  *   - Fine step: stabilised linear semi-implicit scheme with the periodic
  *     5-point Laplacian, solved by the 2D DFT (the scheme family the paper cites
  *     in Sec. 1; the spatial options are in Sec. 3.1).
+ *   - Crank-Nicolson fine step with Picard iteration (the paper's own fine
+ *     scheme, Sec. 3.1, Eq. (fully-discrete)): or_cn_step, or_cn_propagate.
  *   - Coarse propagator: 3x3 circular-padded conv stack (Sec. 3.2).
  *   - Parareal: Algorithm 2 / Sec. 3.3.
  *
@@ -168,6 +170,87 @@ void or_fine_propagate(const or_params* p, int steps, const double* u, double* o
     }
     if (steps == 0) memcpy(out, u, sizeof(double) * m);
     free(a);
+}
+
+/* 5-point periodic Laplacian applied directly (defined below). */
+static void apply_lap(int n, double h, const double* u, double* out);
+
+/* Solve (I - dt/2 eps^2 Lap_h) v = r by the 2D DFT (the linear system of each
+ * Picard iteration in Sec. 3.1). */
+static void solve_cn(const or_params* p, const double* r, double* v) {
+    int n = p->n;
+    double h = p->length / n;
+    cplx* z = malloc(sizeof(cplx) * n * n);
+    for (int i = 0; i < n * n; i++) z[i] = r[i];
+    or_fft2d(z, n, -1);
+    for (int k = 0; k < n; k++)
+        for (int l = 0; l < n; l++) {
+            double D = 1.0 - 0.5 * p->dt * p->eps * p->eps * lap_symbol(k, l, n, h);
+            z[(size_t)k * n + l] /= D;
+        }
+    or_fft2d(z, n, +1);
+    for (int i = 0; i < n * n; i++) v[i] = creal(z[i]) / ((double)n * n);
+    free(z);
+}
+
+/* One Crank-Nicolson step of Sec. 3.1,
+ *   (U' - U)/dt = eps^2 Lap_h (U' + U)/2 + (f(U') + f(U))/2 - g(U, U'),
+ * g = 0 (classic) or g = mean_x (f(U') + f(U))/2 (mass-conserving), solved by
+ * the Picard iteration of Sec. 3.1: U^0 = U and
+ *   (I - dt/2 eps^2 Lap_h) U^{m+1} = U + dt/2 eps^2 Lap_h U + dt/2 (f(U) + f(U^m)) - dt g(U, U^m)
+ * until max |U^{m+1} - U^m| <= tol or maxit iterations; U' = the last iterate.
+ * (The rearranged Eq. (fully-discrete) prints dt/2 g; the first form, whose
+ * mean of the right-hand side vanishes, gives dt g, used here.)  Returns the
+ * number of iterations. */
+int or_cn_step(const or_params* p, const double* u, double* out, double tol, int maxit) {
+    int n = p->n, m = n * n;
+    double h = p->length / n;
+    double* r0 = malloc(sizeof(double) * m);
+    double* r = malloc(sizeof(double) * m);
+    double* um = malloc(sizeof(double) * m);
+    double* lap = malloc(sizeof(double) * m);
+    apply_lap(n, h, u, lap);
+    for (int i = 0; i < m; i++) r0[i] = u[i] + 0.5 * p->dt * (p->eps * p->eps * lap[i] + f_dw(u[i]));
+    memcpy(um, u, sizeof(double) * m);
+    int it = 0;
+    while (it < maxit) {
+        double g = 0.0;
+        if (p->variant == 1) {
+            for (int i = 0; i < m; i++) g += 0.5 * (f_dw(um[i]) + f_dw(u[i]));
+            g /= m;
+        }
+        for (int i = 0; i < m; i++) r[i] = r0[i] + 0.5 * p->dt * f_dw(um[i]) - p->dt * g;
+        solve_cn(p, r, out);
+        ++it;
+        double diff = 0.0;
+        for (int i = 0; i < m; i++) {
+            double d = fabs(out[i] - um[i]);
+            if (d > diff) diff = d;
+        }
+        memcpy(um, out, sizeof(double) * m);
+        if (diff <= tol) break;
+    }
+    if (it == 0) memcpy(out, u, sizeof(double) * m);
+    free(r0);
+    free(r);
+    free(um);
+    free(lap);
+    return it;
+}
+
+/* `steps` Crank-Nicolson steps; returns the total number of Picard iterations. */
+long or_cn_propagate(const or_params* p, int steps, const double* u, double* out, double tol, int maxit) {
+    int m = p->n * p->n;
+    double* a = malloc(sizeof(double) * m);
+    memcpy(a, u, sizeof(double) * m);
+    long total = 0;
+    for (int s = 0; s < steps; s++) {
+        total += or_cn_step(p, a, out, tol, maxit);
+        memcpy(a, out, sizeof(double) * m);
+    }
+    if (steps == 0) memcpy(out, u, sizeof(double) * m);
+    free(a);
+    return total;
 }
 
 /* Discrete energy E_h(u) = h^2 sum eps^2/2 (|D+x u|^2 + |D+y u|^2) + F(u). */
