@@ -127,6 +127,22 @@ int ac_fine_autotune(const ac_params* params, int num_fields, int steps, const v
 int ac_fine_step(const ac_params* params, int batch, const void* u_in, void* u_out,
                  acpr_stream stream);
 
+/* The paper's own fine scheme (Sec. 3.1, Eq. fully-discrete): for each of
+ * `num_fields` fields, `steps` Crank-Nicolson steps
+ *   (U' - U)/dt = eps^2 Lap_h (U' + U)/2 + (f(U') + f(U))/2 - g(U, U'),
+ * g = 0 (AC_CLASSIC) or the mean of (f(U') + f(U))/2 (AC_MASS_CONSERVING; the
+ * first form of the scheme, which conserves mass), each solved by Picard
+ * iteration (U^0 = U; every iteration one DFT solve of (I - dt/2 eps^2 Lap_h))
+ * until max |U^{m+1} - U^m| <= tol or max_iters iterations.  The mean mode of
+ * the mass-conserving variant is held at the field's float64 entry mean.
+ * params->S is not used.  u_in, u_out: device [num_fields][n][n] in
+ * params->precision, 16-byte aligned, not overlapping.  picard_iters:
+ * optional device int[num_fields] receiving each field's total number of
+ * Picard iterations.  Built for n = 64, 128, 256 (AC_F32) and n = 64 (AC_F64);
+ * other sizes return AC_ERR_UNSUPPORTED.  Asynchronous on `stream`. */
+int ac_cn_propagate_slices(const ac_params* params, int num_fields, int steps, const void* u_in, void* u_out,
+                           double tol, int max_iters, int* picard_iters, acpr_stream stream);
+
 /* The fine propagator F(t_n, t_{n+1}, U_n) of Eq. (fine_operator): for every
  * one of `num_fields` independent fields, `steps_per_slice` fine steps
  * (Algorithm 2: the parallel fine solves of all slices).  The field stays on

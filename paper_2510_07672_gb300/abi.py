@@ -47,7 +47,7 @@ class ac_parareal_stats(C.Structure):
                 ("iterations", C.c_longlong)]
 
 
-EXPORTS = ["ac_last_error", "ac_fine_supported", "ac_fine_step", "ac_fine_propagate_slices",
+EXPORTS = ["ac_last_error", "ac_fine_supported", "ac_fine_step", "ac_fine_propagate_slices", "ac_cn_propagate_slices",
            "cnn_packed_bytes", "cnn_work_bytes", "cnn_pack_weights", "cnn_coarse_step",
            "parareal_residual", "parareal_residual_noalloc", "ac_parareal_create", "parareal_iterate", "ac_parareal_set_active",
            "ac_parareal_trajectory", "ac_parareal_copy_trajectory", "ac_parareal_solve", "ac_parareal_create_uneven", "ac_parareal_enable_graphs",
@@ -78,6 +78,7 @@ def load(build_if_missing: bool = True):
         L.ac_fine_supported.argtypes = [I, I]
         L.ac_fine_step.argtypes = [P(ac_params), I, S, S, S]
         L.ac_fine_propagate_slices.argtypes = [P(ac_params), I, I, S, S, S]
+        L.ac_cn_propagate_slices.argtypes = [P(ac_params), I, I, S, S, D, I, S, S]
         L.cnn_packed_bytes.argtypes = [P(cnn_desc)]
         L.cnn_packed_bytes.restype = C.c_size_t
         L.cnn_work_bytes.argtypes = [P(cnn_desc), I, I]
@@ -178,6 +179,24 @@ def ac_fine_step(params: FineParams, u_in, u_out=None, stream=None):
     p = params.c()
     _check(load().ac_fine_step(C.byref(p), batch, _dev(u_in, params.dtype, "u_in"),
                                _dev(u_out, params.dtype, "u_out"), _stream(stream)))
+    return u_out
+
+
+def ac_cn_propagate_slices(params: FineParams, steps: int, u_in, u_out=None, tol: float = 1e-6,
+                           max_iters: int = 50, iters=None, stream=None):
+    """Crank-Nicolson steps with Picard iteration (Sec. 3.1) for every field of
+    u_in.  iters: optional device int32 tensor [fields] for the total Picard
+    iterations per field."""
+    import torch
+    u_out = u_out if u_out is not None else u_in.new_empty(u_in.shape)
+    fields = u_in.numel() // (params.n * params.n)
+    p = params.c()
+    it_ptr = None
+    if iters is not None:
+        it_ptr = _dev(iters, torch.int32, "iters")
+    _check(load().ac_cn_propagate_slices(C.byref(p), fields, int(steps), _dev(u_in, params.dtype, "u_in"),
+                                         _dev(u_out, params.dtype, "u_out"), float(tol), int(max_iters), it_ptr,
+                                         _stream(stream)))
     return u_out
 
 
