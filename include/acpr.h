@@ -322,6 +322,14 @@ int ac_parareal_create_uneven(const ac_params* params, const cnn_desc* coarse, i
  * (k, active problems) pair is met and replay it afterwards. */
 int ac_parareal_enable_graphs(ac_parareal* state, int on);
 
+/* Choose the fine propagator F of the handle's solves: scheme 0 = the
+ * stabilised semi-implicit step (the default), 1 = the Crank-Nicolson step of
+ * Sec. 3.1 with Picard iteration to max |U^{m+1} - U^m| <= tol (at most
+ * max_iters iterations), as in ac_cn_propagate_slices.  Scheme 1 needs a size
+ * ac_cn_propagate_slices is built for (else AC_ERR_UNSUPPORTED).  Drops the
+ * handle's captured iteration graphs.  Call between solves. */
+int ac_parareal_set_fine_scheme(ac_parareal* state, int scheme, double tol, int max_iters);
+
 /* One iteration of Algorithm 2 on every problem not yet converged.
  * *k_inout = 0 runs the initial coarse sweep U^0_{n+1} = G(U^0_n); k >= 1 runs
  * the fine solves F(U^{k-1}_n), n = k-1..s-1, then the sequential correction

@@ -37,6 +37,10 @@ struct CnArgs {
     double lamh_scale;  // dt/2 eps^2 (4 / h^2)
     double dt;
     int* iters;         // optional: total Picard iterations per field
+    // work list (overrides the plain field index and `steps`): field f reads
+    // field work[f].x of `in`, writes field work[f].y of `out`, runs
+    // work[f].z steps
+    const int4* work;
 };
 
 template <int P>
@@ -101,8 +105,16 @@ fine_cn_kernel(CnArgs args) {
     if constexpr (P > 1) rank = int(cg::this_cluster().block_rank());
     const int field = blockIdx.x / P;
     const size_t NN = size_t(N) * N;
-    const T* in = static_cast<const T*>(args.in) + size_t(field) * NN + size_t(rank) * R * N;
-    T* out = static_cast<T*>(args.out) + size_t(field) * NN + size_t(rank) * R * N;
+    long long fin = field, fout = field;
+    int nsteps = args.steps;
+    if (args.work) {
+        const int4 w = args.work[field];
+        fin = w.x;
+        fout = w.y;
+        nsteps = w.z;
+    }
+    const T* in = static_cast<const T*>(args.in) + size_t(fin) * NN + size_t(rank) * R * N;
+    T* out = static_cast<T*>(args.out) + size_t(fout) * NN + size_t(rank) * R * N;
 
     for (int k = tid; k < N; k += Sh::THREADS) {
         double sn, cs;
@@ -275,7 +287,7 @@ fine_cn_kernel(CnArgs args) {
     int slot = 0;  // cluster-max slot, alternating
     const T tol = T(args.tol);
     __shared__ T warp_max[32];
-    for (int step = 0; step < args.steps; ++step) {
+    for (int step = 0; step < nsteps; ++step) {
         // fm = F0 = FFT(f(U)); A = (1 - hmu) U_hat + dt/2 F0
         V fm[A];
 #pragma unroll
@@ -394,30 +406,7 @@ int launch_cn(const CnArgs& args, cudaStream_t st) {
 
 }  // namespace
 
-int cn_propagate(const ac_params* p, int num_fields, int steps, const void* in, void* out, double tol,
-                 int max_iters, int* iters_dev, cudaStream_t st) {
-    ACPR_CHECK_ARG(p != nullptr, "ac_params is NULL");
-    ACPR_CHECK_ARG(p->precision == AC_F32 || p->precision == AC_F64, "bad precision %d", p->precision);
-    ACPR_CHECK_ARG(p->variant == AC_CLASSIC || p->variant == AC_MASS_CONSERVING, "bad variant %d", p->variant);
-    ACPR_CHECK_ARG(p->length > 0 && p->dt > 0 && p->eps >= 0, "need length > 0, dt > 0, eps >= 0");
-    ACPR_CHECK_ARG(num_fields >= 0 && steps >= 0 && max_iters >= 1 && tol >= 0, "bad counts or tolerance");
-    if (num_fields == 0) return AC_OK;
-    ACPR_CHECK_ARG(in && out && in != out, "bad field pointers");
-    ACPR_CHECK_ARG((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % 16 == 0,
-                   "fields must be 16-byte aligned");
-    ACPR_CHECK_ARG(num_fields < (1 << 24), "too many fields");
-    CnArgs a{};
-    a.in = in;
-    a.out = out;
-    a.num_fields = num_fields;
-    a.steps = steps;
-    a.mass = p->variant == AC_MASS_CONSERVING;
-    a.max_iters = max_iters;
-    a.tol = tol;
-    const double h = p->length / p->n;
-    a.lamh_scale = 0.5 * p->dt * p->eps * p->eps * 4.0 / (h * h);
-    a.dt = p->dt;
-    a.iters = iters_dev;
+static int cn_launch(const ac_params* p, const CnArgs& a, cudaStream_t st) {
     if (p->precision == AC_F32) {
         switch (p->n) {
             case 64: return launch_cn<float, 64, 2, 8, 8>(a, st);
@@ -434,6 +423,65 @@ int cn_propagate(const ac_params* p, int num_fields, int steps, const void* in, 
     set_error("ac_cn_propagate_slices: n=%d not built for precision %d (64, 128, 256 f32; 64 f64)", p->n,
               p->precision);
     return AC_ERR_UNSUPPORTED;
+}
+
+bool cn_supported(int n, int precision) {
+    return precision == AC_F32 ? (n == 64 || n == 128 || n == 256) : (precision == AC_F64 && n == 64);
+}
+
+static int cn_check(const ac_params* p, double tol, int max_iters) {
+    ACPR_CHECK_ARG(p != nullptr, "ac_params is NULL");
+    ACPR_CHECK_ARG(p->precision == AC_F32 || p->precision == AC_F64, "bad precision %d", p->precision);
+    ACPR_CHECK_ARG(p->variant == AC_CLASSIC || p->variant == AC_MASS_CONSERVING, "bad variant %d", p->variant);
+    ACPR_CHECK_ARG(p->length > 0 && p->dt > 0 && p->eps >= 0, "need length > 0, dt > 0, eps >= 0");
+    ACPR_CHECK_ARG(max_iters >= 1 && tol >= 0, "need max_iters >= 1 and tol >= 0");
+    return AC_OK;
+}
+
+static CnArgs cn_args(const ac_params* p, double tol, int max_iters) {
+    CnArgs a{};
+    a.mass = p->variant == AC_MASS_CONSERVING;
+    a.max_iters = max_iters;
+    a.tol = tol;
+    const double h = p->length / p->n;
+    a.lamh_scale = 0.5 * p->dt * p->eps * p->eps * 4.0 / (h * h);
+    a.dt = p->dt;
+    return a;
+}
+
+// Work-list form (the Parareal driver's fine sweep): item f advances field
+// work[f].x of `in` by work[f].z steps into field work[f].y of `out`.
+int cn_run_work(const ac_params* p, int count, const int4* work, const void* in, void* out, double tol,
+                int max_iters, cudaStream_t st) {
+    int rc = cn_check(p, tol, max_iters);
+    if (rc) return rc;
+    ACPR_CHECK_ARG(count >= 0 && work && in && out, "bad work-list arguments");
+    if (count == 0) return AC_OK;
+    CnArgs a = cn_args(p, tol, max_iters);
+    a.in = in;
+    a.out = out;
+    a.num_fields = count;
+    a.work = work;
+    return cn_launch(p, a, st);
+}
+
+int cn_propagate(const ac_params* p, int num_fields, int steps, const void* in, void* out, double tol,
+                 int max_iters, int* iters_dev, cudaStream_t st) {
+    int rc = cn_check(p, tol, max_iters);
+    if (rc) return rc;
+    ACPR_CHECK_ARG(num_fields >= 0 && steps >= 0, "bad counts");
+    if (num_fields == 0) return AC_OK;
+    ACPR_CHECK_ARG(in && out && in != out, "bad field pointers");
+    ACPR_CHECK_ARG((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % 16 == 0,
+                   "fields must be 16-byte aligned");
+    ACPR_CHECK_ARG(num_fields < (1 << 24), "too many fields");
+    CnArgs a = cn_args(p, tol, max_iters);
+    a.in = in;
+    a.out = out;
+    a.num_fields = num_fields;
+    a.steps = steps;
+    a.iters = iters_dev;
+    return cn_launch(p, a, st);
 }
 
 }  // namespace acpr

@@ -30,6 +30,9 @@ int fine_propagate_mapped(const ac_params* p, int groups, int per_group, int ste
                           long long in_gs, long long in_off, void* out, long long out_gs,
                           long long out_off, const int* map, cudaStream_t stream);
 int fine_run_work(const ac_params* p, int count, const int4* work, const void* in, void* out, cudaStream_t stream);
+int cn_run_work(const ac_params* p, int count, const int4* work, const void* in, void* out, double tol,
+                int max_iters, cudaStream_t st);
+bool cn_supported(int n, int precision);
 bool fine_supported_internal(int n, int precision);
 
 // ------------------------------------------------------------- kernels ----
@@ -294,6 +297,9 @@ struct ac_parareal {
     cudaStream_t stream_launched = nullptr;
     bool timing = false;
     bool graphs = false;
+    int fine_scheme = 0;       // 0: stabilised semi-implicit step, 1: Crank-Nicolson + Picard
+    double cn_tol = 1e-6;
+    int cn_max_iters = 50;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t done = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream the graphs are captured on
@@ -415,6 +421,8 @@ static int enqueue(ac_parareal* st, int k, int m, int nwork, cudaStream_t stream
         // large fields: the two-pass path runs uniform launches only
         rc = fine_propagate_mapped(&st->p, m, s - k + 1, st->cp[0], st->Ua, s + 1, k - 1, st->Fres, s, k - 1,
                                    st->d_map, stream);
+    } else if (st->fine_scheme == 1) {
+        rc = cn_run_work(&st->p, nwork, st->d_fw, st->Ua, st->Fres, st->cn_tol, st->cn_max_iters, stream);
     } else {
         rc = fine_run_work(&st->p, nwork, st->d_fw, st->Ua, st->Fres, stream);
     }
@@ -817,6 +825,26 @@ extern "C" int ac_parareal_enable_graphs(ac_parareal* state, int on) {
     using namespace acpr;
     ACPR_CHECK_ARG(state, "null state");
     state->graphs = on != 0;
+    return AC_OK;
+}
+
+extern "C" int ac_parareal_set_fine_scheme(ac_parareal* state, int scheme, double tol, int max_iters) {
+    using namespace acpr;
+    ACPR_CHECK_ARG(state, "null state");
+    ACPR_CHECK_ARG(scheme == 0 || scheme == 1, "fine scheme must be 0 (stabilised) or 1 (Crank-Nicolson)");
+    if (scheme == 1) {
+        ACPR_CHECK_ARG(tol >= 0 && max_iters >= 1, "need tol >= 0 and max_iters >= 1");
+        if (!cn_supported(state->p.n, state->p.precision)) {
+            set_error("Crank-Nicolson fine scheme not built for n=%d, precision %d", state->p.n, state->p.precision);
+            return AC_ERR_UNSUPPORTED;
+        }
+        state->cn_tol = tol;
+        state->cn_max_iters = max_iters;
+    }
+    state->fine_scheme = scheme;
+    // captured iterations hold the previous scheme's launches
+    for (auto& kv : state->graph_cache) cudaGraphExecDestroy(kv.second.first);
+    state->graph_cache.clear();
     return AC_OK;
 }
 

@@ -64,3 +64,25 @@ def test_cn_unsupported_size_is_reported():
     u = torch.zeros((1, 512, 512), device="cuda")
     with pytest.raises(G.AcprError):
         G.ac_cn_propagate_slices(fp, 1, u)
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_parareal_with_the_cn_fine_scheme_is_exact_at_k_equals_s(graphs):
+    """Parareal whose F is the Crank-Nicolson step (ac_parareal_set_fine_scheme):
+    at k = s the trajectory is the sequential Crank-Nicolson solve bit for bit
+    (Sec. 3.3 exactness), with and without graph capture."""
+    n, s, c = 64, 4, 20
+    fp = G.FineParams(n, 2.5 / n, 2.0, 5e-5, variant=G.AC_MASS_CONSERVING, precision=G.AC_F32)
+    wt, bs = I.cnn_weights(3, 16, seed=0)
+    net = G.CoarseNet(3, 16, wt.astype(np.float32), bs.astype(np.float32), act=1, precision=G.AC_F32)
+    u0 = torch.tensor(np.stack([I.random_field(n, seed=p, zero_mean=True) for p in range(3)]).astype(np.float32),
+                      device="cuda")
+    pr = G.Parareal(fp, net, u0, s, c)
+    pr.enable_graphs(graphs)
+    pr.set_fine_scheme(1, tol=1e-6, max_iters=50)
+    its, _ = pr.solve(tol=0.0, kmax=s)
+    assert its == [s] * 3
+    seq = [u0]
+    for _ in range(s):
+        seq.append(G.ac_cn_propagate_slices(fp, c, seq[-1], tol=1e-6, max_iters=50))
+    assert torch.equal(pr.trajectory(), torch.stack(seq, dim=1))
