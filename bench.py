@@ -355,30 +355,32 @@ def job_rate(cells_per_rank: float, ms: float, world: int) -> float:
     return world * cells_per_rank / (ms * 1e-3)
 
 
-def cost_model(st, seq_ms, its, steps):
+def cost_model(st, seq_ms, its, steps, s=None, c=None, m=1):
     """The cost model of Sec. 3.4 with the measured unit costs: t_num = one
     fine step of one slice (all problems), from the sequential solve; t_nn =
     one application of G (all problems), from the solve's coarse phase.  The
     model puts every slice on its own device, so iteration k's fine sweep
-    costs c t_num; T(k) = c k t_num + (2s - k)(k + 1)/2 t_nn and
+    costs c t_num; with G composed m times per slice each coarse evaluation
+    costs m t_nn, so T(k) = c k t_num + (2s - k)(k + 1)/2 m t_nn and
     S_k = s c t_num / T(k).  The measured single-GPU solve is parareal_ms."""
-    s, c = WL.slices, WL.steps
+    s = WL.slices if s is None else s
+    c = WL.steps if c is None else c
     calls = st.get("coarse_calls", 0) / max(steps, 1)
     if not calls:
         return None
     t_num = seq_ms / (s * c)
     t_nn = st["coarse_ms"] / max(steps, 1) / calls
     k = max(its) if its else s
-    T = c * k * t_num + (2 * s - k) * (k + 1) / 2 * t_nn
-    return {"t_num_ms": t_num, "t_nn_ms": t_nn, "k": k, "coarse_calls_per_solve": calls,
+    T = c * k * t_num + (2 * s - k) * (k + 1) / 2 * m * t_nn
+    return {"t_num_ms": t_num, "t_nn_ms": t_nn, "k": k, "s": s, "c": c, "m": m, "coarse_calls_per_solve": calls,
             "T_k_ms": T, "S_k": s * c * t_num / T,
             "note": "Sec. 3.4 model, one slice per device; measured on one GPU: parareal_ms"}
 
 
-def fine_traffic_per_launch(st, wl):
+def fine_traffic_per_launch(st, wl, steps=None):
     if wl.n != 256 or not st.get("fine_launches"):
         return None
-    slices = st["fine_cell_steps"] / (wl.n * wl.n * wl.steps)
+    slices = st["fine_cell_steps"] / (wl.n * wl.n * (wl.steps if steps is None else steps))
     return FINE_DRAM_BYTES_PER_FIELD_SLICE_256 * slices / st["fine_launches"]
 
 
@@ -395,6 +397,9 @@ def main():
                          "train: coarse-net training iterations (C = 64, 8 layers); "
                          "adjoint: checkpointed energy gradient through 2000 steps")
     ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--coarse-substeps", type=int, default=1,
+                    help="mass256 only: M > 1 covers the same time span with slices of M x 200 fine steps "
+                         "(32 / M slices) and composes G M times per slice")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -450,7 +455,12 @@ def main():
                       act=WL.act, precision=G.AC_F32, mass_fix=WL.mass_fix, device=dev)
     ics = WL.ics().astype(np.float32)  # same 16 problems on every rank (weak scaling replicas)
     u0 = torch.tensor(ics, device=dev)
-    pr = G.Parareal(fp, net, u0, WL.slices, WL.steps)
+    M = args.coarse_substeps
+    if M < 1 or WL.slices % M:
+        raise SystemExit(f"--coarse-substeps must divide {WL.slices}")
+    slices, steps = WL.slices // M, WL.steps * M
+    pr = G.Parareal(fp, net, u0, slices, steps)
+    pr.set_coarse_substeps(M)
     pr.enable_timing(True)
     pr.enable_graphs(not args.no_graphs)
     stream = torch.cuda.current_stream()
@@ -483,7 +493,7 @@ def main():
     st = pr.stats()
     clocks = clk.summary()
 
-    cells = WL.problems * WL.slices * WL.steps * WL.n * WL.n  # delivered per solve per rank
+    cells = WL.problems * slices * steps * WL.n * WL.n  # delivered per solve per rank
     value = job_rate(cells, ms, world)
 
     # sequential float32 fine solve of the same problems, same kernel
@@ -492,8 +502,8 @@ def main():
 
     def sequential():
         a, b = seq_in, seq_out
-        for _ in range(WL.slices):
-            G.ac_fine_propagate_slices(fp, WL.steps, a, b)
+        for _ in range(slices):
+            G.ac_fine_propagate_slices(fp, steps, a, b)
             a, b = b, a
         return a
 
@@ -509,7 +519,7 @@ def main():
     # end to end through the public API: pinned host ICs in, final fields out
     host_u0 = torch.tensor(ics).pin_memory()
     host_out = torch.empty((WL.problems, WL.n, WL.n), dtype=torch.float32).pin_memory()
-    traj = torch.empty((WL.problems, WL.slices + 1, WL.n, WL.n), dtype=torch.float32, device=dev)
+    traj = torch.empty((WL.problems, slices + 1, WL.n, WL.n), dtype=torch.float32, device=dev)
     dev_u0 = torch.empty_like(u0)
 
     def e2e_step():
@@ -540,8 +550,9 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WL.name, "n": WL.n, "problems": WL.problems, "slices": WL.slices,
-                       "steps_per_slice": WL.steps, "variant": "mass-conserving", "conv": "1-32x6-1 gelu bf16, mACNN mass shift",
+            "config": {"workload": WL.name if M == 1 else f"{WL.name}, G composed {M}x per slice",
+                       "n": WL.n, "problems": WL.problems, "slices": slices,
+                       "steps_per_slice": steps, "coarse_substeps": M, "variant": "mass-conserving", "conv": "1-32x6-1 gelu bf16, mACNN mass shift",
                        "tol": WL.tol, "coarse_weights": wsrc,
                        "l2": "state larger than L2 (trajectories, stored G and F values: 0.54 GB)",
                        "parallelism": f"replicas x{world}", "cuda_graphs": not args.no_graphs},
@@ -554,13 +565,13 @@ def main():
             "conv_tflops": conv_tflops,
             "roofline": {"bound": "alu", "kernel": "fine_field_kernel", "achieved": fine_tflops,
                          "peak": peak, "unit": "TFLOP/s", "frac": fine_tflops / peak,
-                         "traffic": fine_traffic_per_launch(st, WL),
+                         "traffic": fine_traffic_per_launch(st, WL, steps),
                          "traffic_unit": "bytes per launch (ncu DRAM bytes per field-slice x field-slices per launch)",
                          "peak_source": f"FP32 lanes x 2 x sm_max_mhz {sm_mhz:.0f} from {src} peaks",
                          "flops_per_cell_step": fpc},
             "cpu_baseline": cpu,
             "cpu_baseline_1core": cpu1,
-            "cost_model": cost_model(st, seq_ms, its, args.steps),
+            "cost_model": cost_model(st, seq_ms, its, args.steps, slices, steps, M),
             "e2e": {"value": job_rate(cells, e2e_ms, world), "unit": UNIT,
                     "h2d_bytes_per_step": int(host_u0.numel() * 4), "d2h_bytes_per_step": int(host_out.numel() * 4)},
             "gpu_launches": int(launches),

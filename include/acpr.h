@@ -322,6 +322,14 @@ int ac_parareal_create_uneven(const ac_params* params, const cnn_desc* coarse, i
  * (k, active problems) pair is met and replay it afterwards. */
 int ac_parareal_enable_graphs(ac_parareal* state, int on);
 
+/* Coarse-time composition (the remark after Algorithm 2): every coarse
+ * evaluation of the handle's solves applies G `substeps` times in a row
+ * (1 = plain G, the default; at most 64), so one network trained for a
+ * shorter step covers the slice.  The first call with substeps > 1 allocates
+ * two [problems][n][n] buffers for the intermediate fields.  Drops the
+ * handle's captured iteration graphs.  Call between solves. */
+int ac_parareal_set_coarse_substeps(ac_parareal* state, int substeps);
+
 /* Choose the fine propagator F of the handle's solves: scheme 0 = the
  * stabilised semi-implicit step (the default), 1 = the Crank-Nicolson step of
  * Sec. 3.1 with Picard iteration to max |U^{m+1} - U^m| <= tol (at most

@@ -80,6 +80,9 @@ def lib():
                                       C.c_int, C.c_double, C.c_int, dp, dp, dp, dp,
                                       C.POINTER(C.c_int)]
             L.or_parareal.restype = C.c_long
+            L.or_parareal_rep.argtypes = [C.POINTER(Params), C.POINTER(Cnn), C.c_int, C.c_int, C.c_int, C.c_int,
+                                          C.c_int, C.c_double, C.c_int, dp, dp, dp, dp, C.POINTER(C.c_int)]
+            L.or_parareal_rep.restype = C.c_long
             _lib = L
     return _lib
 
@@ -226,8 +229,10 @@ def residual(Unew, Uold):
 
 
 def parareal(p: Params, coarse, s: int, c: int, kmax: int, tol: float, u0,
-             coarse_steps: int = 0, literal: bool = False):
+             coarse_steps: int = 0, literal: bool = False, coarse_repeat: int = 1):
     """Algorithm 2.  coarse: CnnSpec, or None for G = F over coarse_steps fine steps.
+    coarse_repeat > 1 composes that propagator with itself per slice (the
+    remark after Algorithm 2).
 
     Returns dict(U=[s+1,n,n], res_l2=[...], res_max=[...], iters=k, g_calls=...).
     """
@@ -238,8 +243,8 @@ def parareal(p: Params, coarse, s: int, c: int, kmax: int, tol: float, u0,
     rmx = np.zeros(kmax + 2)
     it = C.c_int()
     cptr = C.byref(coarse.s) if coarse is not None else None
-    g = lib().or_parareal(C.byref(p), cptr, int(coarse_steps), int(s), int(c), int(kmax),
-                          float(tol), int(literal), _dp(u0), _dp(U), _dp(rl2), _dp(rmx),
-                          C.byref(it))
+    g = lib().or_parareal_rep(C.byref(p), cptr, int(coarse_steps), int(coarse_repeat), int(s), int(c), int(kmax),
+                              float(tol), int(literal), _dp(u0), _dp(U), _dp(rl2), _dp(rmx),
+                              C.byref(it))
     k = it.value
     return dict(U=U, res_l2=rl2[1:k + 1].copy(), res_max=rmx[1:k + 1].copy(), iters=k, g_calls=g)

@@ -530,18 +530,54 @@ void or_residual(int s, int n, const double* Unew, const double* Uold, double* l
  * stored G(U^{k-1}_n) values are reused, and U^k_{k-1} = U^{k-1}_{k-1} makes its
  * G value known).  G is re-evaluated literally as Algorithm 2 states it only
  * when `literal` is set. */
+/* One application of the coarse propagator: the network, or F over
+ * coarse_steps fine steps. */
+static void or_coarse_once(const or_params* p, const or_cnn* coarse, int coarse_steps, const double* in,
+                           double* out) {
+    if (coarse) or_cnn_forward(coarse, p->n, in, out);
+    else or_fine_propagate(p, coarse_steps, in, out);
+}
+
+/* The coarse evaluation of a slice: `repeat` applications of the coarse
+ * propagator in a row (the composition of the remark after Algorithm 2; 1 is
+ * plain G).  tmp holds one field. */
+static void or_coarse_eval(const or_params* p, const or_cnn* coarse, int coarse_steps, int repeat,
+                           const double* in, double* out, double* tmp) {
+    size_t m = (size_t)p->n * p->n;
+    if (repeat <= 1) { or_coarse_once(p, coarse, coarse_steps, in, out); return; }
+    memcpy(tmp, in, sizeof(double) * m);
+    for (int r = 0; r < repeat; r++) {
+        or_coarse_once(p, coarse, coarse_steps, tmp, out);
+        if (r + 1 < repeat) memcpy(tmp, out, sizeof(double) * m);
+    }
+}
+
+long or_parareal_rep(const or_params* p, const or_cnn* coarse, int coarse_steps, int repeat, int s, int c,
+                     int kmax, double tol, int literal, const double* u0, double* U,
+                     double* res_l2, double* res_max, int* iters);
+
 long or_parareal(const or_params* p, const or_cnn* coarse, int coarse_steps, int s, int c,
                  int kmax, double tol, int literal, const double* u0, double* U,
                  double* res_l2, double* res_max, int* iters) {
+    return or_parareal_rep(p, coarse, coarse_steps, 1, s, c, kmax, tol, literal, u0, U, res_l2, res_max, iters);
+}
+
+/* Algorithm 2 with the coarse propagator composed `repeat` times per slice;
+ * returns the number of coarse applications (repeat per evaluation). */
+long or_parareal_rep(const or_params* p, const or_cnn* coarse, int coarse_steps, int repeat, int s, int c,
+                     int kmax, double tol, int literal, const double* u0, double* U,
+                     double* res_l2, double* res_max, int* iters) {
     int n = p->n;
     size_t m = (size_t)n * n;
     double* Uold = malloc(sizeof(double) * m * (s + 1));
     double* Gold = malloc(sizeof(double) * m * s);
     double* Ff = malloc(sizeof(double) * m * s);
     double* g = malloc(sizeof(double) * m);
+    double* gt = malloc(sizeof(double) * m);
     long gcalls = 0;
-#define GAPPLY(in, out) do { if (coarse) or_cnn_forward(coarse, n, (in), (out)); \
-                             else or_fine_propagate(p, coarse_steps, (in), (out)); gcalls++; } while (0)
+    if (repeat < 1) repeat = 1;
+#define GAPPLY(in, out) do { or_coarse_eval(p, coarse, coarse_steps, repeat, (in), (out), gt); \
+                             gcalls += repeat; } while (0)
     /* k = 0: sequential coarse sweep */
     memcpy(U, u0, sizeof(double) * m);
     for (int j = 0; j < s; j++) {
@@ -579,7 +615,7 @@ long or_parareal(const or_params* p, const or_cnn* coarse, int coarse_steps, int
     }
     if (k > kmax || k > s) k--;
     *iters = k;
-    free(Uold); free(Gold); free(Ff); free(g);
+    free(Uold); free(Gold); free(Ff); free(g); free(gt);
 #undef GAPPLY
     return gcalls;
 }

@@ -51,7 +51,7 @@ EXPORTS = ["ac_last_error", "ac_fine_supported", "ac_fine_step", "ac_fine_propag
            "cnn_packed_bytes", "cnn_work_bytes", "cnn_pack_weights", "cnn_coarse_step",
            "parareal_residual", "parareal_residual_noalloc", "ac_parareal_create", "parareal_iterate", "ac_parareal_set_active",
            "ac_parareal_trajectory", "ac_parareal_copy_trajectory", "ac_parareal_solve", "ac_parareal_create_uneven", "ac_parareal_enable_graphs",
-           "ac_parareal_solve_many", "ac_parareal_reset", "ac_parareal_enable_timing", "ac_parareal_set_fine_scheme",
+           "ac_parareal_solve_many", "ac_parareal_reset", "ac_parareal_enable_timing", "ac_parareal_set_fine_scheme", "ac_parareal_set_coarse_substeps",
            "ac_parareal_get_stats", "ac_parareal_reset_stats", "ac_launch_count", "ac_parareal_destroy",
            "ac_fine_variant_count", "ac_fine_variant_name", "ac_fine_get_variant", "ac_fine_set_variant",
            "ac_fine_autotune", "ac_fine_propagate_work", "ac_fine_trajectory", "ac_fine_adjoint", "ac_energy", "ac_energy_grad",
@@ -95,6 +95,7 @@ def load(build_if_missing: bool = True):
         L.ac_parareal_copy_trajectory.argtypes = [S, S, S]
         L.ac_parareal_solve.argtypes = [S, D, I, P(I), P(D), S]
         L.ac_parareal_set_fine_scheme.argtypes = [S, I, D, I]
+        L.ac_parareal_set_coarse_substeps.argtypes = [S, I]
         L.ac_parareal_create_uneven.argtypes = [P(ac_params), P(cnn_desc), I, P(I), P(I), S, P(S)]
         L.ac_parareal_enable_graphs.argtypes = [S, I]
         L.ac_parareal_solve_many.argtypes = [P(S), I, P(S), D, I, P(I), P(D)]
@@ -545,6 +546,11 @@ class Parareal:
 
     def enable_graphs(self, on=True):
         _check(load().ac_parareal_enable_graphs(self._h, int(on)))
+
+    def set_coarse_substeps(self, substeps: int):
+        """Each coarse evaluation applies G `substeps` times (the remark after
+        Algorithm 2)."""
+        _check(load().ac_parareal_set_coarse_substeps(self._h, int(substeps)))
 
     def set_fine_scheme(self, scheme: int, tol: float = 1e-6, max_iters: int = 50):
         """0: the stabilised semi-implicit step; 1: Crank-Nicolson with Picard

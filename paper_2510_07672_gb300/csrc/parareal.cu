@@ -297,6 +297,8 @@ struct ac_parareal {
     cudaStream_t stream_launched = nullptr;
     bool timing = false;
     bool graphs = false;
+    int g_sub = 1;             // coarse composition: G applied g_sub times per slice
+    void* gsub[2] = {nullptr, nullptr};  // [problems][nn] each: intermediate G applications
     int fine_scheme = 0;       // 0: stabilised semi-implicit step, 1: Crank-Nicolson + Picard
     double cn_tol = 1e-6;
     int cn_max_iters = 50;
@@ -311,7 +313,7 @@ namespace acpr {
 
 static void free_state(ac_parareal* st) {
     if (!st) return;
-    for (void* ptr : {st->Ua, st->Ub, st->Gold, st->Fres, st->gtmp, st->work, st->packed,
+    for (void* ptr : {st->Ua, st->Ub, st->Gold, st->Fres, st->gtmp, st->work, st->packed, st->gsub[0], st->gsub[1],
                       static_cast<void*>(st->d_map), static_cast<void*>(st->d_fw), static_cast<void*>(st->d_part),
                       static_cast<void*>(st->d_res)})
         if (ptr) cudaFree(ptr);
@@ -324,6 +326,26 @@ static void free_state(ac_parareal* st) {
     for (auto& kv : st->graph_cache) cudaGraphExecDestroy(kv.second.first);
     if (st->cap_stream) cudaStreamDestroy(st->cap_stream);
     delete st;
+}
+
+// One coarse evaluation of the sweep: G, or G composed g_sub times (the
+// recursive composition of the remark after Algorithm 2: a coarse step that
+// covers the slice in g_sub sub-steps).  The intermediate applications go
+// through compact [mn][nn] buffers; the last one writes the mapped output.
+static int coarse_apply(ac_parareal* st, int mn, const void* in, long long in_bs, const int* in_map, void* out,
+                        long long out_bs, const int* out_map, cudaStream_t stream) {
+    const void* cur = in;
+    long long cur_bs = in_bs;
+    const int* cur_map = in_map;
+    for (int i = 0; i + 1 < st->g_sub; ++i) {
+        void* dst = st->gsub[i & 1];
+        int rc = coarse_step_mapped(&st->g, st->p.n, mn, cur, cur_bs, cur_map, dst, st->nn, nullptr, stream);
+        if (rc) return rc;
+        cur = dst;
+        cur_bs = st->nn;
+        cur_map = nullptr;
+    }
+    return coarse_step_mapped(&st->g, st->p.n, mn, cur, cur_bs, cur_map, out, out_bs, out_map, stream);
 }
 
 static unsigned grid_for(long long total, int threads) {
@@ -408,7 +430,7 @@ static int enqueue(ac_parareal* st, int k, int m, int nwork, cudaStream_t stream
         for (int n = 0; n < s; ++n) {
             const int mn = sweeping(st, m, n);
             if (!mn) break;
-            rc = coarse_step_mapped(&st->g, st->p.n, mn, static_cast<char*>(st->Ua) + n * fb, nn * (s + 1),
+            rc = coarse_apply(st, mn, static_cast<char*>(st->Ua) + n * fb, nn * (s + 1),
                                     st->d_map, static_cast<char*>(st->Gold) + n * fb, nn * s, st->d_map, stream);
             if (rc) return rc;
             if ((rc = copy_slice(st, st->Ua, st->Gold, n + 1, n, s + 1, s, mn, stream))) return rc;
@@ -435,8 +457,8 @@ static int enqueue(ac_parareal* st, int k, int m, int nwork, cudaStream_t stream
     for (int n = k; n < s; ++n) {
         const int mn = sweeping(st, m, n);
         if (!mn) break;
-        rc = coarse_step_mapped(&st->g, st->p.n, mn, static_cast<char*>(st->Ub) + n * fb, nn * (s + 1), st->d_map,
-                                st->gtmp, nn, nullptr, stream);
+        rc = coarse_apply(st, mn, static_cast<char*>(st->Ub) + n * fb, nn * (s + 1), st->d_map, st->gtmp, nn,
+                          nullptr, stream);
         if (rc) return rc;
         if ((rc = correct(st, st->Ub, n, st->gtmp, mn, stream))) return rc;
     }
@@ -456,8 +478,8 @@ static void account(ac_parareal* st, int k, int m, int nwork) {
     for (int n = k; n < st->s; ++n) {
         const int mn = sweeping(st, m, n);
         if (!mn) break;
-        st->stats.coarse_calls += 1;
-        st->stats.coarse_cells += (long long)mn * st->nn;
+        st->stats.coarse_calls += st->g_sub;
+        st->stats.coarse_cells += (long long)mn * st->nn * st->g_sub;
     }
 }
 
@@ -825,6 +847,21 @@ extern "C" int ac_parareal_enable_graphs(ac_parareal* state, int on) {
     using namespace acpr;
     ACPR_CHECK_ARG(state, "null state");
     state->graphs = on != 0;
+    return AC_OK;
+}
+
+extern "C" int ac_parareal_set_coarse_substeps(ac_parareal* state, int substeps) {
+    using namespace acpr;
+    ACPR_CHECK_ARG(state, "null state");
+    ACPR_CHECK_ARG(substeps >= 1 && substeps <= 64, "coarse substeps must be 1..64 (got %d)", substeps);
+    if (substeps > 1 && !state->gsub[0]) {
+        const size_t bytes = state->esz * size_t(state->nn) * state->problems;
+        ACPR_CUDA(cudaMalloc(&state->gsub[0], bytes));
+        ACPR_CUDA(cudaMalloc(&state->gsub[1], bytes));
+    }
+    state->g_sub = substeps;
+    for (auto& kv : state->graph_cache) cudaGraphExecDestroy(kv.second.first);
+    state->graph_cache.clear();
     return AC_OK;
 }
 

@@ -56,6 +56,66 @@ def test_plain_f64_workload_end_to_end():
     assert np.allclose(incs, ref["res_l2"], rtol=1e-6, atol=1e-14)
 
 
+@pytest.mark.parametrize("m", [2, 3])
+def test_coarse_composition_matches_oracle_f64(m):
+    """G composed m times per slice (the remark after Algorithm 2), float64:
+    the k = 0 sweep and every later iterate match the oracle's Algorithm 2
+    with the same composition to 1e-10, and the handle counts m coarse
+    applications per evaluation."""
+    w = I.PLAIN_F64_64
+    u0 = w.ics()
+    wt, bs = w.weights()
+    fp = G.FineParams(w.n, w.eps, w.S, w.dt, variant=w.variant, precision=G.AC_F64)
+    net = G.CoarseNet(w.layers, w.channels, wt, bs, act=w.act, precision=G.AC_F64)
+    s, c, kmax = 6, 40, 3
+    pr = G.Parareal(fp, net, torch.tensor(u0, device="cuda"), s, c)
+    pr.set_coarse_substeps(m)
+    pr.iterate()  # k = 0
+    ref0 = O.parareal(O.params(w.n, w.eps, w.S, w.dt, w.variant), O.CnnSpec(w.layers, w.channels, wt, bs, act=w.act),
+                      s, c, kmax=0, tol=0.0, u0=u0[0], coarse_repeat=m)
+    assert np.abs(pr.trajectory()[0].cpu().numpy() - ref0["U"]).max() < 1e-10
+    incs = [pr.iterate()[0][0] for _ in range(kmax)]
+    ref = O.parareal(O.params(w.n, w.eps, w.S, w.dt, w.variant), O.CnnSpec(w.layers, w.channels, wt, bs, act=w.act),
+                     s, c, kmax=kmax, tol=0.0, u0=u0[0], coarse_repeat=m)
+    assert np.abs(pr.trajectory()[0].cpu().numpy() - ref["U"]).max() < 1e-10
+    assert np.allclose(incs, ref["res_l2"], rtol=1e-6, atol=1e-14)
+    st = pr.stats()
+    assert st["coarse_calls"] % m == 0 and st["coarse_calls"] > 0
+
+
+def test_coarse_composition_exactness_f32():
+    """With G composed three times, slices 0..k are still the sequential fine
+    solve bit for bit after k iterations (Sec. 3.3), in float32 with the bf16
+    conv; switching back to m = 1 restores the plain-G iterates."""
+    n, s, c = 64, 5, 30
+    fp = G.FineParams(n, 0.04, 2.0, 1e-4, variant=G.AC_MASS_CONSERVING, precision=G.AC_F32)
+    wt, bs = I.cnn_weights(6, 32, seed=0)
+    net = G.CoarseNet(6, 32, wt.astype(np.float32), bs.astype(np.float32), act=1, precision=G.AC_F32)
+    u0 = torch.tensor(np.stack([I.random_field(n, 7, zero_mean=True), I.random_field(n, 8, zero_mean=True)]),
+                      dtype=torch.float32, device="cuda")
+    seq = [u0]
+    for j in range(s):
+        seq.append(G.ac_fine_propagate_slices(fp, c, seq[-1]))
+    seq = torch.stack(seq, 1)
+    pr = G.Parareal(fp, net, u0, s, c)
+    pr.set_coarse_substeps(3)
+    pr.enable_graphs(True)
+    pr.iterate()
+    g3 = u0
+    for _ in range(3):
+        g3 = G.cnn_coarse_step(net, g3)
+    assert torch.equal(pr.trajectory()[:, 1], g3)
+    for k in range(1, s + 1):
+        pr.iterate()
+        assert torch.equal(pr.trajectory()[:, : k + 1], seq[:, : k + 1]), k
+    plain = G.Parareal(fp, net, u0, s, c)
+    plain.iterate()
+    pr.set_coarse_substeps(1)
+    pr.reset(u0)
+    pr.iterate()
+    assert torch.equal(pr.trajectory(), plain.trajectory())
+
+
 def test_exactness_on_gpu_f32():
     """After k iterations slices 0..k equal the GPU's own sequential fine solve
     bitwise (Sec. 3.3), in float32 with the bf16 conv."""

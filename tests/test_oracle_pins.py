@@ -396,6 +396,37 @@ def test_parareal_reuse_equals_literal_algorithm():
         assert np.array_equal(a["res_l2"], b["res_l2"])
 
 
+def test_parareal_coarse_composition_of_fine_is_longer_fine():
+    """Composing G = F over c0 steps m times is F over m*c0 steps (the coarse
+    composition of the remark after Algorithm 2), so the iterates are
+    identical to those with coarse_steps = m*c0, and each evaluation counts m
+    applications."""
+    p, _, n, s, c, u0 = _small_problem(1)
+    for m in (2, 3):
+        a = O.parareal(p, None, s, c, kmax=3, tol=0.0, u0=u0, coarse_steps=2, coarse_repeat=m)
+        b = O.parareal(p, None, s, c, kmax=3, tol=0.0, u0=u0, coarse_steps=2 * m)
+        assert np.array_equal(a["U"], b["U"])
+        assert np.array_equal(a["res_l2"], b["res_l2"])
+        assert a["g_calls"] == m * b["g_calls"]
+
+
+def test_parareal_coarse_composition_first_sweep_and_exactness():
+    """With G composed twice the k = 0 sweep is U_{j+1} = G(G(U_j)) (brute force
+    with the network), and after k = s iterations the trajectory is still the
+    sequential fine solve (Sec. 3.3: exactness does not depend on G)."""
+    p, G, n, s, c, u0 = _small_problem(0)
+    r = O.parareal(p, G, s, c, kmax=0, tol=0.0, u0=u0, coarse_repeat=2)
+    u = u0.copy()
+    for j in range(s):
+        u = O.cnn_forward(G, O.cnn_forward(G, u))
+        assert np.array_equal(r["U"][j + 1], u)
+    r = O.parareal(p, G, s, c, kmax=s, tol=0.0, u0=u0, coarse_repeat=2)
+    seq = [u0]
+    for j in range(s):
+        seq.append(O.fine_propagate(p, c, seq[-1]))
+    assert np.array_equal(r["U"], np.stack(seq))
+
+
 def test_residual_definition():
     """Relative L2 over slices 1..s and the sup norm (slice 0 is the fixed IC)."""
     Un = np.zeros((3, 2, 2)); Uo = np.zeros((3, 2, 2))
