@@ -109,6 +109,29 @@ def cnn_weights(layers: int, channels: int, seed: int, sigma: float = 0.01):
     return normal(seed, STREAM_WEIGHTS, nw, sigma), normal(seed, STREAM_BIAS, nb, sigma)
 
 
+def acnn_layer_dims(channels: int, blocks: int):
+    """(cin, cout) of each convolution of the ResBlock ACNN, in parameter order:
+    input conv, two per block, output conv."""
+    return [(1, channels)] + [(channels, channels)] * (2 * blocks) + [(channels, 1)]
+
+
+def acnn_weights(channels: int, blocks: int, seed: int, gain: float = 1.0):
+    """Initial ResBlock ACNN parameters: every weight and bias of a convolution
+    with fan-in 9 cin uniform in (-gain/sqrt(9 cin), gain/sqrt(9 cin)) (the usual
+    default initialisation of a 3x3 convolution).  Returns (w, b) float64 in the
+    concatenated layout of the network's parameters."""
+    dims = acnn_layer_dims(channels, blocks)
+    w, b = [], []
+    ow = ob = 0
+    for ci, co in dims:
+        bound = gain / np.sqrt(9.0 * ci)
+        w.append(bound * (2.0 * uniform01(seed, STREAM_WEIGHTS, ci * co * 9, offset=ow) - 1.0))
+        b.append(bound * (2.0 * uniform01(seed, STREAM_BIAS, co, offset=ob) - 1.0))
+        ow += ci * co * 9
+        ob += co
+    return np.concatenate(w), np.concatenate(b)
+
+
 @dataclasses.dataclass(frozen=True)
 class Workload:
     """One Allen-Cahn Parareal workload (all problems share these settings)."""

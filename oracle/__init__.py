@@ -37,6 +37,12 @@ class Cnn(C.Structure):
                 ("w", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double))]
 
 
+class Acnn(C.Structure):
+    _fields_ = [("channels", C.c_int), ("blocks", C.c_int), ("mass_fix", C.c_int), ("limiter", C.c_int),
+                ("lo", C.c_double), ("hi", C.c_double),
+                ("w", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double))]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle (gcc, -O2, no FMA contraction so x86 and Arm agree)."""
     os.makedirs(_BUILD, exist_ok=True)
@@ -83,6 +89,17 @@ def lib():
             L.or_parareal_rep.argtypes = [C.POINTER(Params), C.POINTER(Cnn), C.c_int, C.c_int, C.c_int, C.c_int,
                                           C.c_int, C.c_double, C.c_int, dp, dp, dp, dp, C.POINTER(C.c_int)]
             L.or_parareal_rep.restype = C.c_long
+            L.or_acnn_param_counts.argtypes = [C.POINTER(Acnn), C.POINTER(C.c_long)]
+            L.or_acnn_param_counts.restype = C.c_long
+            L.or_acnn_forward.argtypes = [C.POINTER(Acnn), C.c_int, C.c_int, dp, dp]
+            L.or_acnn_backward.argtypes = [C.POINTER(Acnn), C.c_int, C.c_int, dp, dp, dp, dp]
+            L.or_loss_acn.argtypes = [C.POINTER(Params), C.c_int, dp, dp, dp]
+            L.or_loss_acn.restype = C.c_double
+            L.or_adam.argtypes = [dp, dp, dp, dp, C.c_long, C.c_double, C.c_double, C.c_double, C.c_double,
+                                  C.c_int]
+            L.or_acnn_train.argtypes = [C.POINTER(Params), C.POINTER(Acnn), dp, dp, C.c_int, dp,
+                                        C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                                        C.c_double, C.c_double, C.c_double, dp, dp, C.POINTER(C.c_int), dp]
             _lib = L
     return _lib
 
@@ -109,6 +126,85 @@ class CnnSpec:
         self.b = _f64(b).ravel().copy()
         self.s = Cnn(int(layers), int(channels), int(act), int(residual), int(mass_fix),
                      int(limiter), int(bf16), float(lo), float(hi), _dp(self.w), _dp(self.b))
+
+
+class AcnnSpec:
+    """The paper's ResBlock ACNN / mACNN (Sec. 3.2) with float64 copies of its
+    parameters: input conv 1 -> C, `blocks` blocks x -> x + tanh(conv(tanh(conv(x)))),
+    output conv C -> 1, then the mass shift and the bound limiter."""
+
+    def __init__(self, channels, blocks, w, b, mass_fix=0, limiter=0, lo=-1.0, hi=1.0):
+        self.w = _f64(w).ravel().copy()
+        self.b = _f64(b).ravel().copy()
+        self.s = Acnn(int(channels), int(blocks), int(mass_fix), int(limiter), float(lo), float(hi),
+                      _dp(self.w), _dp(self.b))
+        nb = C.c_long()
+        nw = lib().or_acnn_param_counts(C.byref(self.s), C.byref(nb))
+        if self.w.size != nw or self.b.size != nb.value:
+            raise ValueError(f"ACNN C={channels} blocks={blocks} takes {nw} weights and {nb.value} biases")
+
+
+def acnn_param_counts(channels: int, blocks: int):
+    """(number of weights, number of biases) of the ResBlock ACNN."""
+    d = Acnn(int(channels), int(blocks), 0, 0, 0.0, 0.0, None, None)
+    nb = C.c_long()
+    nw = lib().or_acnn_param_counts(C.byref(d), C.byref(nb))
+    return int(nw), int(nb.value)
+
+
+def acnn_forward(spec: AcnnSpec, u) -> np.ndarray:
+    u = _f64(u)
+    out = np.empty_like(u)
+    batch = 1 if u.ndim == 2 else u.shape[0]
+    lib().or_acnn_forward(C.byref(spec.s), u.shape[-1], batch, _dp(u), _dp(out))
+    return out
+
+
+def acnn_backward(spec: AcnnSpec, u, gout):
+    """(dL/dW, dL/db) summed over the batch for gout = dL/d(output)."""
+    u, gout = _f64(u), _f64(gout)
+    batch = 1 if u.ndim == 2 else u.shape[0]
+    gw = np.empty_like(spec.w)
+    gb = np.empty_like(spec.b)
+    lib().or_acnn_backward(C.byref(spec.s), u.shape[-1], batch, _dp(u), _dp(gout), _dp(gw), _dp(gb))
+    return gw, gb
+
+
+def loss_acn(p: Params, U0, U1, grad: bool = True):
+    """Eq. loss_ACN with time step p.dt: (loss, dL/dU1 or None)."""
+    U0, U1 = _f64(U0), _f64(U1)
+    batch = 1 if U0.ndim == 2 else U0.shape[0]
+    g = np.empty_like(U1) if grad else None
+    loss = lib().or_loss_acn(C.byref(p), batch, _dp(U0), _dp(U1), _dp(g) if grad else None)
+    return loss, g
+
+
+def adam(w, g, m, v, lr, b1, b2, eps, t):
+    """One Adam step in place on float64 arrays w, m, v."""
+    for a in (w, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = _f64(g)
+    lib().or_adam(_dp(w), _dp(g), _dp(m), _dp(v), w.size, lr, b1, b2, eps, int(t))
+
+
+def acnn_train(p: Params, spec: AcnnSpec, U0s, perm, q, steps, b_inner, lr=1e-3, b1=0.9, b2=0.999, aeps=1e-8,
+               state=None):
+    """Algorithm 1 on `spec` (parameters updated in place).  perm: [epochs][R]
+    visiting order.  state: dict(m, v, t) carried between calls.  Returns
+    (losses per update, state)."""
+    U0s = _f64(U0s)
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    epochs, R = perm.shape
+    nw, nb = spec.w.size, spec.b.size
+    if state is None:
+        state = {"m": np.zeros(nw + nb), "v": np.zeros(nw + nb), "t": 0}
+    t = C.c_int(state["t"])
+    losses = np.zeros(epochs * (R // q) * steps * b_inner)
+    lib().or_acnn_train(C.byref(p), C.byref(spec.s), _dp(spec.w), _dp(spec.b), R, _dp(U0s),
+                        perm.ctypes.data_as(C.POINTER(C.c_int)), int(q), int(steps), int(b_inner), epochs,
+                        lr, b1, b2, aeps, _dp(state["m"]), _dp(state["v"]), C.byref(t), _dp(losses))
+    state["t"] = t.value
+    return losses, state
 
 
 # ------------------------------------------------------------------ FFT --

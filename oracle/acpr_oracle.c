@@ -619,3 +619,291 @@ long or_parareal_rep(const or_params* p, const or_cnn* coarse, int coarse_steps,
 #undef GAPPLY
     return gcalls;
 }
+
+/* ------------------------------------------------ ResBlock ACNN (Sec. 3.2) */
+/* The paper's coarse network: an input convolution 1 -> C, `blocks` residual
+ * blocks of two C -> C convolutions, an output convolution C -> 1; tanh after
+ * every convolution but the output one; circular padding; then the mACNN mass
+ * shift and the bound limiter.  A block maps x to x + tanh(conv2(tanh(conv1(x)))).
+ * Parameters: concat of W_in[C][1][3][3], per block W_1, W_2 [C][C][3][3],
+ * W_out[1][C][3][3]; biases in the same order (b_in[C], b_1[C], b_2[C],
+ * b_out[1]). */
+typedef struct {
+    int channels;
+    int blocks;
+    int mass_fix;   /* 1: add mean(input) - mean(output) */
+    int limiter;    /* 1: clamp to [lo, hi] */
+    double lo, hi;
+    const double* w;
+    const double* b;
+} or_acnn;
+
+static int acnn_convs(const or_acnn* d) { return 2 + 2 * d->blocks; }
+
+static void acnn_dims(const or_acnn* d, int l, int* cin, int* cout) {
+    *cin = (l == 0) ? 1 : d->channels;
+    *cout = (l == acnn_convs(d) - 1) ? 1 : d->channels;
+}
+
+static void acnn_offsets(const or_acnn* d, int l, int* wo, int* bo) {
+    int w = 0, b = 0;
+    for (int i = 0; i < l; i++) { int ci, co; acnn_dims(d, i, &ci, &co); w += ci * co * 9; b += co; }
+    *wo = w; *bo = b;
+}
+
+long or_acnn_param_counts(const or_acnn* d, long* nb) {
+    int wo, bo;
+    acnn_offsets(d, acnn_convs(d), &wo, &bo);
+    if (nb) *nb = bo;
+    return wo;
+}
+
+/* Saved state of one forward pass: x[0..R] block inputs (x[R] feeds the
+ * output conv), h[R] and t[R] the two tanh outputs of each block, o the
+ * output conv, s the field after the mass shift (before the limiter). */
+typedef struct { double *x, *h, *t, *o, *s; } acnn_saved;
+
+static void acnn_forward_saved(const or_acnn* d, int n, const double* u, double* out, acnn_saved* sv) {
+    size_t m = (size_t)n * n;
+    int C = d->channels, R = d->blocks;
+    int wo, bo;
+    acnn_offsets(d, 0, &wo, &bo);
+    conv3x3(n, 1, C, d->w + wo, d->b + bo, u, sv->x);
+    for (size_t i = 0; i < (size_t)C * m; i++) sv->x[i] = tanh(sv->x[i]);
+    for (int r = 0; r < R; r++) {
+        double* x = sv->x + (size_t)r * C * m;
+        double* xn = sv->x + (size_t)(r + 1) * C * m;
+        double* h = sv->h + (size_t)r * C * m;
+        double* t = sv->t + (size_t)r * C * m;
+        acnn_offsets(d, 1 + 2 * r, &wo, &bo);
+        conv3x3(n, C, C, d->w + wo, d->b + bo, x, h);
+        for (size_t i = 0; i < (size_t)C * m; i++) h[i] = tanh(h[i]);
+        acnn_offsets(d, 2 + 2 * r, &wo, &bo);
+        conv3x3(n, C, C, d->w + wo, d->b + bo, h, t);
+        for (size_t i = 0; i < (size_t)C * m; i++) { t[i] = tanh(t[i]); xn[i] = x[i] + t[i]; }
+    }
+    acnn_offsets(d, 1 + 2 * R, &wo, &bo);
+    conv3x3(n, C, 1, d->w + wo, d->b + bo, sv->x + (size_t)R * C * m, sv->o);
+    double shift = 0.0;
+    if (d->mass_fix) {
+        double su = 0.0, so = 0.0;
+        for (size_t i = 0; i < m; i++) { su += u[i]; so += sv->o[i]; }
+        shift = (su - so) / (double)m;
+    }
+    for (size_t i = 0; i < m; i++) {
+        sv->s[i] = sv->o[i] + shift;
+        double v = sv->s[i];
+        if (d->limiter) v = v < d->lo ? d->lo : (v > d->hi ? d->hi : v);
+        out[i] = v;
+    }
+}
+
+static acnn_saved acnn_alloc(const or_acnn* d, int n) {
+    size_t m = (size_t)n * n, C = d->channels, R = d->blocks;
+    acnn_saved sv;
+    sv.x = malloc(sizeof(double) * (R + 1) * C * m);
+    sv.h = malloc(sizeof(double) * (R ? R : 1) * C * m);
+    sv.t = malloc(sizeof(double) * (R ? R : 1) * C * m);
+    sv.o = malloc(sizeof(double) * m);
+    sv.s = malloc(sizeof(double) * m);
+    return sv;
+}
+
+static void acnn_free(acnn_saved* sv) { free(sv->x); free(sv->h); free(sv->t); free(sv->o); free(sv->s); }
+
+void or_acnn_forward(const or_acnn* d, int n, int batch, const double* u, double* out) {
+    size_t m = (size_t)n * n;
+    acnn_saved sv = acnn_alloc(d, n);
+    for (int p = 0; p < batch; p++) acnn_forward_saved(d, n, u + p * m, out + p * m, &sv);
+    acnn_free(&sv);
+}
+
+/* dL/dW of one 3x3 circular correlation: gw[o][c][a][e] += sum_ij g[o][i][j] in[c][i+a-1][j+e-1],
+ * gb[o] += sum_ij g[o][i][j]. */
+static void conv3x3_wgrad(int n, int cin, int cout, const double* in, const double* g, double* gw, double* gb) {
+    size_t m = (size_t)n * n;
+    for (int o = 0; o < cout; o++) {
+        for (size_t i = 0; i < m; i++) gb[o] += g[o * m + i];
+        for (int c = 0; c < cin; c++)
+            for (int a = 0; a < 3; a++)
+                for (int e = 0; e < 3; e++) {
+                    double acc = 0.0;
+                    for (int i = 0; i < n; i++)
+                        for (int j = 0; j < n; j++)
+                            acc += g[o * m + (size_t)i * n + j] *
+                                   in[c * m + (size_t)((i + a - 1 + n) % n) * n + (j + e - 1 + n) % n];
+                    gw[((o * cin + c) * 3 + a) * 3 + e] += acc;
+                }
+    }
+}
+
+/* Adjoint of the correlation with respect to its input: every output
+ * gradient scattered back through the stencil (gin is overwritten). */
+static void conv3x3_dgrad(int n, int cin, int cout, const double* W, const double* g, double* gin) {
+    size_t m = (size_t)n * n;
+    memset(gin, 0, sizeof(double) * cin * m);
+    for (int o = 0; o < cout; o++)
+        for (int i = 0; i < n; i++)
+            for (int j = 0; j < n; j++) {
+                double gv = g[o * m + (size_t)i * n + j];
+                for (int c = 0; c < cin; c++)
+                    for (int a = 0; a < 3; a++)
+                        for (int e = 0; e < 3; e++)
+                            gin[c * m + (size_t)((i + a - 1 + n) % n) * n + (j + e - 1 + n) % n] +=
+                                W[((o * cin + c) * 3 + a) * 3 + e] * gv;
+            }
+}
+
+/* Weight and bias gradients of the ACNN, summed over the batch, for
+ * gout = dL/d(output) (after the limiter).  gw, gb are overwritten.  The
+ * limiter passes the gradient where lo < s < hi (zero where it clamps); the
+ * mass shift contributes -mean(g) (its input term does not reach the
+ * parameters). */
+void or_acnn_backward(const or_acnn* d, int n, int batch, const double* u, const double* gout,
+                      double* gw, double* gb) {
+    size_t m = (size_t)n * n;
+    int C = d->channels, R = d->blocks;
+    long nb, nw = or_acnn_param_counts(d, &nb);
+    memset(gw, 0, sizeof(double) * nw);
+    memset(gb, 0, sizeof(double) * nb);
+    acnn_saved sv = acnn_alloc(d, n);
+    double* out = malloc(sizeof(double) * m);
+    double* go = malloc(sizeof(double) * m);
+    double* gx = malloc(sizeof(double) * C * m);
+    double* gz = malloc(sizeof(double) * C * m);
+    double* gh = malloc(sizeof(double) * C * m);
+    for (int p = 0; p < batch; p++) {
+        acnn_forward_saved(d, n, u + p * m, out, &sv);
+        for (size_t i = 0; i < m; i++) {
+            double g = gout[p * m + i];
+            if (d->limiter && !(sv.s[i] > d->lo && sv.s[i] < d->hi)) g = 0.0;
+            go[i] = g;
+        }
+        if (d->mass_fix) {
+            double mean = 0.0;
+            for (size_t i = 0; i < m; i++) mean += go[i];
+            mean /= (double)m;
+            for (size_t i = 0; i < m; i++) go[i] -= mean;
+        }
+        int wo, bo;
+        acnn_offsets(d, 1 + 2 * R, &wo, &bo);
+        conv3x3_wgrad(n, C, 1, sv.x + (size_t)R * C * m, go, gw + wo, gb + bo);
+        conv3x3_dgrad(n, C, 1, d->w + wo, go, gx);
+        for (int r = R - 1; r >= 0; r--) {
+            const double* x = sv.x + (size_t)r * C * m;
+            const double* h = sv.h + (size_t)r * C * m;
+            const double* t = sv.t + (size_t)r * C * m;
+            for (size_t i = 0; i < (size_t)C * m; i++) gz[i] = gx[i] * (1.0 - t[i] * t[i]);
+            acnn_offsets(d, 2 + 2 * r, &wo, &bo);
+            conv3x3_wgrad(n, C, C, h, gz, gw + wo, gb + bo);
+            conv3x3_dgrad(n, C, C, d->w + wo, gz, gh);
+            for (size_t i = 0; i < (size_t)C * m; i++) gz[i] = gh[i] * (1.0 - h[i] * h[i]);
+            acnn_offsets(d, 1 + 2 * r, &wo, &bo);
+            conv3x3_wgrad(n, C, C, x, gz, gw + wo, gb + bo);
+            conv3x3_dgrad(n, C, C, d->w + wo, gz, gh);
+            for (size_t i = 0; i < (size_t)C * m; i++) gx[i] += gh[i];
+        }
+        for (size_t i = 0; i < (size_t)C * m; i++) gz[i] = gx[i] * (1.0 - sv.x[i] * sv.x[i]);
+        acnn_offsets(d, 0, &wo, &bo);
+        conv3x3_wgrad(n, 1, C, u + p * m, gz, gw + wo, gb + bo);
+    }
+    acnn_free(&sv);
+    free(out); free(go); free(gx); free(gz); free(gh);
+}
+
+/* Scheme-residual loss (Eq. loss_ACN) of a batch of pairs (U_n, U_{n+1}) with
+ * the time step p->dt:  r = U1 - U0 - dt/2 (eps^2 Lap_h (U1 + U0) + f(U1) + f(U0)
+ * - g(U1) - g(U0)),  g(U) = mean f(U) for the mass-conserving variant, 0 for
+ * the classic one;  L = sum r^2 / (batch N^2).  If grad != NULL it receives
+ * dL/dU1 = 2/(batch N^2) (r - dt/2 (eps^2 Lap_h r + f'(U1) r - [mass] f'(U1) mean r))
+ * (Lap_h is symmetric; d g(U1)/dU1 = f'(U1)/N^2 at every entry). */
+double or_loss_acn(const or_params* p, int batch, const double* U0, const double* U1, double* grad) {
+    int n = p->n;
+    size_t m = (size_t)n * n;
+    double h = p->length / n, e2 = p->eps * p->eps, dt = p->dt;
+    double* s = malloc(sizeof(double) * m);
+    double* ls = malloc(sizeof(double) * m);
+    double* r = malloc(sizeof(double) * m);
+    double total = 0.0;
+    for (int b = 0; b < batch; b++) {
+        const double* a = U0 + b * m;
+        const double* c = U1 + b * m;
+        double g0 = 0.0, g1 = 0.0;
+        if (p->variant == 1) {
+            for (size_t i = 0; i < m; i++) { g0 += f_dw(a[i]); g1 += f_dw(c[i]); }
+            g0 /= (double)m; g1 /= (double)m;
+        }
+        for (size_t i = 0; i < m; i++) s[i] = a[i] + c[i];
+        apply_lap(n, h, s, ls);
+        double rmean = 0.0;
+        for (size_t i = 0; i < m; i++) {
+            r[i] = c[i] - a[i] - 0.5 * dt * (e2 * ls[i] + f_dw(c[i]) + f_dw(a[i]) - g1 - g0);
+            total += r[i] * r[i];
+            rmean += r[i];
+        }
+        rmean /= (double)m;
+        if (grad) {
+            double scale = 2.0 / ((double)batch * (double)m);
+            apply_lap(n, h, r, ls);
+            for (size_t i = 0; i < m; i++) {
+                double fp = fprime_dw(c[i]);
+                double jr = e2 * ls[i] + fp * r[i] - (p->variant == 1 ? fp * rmean : 0.0);
+                grad[b * m + i] = scale * (r[i] - 0.5 * dt * jr);
+            }
+        }
+    }
+    free(s); free(ls); free(r);
+    return total / ((double)batch * (double)m);
+}
+
+/* One Adam update (Kingma & Ba, Algorithm 1) of `count` parameters at step t >= 1:
+ * m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2, w -= lr (m/(1-b1^t)) / (sqrt(v/(1-b2^t)) + eps). */
+void or_adam(double* w, const double* g, double* mo, double* vo, long count, double lr, double b1, double b2,
+             double eps, int t) {
+    double c1 = 1.0 - pow(b1, t), c2 = 1.0 - pow(b2, t);
+    for (long i = 0; i < count; i++) {
+        mo[i] = b1 * mo[i] + (1.0 - b1) * g[i];
+        vo[i] = b2 * vo[i] + (1.0 - b2) * g[i] * g[i];
+        w[i] -= lr * (mo[i] / c1) / (sqrt(vo[i] / c2) + eps);
+    }
+}
+
+/* Algorithm 1: training of the ACNN with the scheme-residual loss.
+ * For each epoch e the R initial conditions are visited in the order
+ * perm[e][0..R-1], cut into R/q subsets of q.  For each subset, U starts at
+ * its q initial conditions; for each of `steps` time steps, b inner updates
+ * each predict U1 = G(U; theta), take the loss of (U, U1) and one Adam step
+ * on theta; U then becomes the U1 of the last inner update.  w, b (the
+ * network's parameters, updated in place), m, v (Adam moments, w then b) and
+ * *t (Adam step count) carry over between calls.  losses receives one value
+ * per update, in order (epochs * (R/q) * steps * b_inner). */
+void or_acnn_train(const or_params* p, or_acnn* d, double* w, double* bias, int R, const double* U0s,
+                   const int* perm, int q, int steps, int b_inner, int epochs, double lr, double b1, double b2,
+                   double aeps, double* mo, double* vo, int* t, double* losses) {
+    int n = p->n;
+    size_t m = (size_t)n * n;
+    long nb, nw = or_acnn_param_counts(d, &nb);
+    d->w = w;
+    d->b = bias;
+    double* U = malloc(sizeof(double) * q * m);
+    double* U1 = malloc(sizeof(double) * q * m);
+    double* g = malloc(sizeof(double) * q * m);
+    double* gw = malloc(sizeof(double) * (nw + nb));
+    long li = 0;
+    for (int e = 0; e < epochs; e++)
+        for (int sub = 0; sub < R / q; sub++) {
+            for (int j = 0; j < q; j++) memcpy(U + j * m, U0s + (size_t)perm[e * R + sub * q + j] * m, sizeof(double) * m);
+            for (int st = 0; st < steps; st++) {
+                for (int k = 0; k < b_inner; k++) {
+                    or_acnn_forward(d, n, q, U, U1);
+                    losses[li++] = or_loss_acn(p, q, U, U1, g);
+                    or_acnn_backward(d, n, q, U, g, gw, gw + nw);
+                    *t += 1;
+                    or_adam(w, gw, mo, vo, nw, lr, b1, b2, aeps, *t);
+                    or_adam(bias, gw + nw, mo + nw, vo + nw, nb, lr, b1, b2, aeps, *t);
+                }
+                memcpy(U, U1, sizeof(double) * q * m);
+            }
+        }
+    free(U); free(U1); free(g); free(gw);
+}
