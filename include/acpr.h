@@ -296,6 +296,103 @@ int mse_loss_grad(const float* pred, const float* target, long long count, doubl
                   acpr_stream stream);
 
 /* ------------------------------------------------------------------------
+ * The paper's ResBlock ACNN / mACNN (Sec. 3.2) and its training with the
+ * scheme-residual loss (Eq. loss_ACN, Algorithm 1).
+ *
+ * Network: an input 3x3 convolution 1 -> C, `blocks` residual blocks that map
+ * x to x + tanh(conv2(tanh(conv1(x)))) (C -> C each), an output convolution
+ * C -> 1; tanh after every convolution but the output one; circular padding 1,
+ * cross-correlation as torch.nn.Conv2d; then the mACNN mass shift (add
+ * mean(input) - mean(output)) and the bound limiter (clamp to [lo, hi]).
+ * There is no global skip: the output layer produces U_{n+1}.
+ * Parameters (device, `precision` floats): w = W_in[C][1][3][3], then per
+ * block W_1[C][C][3][3], W_2[C][C][3][3], then W_out[1][C][3][3]; b = b_in[C],
+ * per block b_1[C], b_2[C], then b_out[1].  Arithmetic in the field precision
+ * on CUDA cores (the float32 tanh is 1 - 2/(1 + e^{2x}) on the fast
+ * exponential, absolute error < 1e-6).  C = 4 or 16, blocks 0..4.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int channels;    /* C: 4 or 16 */
+    int blocks;      /* residual blocks, 0..4 */
+    int mass_fix;    /* 1: mACNN mass shift */
+    int limiter;     /* 1: clamp to [lo, hi] */
+    double lo, hi;
+    int precision;   /* AC_F64 or AC_F32 (parameters, fields, arithmetic) */
+    void* w;         /* device parameters, layouts above */
+    void* b;
+} acnn_desc;
+
+/* Number of weights of the network (and of biases in *num_bias if not NULL);
+ * -1 if the shape is not built. */
+long long acnn_param_count(int channels, int blocks, long long* num_bias);
+
+/* Inference handle: acnn_create copies the parameters once (synchronously)
+ * into the handle, which passes them to its kernels by value.  C = 4 with at
+ * most 3 blocks runs one fused kernel per 32 x 32 output tile (all layers in
+ * shared memory); other shapes run the per-layer kernels. */
+typedef struct acnn_net acnn_net;
+int acnn_create(const acnn_desc* desc, acnn_net** out);
+void acnn_destroy(acnn_net* net);
+
+/* Device scratch bytes acnn_forward needs for `batch` n x n fields. */
+size_t acnn_work_bytes(const acnn_net* net, int n, int batch);
+
+/* U_out = G(U_in) for `batch` fields, device [batch][n][n] in the net's
+ * precision; n a power of two, 32 <= n <= 1024; u_in and u_out must not
+ * overlap.  work: acnn_work_bytes() bytes.  Asynchronous on `stream`. */
+int acnn_forward(const acnn_net* net, int n, int batch, const void* u_in, void* u_out, void* work,
+                 size_t work_bytes, acpr_stream stream);
+
+/* Training workspace bytes (saved activations, gradient buffers, reduction
+ * partials) for `batch` fields. */
+size_t acnn_train_bytes(const acnn_desc* desc, int n, int batch);
+
+/* Forward pass with the parameters in desc->w, desc->b (read on the device,
+ * so an update between calls needs no host copy) that saves into train_ws
+ * what acnn_backward needs. */
+int acnn_forward_train(const acnn_desc* desc, int n, int batch, const void* u_in, void* u_out, void* train_ws,
+                       acpr_stream stream);
+
+/* Parameter gradients of the last acnn_forward_train on the same u_in and
+ * train_ws, for grad_out = dL/d(output): written (not added) to grad_w,
+ * grad_b (device, the layouts of desc->w, desc->b), summed over the batch in
+ * a fixed order (deterministic).  The limiter passes the gradient where
+ * lo < value < hi; the mass shift subtracts its field mean. */
+int acnn_backward(const acnn_desc* desc, int n, int batch, const void* u_in, const void* grad_out, void* grad_w,
+                  void* grad_b, void* train_ws, acpr_stream stream);
+
+/* Scheme-residual loss (Eq. loss_ACN) of `batch` pairs (U0, U1) with time step
+ * params->dt:  r = U1 - U0 - dt/2 (eps^2 Lap_h (U1 + U0) + f(U1) + f(U0)
+ * - g(U1) - g(U0)),  g(U) = mean f(U) for AC_MASS_CONSERVING, else 0,
+ * L = sum r^2 / (batch n^2), written to loss_dev[0] (float64).  If grad is not
+ * NULL it receives dL/dU1 (device, field precision).  work: device,
+ * loss_acn_work_bytes(n, batch) bytes.  params->precision gives the field
+ * type; S is unused. */
+size_t loss_acn_work_bytes(int n, int batch);
+int loss_acn(const ac_params* params, int batch, const void* U0, const void* U1, double* loss_dev, void* grad,
+             void* work, acpr_stream stream);
+
+/* One Adam step (Kingma & Ba) on `count` parameters of `precision` at step
+ * t >= 1: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
+int acnn_adam_step(int precision, void* w, const void* grad, void* m, void* v, long long count, double lr,
+                   double beta1, double beta2, double eps, int t, acpr_stream stream);
+
+/* Algorithm 1: train desc's parameters in place with the scheme-residual loss.
+ * U0s: device [R][n][n] initial conditions; perm: HOST int[epochs][R], the
+ * visiting order of each epoch, cut into R/q subsets of q.  For each subset U
+ * starts at its q initial conditions; for each of `steps` time steps, b_inner
+ * updates each predict U1 = G(U), take the loss of (U, U1), its gradient and
+ * one Adam step; U then becomes the U1 of the last update.  adam_m, adam_v:
+ * device moments (weights then biases, zeroed by the caller before the first
+ * call); *t: Adam step count, carried between calls.  losses_dev: device
+ * float64[epochs * (R/q) * steps * b_inner], one loss per update.  Allocates
+ * its workspace per call; SYNCHRONOUS. */
+int acnn_train_alg1(const ac_params* params, const acnn_desc* desc, int R, const void* U0s, const int* perm,
+                    int epochs, int q, int steps, int b_inner, double lr, double beta1, double beta2, double eps,
+                    void* adam_m, void* adam_v, int* t, double* losses_dev, acpr_stream stream);
+
+/* ------------------------------------------------------------------------
  * Parareal driver (Algorithm 2) for `problems` independent problems that
  * share one ac_params, one coarse propagator, s slices of c fine steps.
  * ------------------------------------------------------------------------ */
@@ -304,7 +401,9 @@ typedef struct ac_parareal ac_parareal;
 /* Allocates the device state (trajectory U[problems][s+1][n][n], stored coarse
  * values, fine results, residual scratch) and copies the initial data
  * u0 (device [problems][n][n], precision of params).  *out receives the
- * handle.  The cnn_desc is copied; its device buffers must outlive the handle. */
+ * handle.  The cnn_desc is copied; its device buffers must outlive the handle.
+ * coarse may be NULL when G is the ResBlock ACNN, set with
+ * ac_parareal_set_coarse_acnn before the first iteration. */
 int ac_parareal_create(const ac_params* params, const cnn_desc* coarse, int problems,
                        int num_slices, int steps_per_slice, const void* u0,
                        ac_parareal** out);
@@ -329,6 +428,12 @@ int ac_parareal_enable_graphs(ac_parareal* state, int on);
  * two [problems][n][n] buffers for the intermediate fields.  Drops the
  * handle's captured iteration graphs.  Call between solves. */
 int ac_parareal_set_coarse_substeps(ac_parareal* state, int substeps);
+
+/* Use the ResBlock ACNN `net` as the coarse propagator G of the handle's
+ * solves instead of the conv stack it was created with (NULL switches back).
+ * net must match the handle's precision and outlive its use; allocates the
+ * net's scratch for all problems and drops the captured iteration graphs. */
+int ac_parareal_set_coarse_acnn(ac_parareal* state, const acnn_net* net);
 
 /* Choose the fine propagator F of the handle's solves: scheme 0 = the
  * stabilised semi-implicit step (the default), 1 = the Crank-Nicolson step of

@@ -89,6 +89,9 @@ def lib():
             L.or_parareal_rep.argtypes = [C.POINTER(Params), C.POINTER(Cnn), C.c_int, C.c_int, C.c_int, C.c_int,
                                           C.c_int, C.c_double, C.c_int, dp, dp, dp, dp, C.POINTER(C.c_int)]
             L.or_parareal_rep.restype = C.c_long
+            L.or_parareal_acnn.argtypes = [C.POINTER(Params), C.POINTER(Acnn), C.c_int, C.c_int, C.c_int, C.c_int,
+                                           C.c_double, dp, dp, dp, dp, C.POINTER(C.c_int)]
+            L.or_parareal_acnn.restype = C.c_long
             L.or_acnn_param_counts.argtypes = [C.POINTER(Acnn), C.POINTER(C.c_long)]
             L.or_acnn_param_counts.restype = C.c_long
             L.or_acnn_forward.argtypes = [C.POINTER(Acnn), C.c_int, C.c_int, dp, dp]
@@ -326,7 +329,8 @@ def residual(Unew, Uold):
 
 def parareal(p: Params, coarse, s: int, c: int, kmax: int, tol: float, u0,
              coarse_steps: int = 0, literal: bool = False, coarse_repeat: int = 1):
-    """Algorithm 2.  coarse: CnnSpec, or None for G = F over coarse_steps fine steps.
+    """Algorithm 2.  coarse: CnnSpec, AcnnSpec (the ResBlock ACNN), or None for
+    G = F over coarse_steps fine steps.
     coarse_repeat > 1 composes that propagator with itself per slice (the
     remark after Algorithm 2).
 
@@ -338,6 +342,13 @@ def parareal(p: Params, coarse, s: int, c: int, kmax: int, tol: float, u0,
     rl2 = np.zeros(kmax + 2)
     rmx = np.zeros(kmax + 2)
     it = C.c_int()
+    if isinstance(coarse, AcnnSpec):
+        if literal:
+            raise ValueError("the literal form is built for the conv stack only")
+        g = lib().or_parareal_acnn(C.byref(p), C.byref(coarse.s), int(coarse_repeat), int(s), int(c), int(kmax),
+                                   float(tol), _dp(u0), _dp(U), _dp(rl2), _dp(rmx), C.byref(it))
+        k = it.value
+        return dict(U=U, res_l2=rl2[1:k + 1].copy(), res_max=rmx[1:k + 1].copy(), iters=k, g_calls=g)
     cptr = C.byref(coarse.s) if coarse is not None else None
     g = lib().or_parareal_rep(C.byref(p), cptr, int(coarse_steps), int(coarse_repeat), int(s), int(c), int(kmax),
                               float(tol), int(literal), _dp(u0), _dp(U), _dp(rl2), _dp(rmx),

@@ -530,36 +530,42 @@ void or_residual(int s, int n, const double* Unew, const double* Uold, double* l
  * stored G(U^{k-1}_n) values are reused, and U^k_{k-1} = U^{k-1}_{k-1} makes its
  * G value known).  G is re-evaluated literally as Algorithm 2 states it only
  * when `literal` is set. */
-/* One application of the coarse propagator: the network, or F over
- * coarse_steps fine steps. */
-static void or_coarse_once(const or_params* p, const or_cnn* coarse, int coarse_steps, const double* in,
-                           double* out) {
-    if (coarse) or_cnn_forward(coarse, p->n, in, out);
-    else or_fine_propagate(p, coarse_steps, in, out);
+typedef struct or_acnn_s or_acnn;
+void or_acnn_forward(const or_acnn* d, int n, int batch, const double* u, double* out);
+
+/* The coarse propagator of one solve: the conv stack, the ResBlock ACNN, or
+ * (both NULL) F over coarse_steps fine steps. */
+typedef struct { const or_cnn* cnn; const or_acnn* acnn; int coarse_steps; } or_coarse;
+
+/* One application of the coarse propagator. */
+static void or_coarse_once(const or_params* p, const or_coarse* g, const double* in, double* out) {
+    if (g->acnn) or_acnn_forward(g->acnn, p->n, 1, in, out);
+    else if (g->cnn) or_cnn_forward(g->cnn, p->n, in, out);
+    else or_fine_propagate(p, g->coarse_steps, in, out);
 }
 
 /* The coarse evaluation of a slice: `repeat` applications of the coarse
  * propagator in a row (the composition of the remark after Algorithm 2; 1 is
  * plain G).  tmp holds one field. */
-static void or_coarse_eval(const or_params* p, const or_cnn* coarse, int coarse_steps, int repeat,
-                           const double* in, double* out, double* tmp) {
+static void or_coarse_eval(const or_params* p, const or_coarse* g, int repeat, const double* in, double* out,
+                           double* tmp) {
     size_t m = (size_t)p->n * p->n;
-    if (repeat <= 1) { or_coarse_once(p, coarse, coarse_steps, in, out); return; }
+    if (repeat <= 1) { or_coarse_once(p, g, in, out); return; }
     memcpy(tmp, in, sizeof(double) * m);
     for (int r = 0; r < repeat; r++) {
-        or_coarse_once(p, coarse, coarse_steps, tmp, out);
+        or_coarse_once(p, g, tmp, out);
         if (r + 1 < repeat) memcpy(tmp, out, sizeof(double) * m);
     }
 }
 
-long or_parareal_rep(const or_params* p, const or_cnn* coarse, int coarse_steps, int repeat, int s, int c,
-                     int kmax, double tol, int literal, const double* u0, double* U,
-                     double* res_l2, double* res_max, int* iters);
+static long or_parareal_g(const or_params* p, const or_coarse* g, int repeat, int s, int c, int kmax, double tol,
+                          int literal, const double* u0, double* U, double* res_l2, double* res_max, int* iters);
 
 long or_parareal(const or_params* p, const or_cnn* coarse, int coarse_steps, int s, int c,
                  int kmax, double tol, int literal, const double* u0, double* U,
                  double* res_l2, double* res_max, int* iters) {
-    return or_parareal_rep(p, coarse, coarse_steps, 1, s, c, kmax, tol, literal, u0, U, res_l2, res_max, iters);
+    or_coarse g = {coarse, NULL, coarse_steps};
+    return or_parareal_g(p, &g, 1, s, c, kmax, tol, literal, u0, U, res_l2, res_max, iters);
 }
 
 /* Algorithm 2 with the coarse propagator composed `repeat` times per slice;
@@ -567,6 +573,19 @@ long or_parareal(const or_params* p, const or_cnn* coarse, int coarse_steps, int
 long or_parareal_rep(const or_params* p, const or_cnn* coarse, int coarse_steps, int repeat, int s, int c,
                      int kmax, double tol, int literal, const double* u0, double* U,
                      double* res_l2, double* res_max, int* iters) {
+    or_coarse g = {coarse, NULL, coarse_steps};
+    return or_parareal_g(p, &g, repeat, s, c, kmax, tol, literal, u0, U, res_l2, res_max, iters);
+}
+
+/* Algorithm 2 with the ResBlock ACNN (Sec. 3.2) as G. */
+long or_parareal_acnn(const or_params* p, const or_acnn* coarse, int repeat, int s, int c, int kmax, double tol,
+                      const double* u0, double* U, double* res_l2, double* res_max, int* iters) {
+    or_coarse g = {NULL, coarse, 0};
+    return or_parareal_g(p, &g, repeat, s, c, kmax, tol, 0, u0, U, res_l2, res_max, iters);
+}
+
+static long or_parareal_g(const or_params* p, const or_coarse* gc, int repeat, int s, int c, int kmax, double tol,
+                          int literal, const double* u0, double* U, double* res_l2, double* res_max, int* iters) {
     int n = p->n;
     size_t m = (size_t)n * n;
     double* Uold = malloc(sizeof(double) * m * (s + 1));
@@ -576,7 +595,7 @@ long or_parareal_rep(const or_params* p, const or_cnn* coarse, int coarse_steps,
     double* gt = malloc(sizeof(double) * m);
     long gcalls = 0;
     if (repeat < 1) repeat = 1;
-#define GAPPLY(in, out) do { or_coarse_eval(p, coarse, coarse_steps, repeat, (in), (out), gt); \
+#define GAPPLY(in, out) do { or_coarse_eval(p, gc, repeat, (in), (out), gt); \
                              gcalls += repeat; } while (0)
     /* k = 0: sequential coarse sweep */
     memcpy(U, u0, sizeof(double) * m);
@@ -628,7 +647,7 @@ long or_parareal_rep(const or_params* p, const or_cnn* coarse, int coarse_steps,
  * Parameters: concat of W_in[C][1][3][3], per block W_1, W_2 [C][C][3][3],
  * W_out[1][C][3][3]; biases in the same order (b_in[C], b_1[C], b_2[C],
  * b_out[1]). */
-typedef struct {
+struct or_acnn_s {
     int channels;
     int blocks;
     int mass_fix;   /* 1: add mean(input) - mean(output) */
@@ -636,7 +655,7 @@ typedef struct {
     double lo, hi;
     const double* w;
     const double* b;
-} or_acnn;
+};
 
 static int acnn_convs(const or_acnn* d) { return 2 + 2 * d->blocks; }
 

@@ -40,6 +40,12 @@ class cnn_desc(C.Structure):
                 ("work", C.c_void_p), ("work_bytes", C.c_size_t)]
 
 
+class acnn_desc(C.Structure):
+    _fields_ = [("channels", C.c_int), ("blocks", C.c_int), ("mass_fix", C.c_int), ("limiter", C.c_int),
+                ("lo", C.c_double), ("hi", C.c_double), ("precision", C.c_int), ("w", C.c_void_p),
+                ("b", C.c_void_p)]
+
+
 class ac_parareal_stats(C.Structure):
     _fields_ = [("fine_ms", C.c_double), ("coarse_ms", C.c_double), ("increment_ms", C.c_double),
                 ("fine_launches", C.c_longlong), ("fine_cell_steps", C.c_longlong),
@@ -56,7 +62,10 @@ EXPORTS = ["ac_last_error", "ac_fine_supported", "ac_fine_step", "ac_fine_propag
            "ac_fine_variant_count", "ac_fine_variant_name", "ac_fine_get_variant", "ac_fine_set_variant",
            "ac_fine_autotune", "ac_fine_propagate_work", "ac_fine_trajectory", "ac_fine_adjoint", "ac_energy", "ac_energy_grad",
            "ac_energy_gradient_workspace", "ac_energy_gradient_ic",
-           "cnn_train_bytes", "cnn_forward_train", "cnn_backward", "cnn_adam_step", "mse_loss_grad"]
+           "cnn_train_bytes", "cnn_forward_train", "cnn_backward", "cnn_adam_step", "mse_loss_grad",
+           "acnn_param_count", "acnn_create", "acnn_destroy", "acnn_work_bytes", "acnn_forward", "acnn_train_bytes",
+           "acnn_forward_train", "acnn_backward", "loss_acn_work_bytes", "loss_acn", "acnn_adam_step",
+           "acnn_train_alg1", "ac_parareal_set_coarse_acnn"]
 
 
 def lib_path() -> str:
@@ -126,6 +135,25 @@ def load(build_if_missing: bool = True):
         L.mse_loss_grad.argtypes = [S, S, C.c_longlong, D, S, I, S, S, I, S]
         L.ac_parareal_destroy.argtypes = [S]
         L.ac_parareal_destroy.restype = None
+        L.acnn_param_count.argtypes = [I, I, P(C.c_longlong)]
+        L.acnn_param_count.restype = C.c_longlong
+        L.acnn_create.argtypes = [P(acnn_desc), P(S)]
+        L.acnn_destroy.argtypes = [S]
+        L.acnn_destroy.restype = None
+        L.acnn_work_bytes.argtypes = [S, I, I]
+        L.acnn_work_bytes.restype = C.c_size_t
+        L.acnn_forward.argtypes = [S, I, I, S, S, S, C.c_size_t, S]
+        L.acnn_train_bytes.argtypes = [P(acnn_desc), I, I]
+        L.acnn_train_bytes.restype = C.c_size_t
+        L.acnn_forward_train.argtypes = [P(acnn_desc), I, I, S, S, S, S]
+        L.acnn_backward.argtypes = [P(acnn_desc), I, I, S, S, S, S, S, S]
+        L.loss_acn_work_bytes.argtypes = [I, I]
+        L.loss_acn_work_bytes.restype = C.c_size_t
+        L.loss_acn.argtypes = [P(ac_params), I, S, S, S, S, S, S]
+        L.acnn_adam_step.argtypes = [I, S, S, S, S, C.c_longlong, D, D, D, D, I, S]
+        L.acnn_train_alg1.argtypes = [P(ac_params), P(acnn_desc), I, S, P(I), I, I, I, I, D, D, D, D, S, S, P(I),
+                                      S, S]
+        L.ac_parareal_set_coarse_acnn.argtypes = [S, S]
         _lib = L
         return L
 
@@ -416,6 +444,169 @@ def mse_loss_grad(pred, target, scale, grad=None, grad_accumulate=False, loss=No
     return loss
 
 
+def acnn_param_count(channels: int, blocks: int):
+    """(number of weights, number of biases) of the ResBlock ACNN."""
+    nb = C.c_longlong()
+    nw = load().acnn_param_count(int(channels), int(blocks), C.byref(nb))
+    if nw < 0:
+        raise AcprError(-2, f"ACNN C={channels} blocks={blocks} not built")
+    return int(nw), int(nb.value)
+
+
+class Acnn:
+    """The paper's ResBlock ACNN / mACNN coarse network (Sec. 3.2).
+
+    Parameters live on the device (w, b, in the layouts of include/acpr.h) and
+    train in place; `handle()` builds the inference handle (parameters baked
+    into the kernel argument) and is rebuilt after every update."""
+
+    def __init__(self, channels, blocks, w, b, mass_fix=0, limiter=0, lo=-1.0, hi=1.0, precision=AC_F32,
+                 device="cuda"):
+        import torch
+        self.channels, self.blocks = int(channels), int(blocks)
+        self.mass_fix, self.limiter, self.lo, self.hi = int(mass_fix), int(limiter), float(lo), float(hi)
+        self.precision = int(precision)
+        dt = _dtype(self.precision)
+        nw, nb = acnn_param_count(self.channels, self.blocks)
+        self.w = torch.as_tensor(w, dtype=dt).reshape(-1).to(device).contiguous()
+        self.b = torch.as_tensor(b, dtype=dt).reshape(-1).to(device).contiguous()
+        if self.w.numel() != nw or self.b.numel() != nb:
+            raise ValueError(f"ACNN C={channels} blocks={blocks} takes {nw} weights and {nb} biases")
+        self.nw, self.nb = nw, nb
+        self._h = None
+        self._work = {}
+        self.m = self.v = None
+        self.t = 0
+
+    def desc(self) -> acnn_desc:
+        return acnn_desc(self.channels, self.blocks, self.mass_fix, self.limiter, self.lo, self.hi, self.precision,
+                         self.w.data_ptr(), self.b.data_ptr())
+
+    def handle(self):
+        if self._h is None:
+            h = C.c_void_p()
+            d = self.desc()
+            _check(load().acnn_create(C.byref(d), C.byref(h)))
+            self._h = h
+        return self._h
+
+    def invalidate(self):
+        """Drop the inference handle (call after changing w or b in place)."""
+        if self._h is not None:
+            load().acnn_destroy(self._h)
+            self._h = None
+
+    def __call__(self, u, out=None, stream=None):
+        """G(u) for u [batch][n][n] (or [n][n]) through the inference handle."""
+        import torch
+        n = u.shape[-1]
+        batch = u.numel() // (n * n)
+        h = self.handle()
+        need = load().acnn_work_bytes(h, n, batch)
+        key = (n, batch)
+        if key not in self._work or self._work[key].numel() < need:
+            self._work[key] = torch.empty(max(need, 1), dtype=torch.uint8, device=u.device)
+        out = out if out is not None else torch.empty_like(u)
+        dt = _dtype(self.precision)
+        _check(load().acnn_forward(h, n, batch, _dev(u, dt, "u"), _dev(out, dt, "out"),
+                                   _dev(self._work[key], None, "work"), need, _stream(stream)))
+        return out
+
+    def new_workspace(self, n, batch):
+        import torch
+        d = self.desc()
+        nb = load().acnn_train_bytes(C.byref(d), int(n), int(batch))
+        return torch.empty(max(nb, 1), dtype=torch.uint8, device=self.w.device)
+
+    def forward_train(self, u, ws, out=None, stream=None):
+        import torch
+        n = u.shape[-1]
+        batch = u.numel() // (n * n)
+        out = out if out is not None else torch.empty_like(u)
+        d = self.desc()
+        dt = _dtype(self.precision)
+        _check(load().acnn_forward_train(C.byref(d), n, batch, _dev(u, dt, "u"), _dev(out, dt, "out"),
+                                         _dev(ws, None, "ws"), _stream(stream)))
+        return out
+
+    def backward(self, u, grad_out, ws, gw=None, gb=None, stream=None):
+        """(dL/dw, dL/db) of the last forward_train for grad_out = dL/d(output)."""
+        import torch
+        n = u.shape[-1]
+        batch = u.numel() // (n * n)
+        gw = gw if gw is not None else torch.empty_like(self.w)
+        gb = gb if gb is not None else torch.empty_like(self.b)
+        d = self.desc()
+        dt = _dtype(self.precision)
+        _check(load().acnn_backward(C.byref(d), n, batch, _dev(u, dt, "u"), _dev(grad_out, dt, "grad_out"),
+                                    _dev(gw, dt, "gw"), _dev(gb, dt, "gb"), _dev(ws, None, "ws"), _stream(stream)))
+        return gw, gb
+
+    def _moments(self):
+        import torch
+        if self.m is None:
+            self.m = torch.zeros(self.nw + self.nb, dtype=self.w.dtype, device=self.w.device)
+            self.v = torch.zeros_like(self.m)
+
+    def adam(self, gw, gb, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        """One Adam step on w and b (moments held by the object)."""
+        self._moments()
+        self.t += 1
+        dt = _dtype(self.precision)
+        for par, g, off in ((self.w, gw, 0), (self.b, gb, self.nw)):
+            _check(load().acnn_adam_step(self.precision, _dev(par, dt, "w"), _dev(g, dt, "grad"),
+                                         C.c_void_p(self.m.data_ptr() + off * self.m.element_size()),
+                                         C.c_void_p(self.v.data_ptr() + off * self.v.element_size()),
+                                         par.numel(), lr, beta1, beta2, eps, self.t, _stream(stream)))
+        self.invalidate()
+
+    def train_alg1(self, params: FineParams, U0s, perm, q, steps, b_inner, lr=1e-3, beta1=0.9, beta2=0.999,
+                   eps=1e-8, stream=None):
+        """Algorithm 1 with the scheme-residual loss at time step params.dt.
+        perm: int array [epochs][R].  Returns the losses (float64 device
+        tensor, one per update)."""
+        import numpy as np
+        import torch
+        self._moments()
+        perm = np.ascontiguousarray(perm, dtype=np.int32)
+        epochs, R = perm.shape
+        losses = torch.zeros(max(epochs * (R // q) * steps * b_inner, 1), dtype=torch.float64, device=self.w.device)
+        p = params.c()
+        d = self.desc()
+        t = C.c_int(self.t)
+        _check(load().acnn_train_alg1(C.byref(p), C.byref(d), R, _dev(U0s, _dtype(self.precision), "U0s"),
+                                      perm.ctypes.data_as(C.POINTER(C.c_int)), epochs, int(q), int(steps),
+                                      int(b_inner), lr, beta1, beta2, eps, C.c_void_p(self.m.data_ptr()),
+                                      C.c_void_p(self.v.data_ptr()), C.byref(t),
+                                      _dev(losses, torch.float64, "losses"), _stream(stream)))
+        self.t = t.value
+        self.invalidate()
+        return losses[: epochs * (R // q) * steps * b_inner]
+
+    def __del__(self):
+        try:
+            self.invalidate()
+        except Exception:
+            pass
+
+
+def loss_acn(params: FineParams, U0, U1, grad=True, stream=None):
+    """Eq. loss_ACN at time step params.dt: (loss as a float64 device tensor
+    of one element, dL/dU1 or None), computed by the library's kernels."""
+    import torch
+    n = U0.shape[-1]
+    batch = U0.numel() // (n * n)
+    dt = params.dtype
+    work = torch.empty(load().loss_acn_work_bytes(n, batch), dtype=torch.uint8, device=U0.device)
+    loss = torch.zeros(1, dtype=torch.float64, device=U0.device)
+    g = torch.empty_like(U1) if grad else None
+    p = params.c()
+    _check(load().loss_acn(C.byref(p), batch, _dev(U0, dt, "U0"), _dev(U1, dt, "U1"),
+                           _dev(loss, torch.float64, "loss"), _dev(g, dt, "grad") if grad else None,
+                           _dev(work, None, "work"), _stream(stream)))
+    return loss, g
+
+
 def coarse_step_function():
     """torch.autograd.Function over the conv stack: forward = cnn_forward_train,
     backward = cnn_backward (gradients for u, w and b)."""
@@ -522,27 +713,39 @@ class Parareal:
     """Handle on ac_parareal: Algorithm 2 for `problems` independent problems.
     `slices` / `steps` may be per-problem sequences (ac_parareal_create_uneven)."""
 
-    def __init__(self, params: FineParams, net: CoarseNet, u0, slices, steps):
-        import torch
+    def __init__(self, params: FineParams, net, u0, slices, steps):
+        """net: a CoarseNet (the conv stack) or an Acnn (the paper's ResBlock
+        network, Sec. 3.2)."""
         self.params, self.net = params, net
         self.problems = u0.shape[0] if u0.dim() == 3 else 1
         self._u0 = u0.contiguous()
         p = params.c()
-        d = net.desc()
+        acnn = net if isinstance(net, Acnn) else None
+        d = None if acnn is not None else net.desc()
+        dref = C.byref(d) if d is not None else None
         h = C.c_void_p()
         if isinstance(slices, int) and isinstance(steps, int):
             self.s, self.c = int(slices), int(steps)
-            _check(load().ac_parareal_create(C.byref(p), C.byref(d), self.problems, self.s, self.c,
+            _check(load().ac_parareal_create(C.byref(p), dref, self.problems, self.s, self.c,
                                              _dev(self._u0, params.dtype, "u0"), C.byref(h)))
         else:
             sl = [int(x) for x in (slices if not isinstance(slices, int) else [slices] * self.problems)]
             st = [int(x) for x in (steps if not isinstance(steps, int) else [steps] * self.problems)]
             self.s, self.c = max(sl), st
-            _check(load().ac_parareal_create_uneven(C.byref(p), C.byref(d), self.problems, (C.c_int * len(sl))(*sl),
+            _check(load().ac_parareal_create_uneven(C.byref(p), dref, self.problems, (C.c_int * len(sl))(*sl),
                                                     (C.c_int * len(st))(*st), _dev(self._u0, params.dtype, "u0"),
                                                     C.byref(h)))
         self._h = h
         self.k = 0
+        self._acnn = None
+        if acnn is not None:
+            self.set_coarse_acnn(acnn)
+
+    def set_coarse_acnn(self, acnn):
+        """Use the ResBlock ACNN as G (None: back to the conv stack the handle
+        was created with)."""
+        self._acnn = acnn
+        _check(load().ac_parareal_set_coarse_acnn(self._h, acnn.handle() if acnn is not None else None))
 
     def enable_graphs(self, on=True):
         _check(load().ac_parareal_enable_graphs(self._h, int(on)))

@@ -21,6 +21,7 @@
 #include <utility>
 #include <vector>
 
+#include "acnn.cuh"
 #include "cnn.cuh"
 #include "common.cuh"
 
@@ -297,6 +298,10 @@ struct ac_parareal {
     cudaStream_t stream_launched = nullptr;
     bool timing = false;
     bool graphs = false;
+    bool has_cnn = false;            // created with a conv-stack G
+    const acnn_net* acnn = nullptr;  // the ResBlock ACNN as G instead of the conv stack
+    void* acnn_work = nullptr;
+    size_t acnn_work_bytes = 0;
     int g_sub = 1;             // coarse composition: G applied g_sub times per slice
     void* gsub[2] = {nullptr, nullptr};  // [problems][nn] each: intermediate G applications
     int fine_scheme = 0;       // 0: stabilised semi-implicit step, 1: Crank-Nicolson + Picard
@@ -314,6 +319,7 @@ namespace acpr {
 static void free_state(ac_parareal* st) {
     if (!st) return;
     for (void* ptr : {st->Ua, st->Ub, st->Gold, st->Fres, st->gtmp, st->work, st->packed, st->gsub[0], st->gsub[1],
+                      st->acnn_work,
                       static_cast<void*>(st->d_map), static_cast<void*>(st->d_fw), static_cast<void*>(st->d_part),
                       static_cast<void*>(st->d_res)})
         if (ptr) cudaFree(ptr);
@@ -332,6 +338,15 @@ static void free_state(ac_parareal* st) {
 // recursive composition of the remark after Algorithm 2: a coarse step that
 // covers the slice in g_sub sub-steps).  The intermediate applications go
 // through compact [mn][nn] buffers; the last one writes the mapped output.
+static int coarse_once(ac_parareal* st, int mn, const void* in, long long in_bs, const int* in_map, void* out,
+                       long long out_bs, const int* out_map, cudaStream_t stream) {
+    if (st->acnn)
+        return acnn_forward_mapped(st->acnn, st->p.n, mn, in, in_bs, in_map, out, out_bs, out_map, st->acnn_work,
+                                   st->acnn_work_bytes, stream);
+    ACPR_CHECK_ARG(st->has_cnn, "no coarse propagator: the handle was created without one and no ACNN is set");
+    return coarse_step_mapped(&st->g, st->p.n, mn, in, in_bs, in_map, out, out_bs, out_map, stream);
+}
+
 static int coarse_apply(ac_parareal* st, int mn, const void* in, long long in_bs, const int* in_map, void* out,
                         long long out_bs, const int* out_map, cudaStream_t stream) {
     const void* cur = in;
@@ -339,13 +354,13 @@ static int coarse_apply(ac_parareal* st, int mn, const void* in, long long in_bs
     const int* cur_map = in_map;
     for (int i = 0; i + 1 < st->g_sub; ++i) {
         void* dst = st->gsub[i & 1];
-        int rc = coarse_step_mapped(&st->g, st->p.n, mn, cur, cur_bs, cur_map, dst, st->nn, nullptr, stream);
+        int rc = coarse_once(st, mn, cur, cur_bs, cur_map, dst, st->nn, nullptr, stream);
         if (rc) return rc;
         cur = dst;
         cur_bs = st->nn;
         cur_map = nullptr;
     }
-    return coarse_step_mapped(&st->g, st->p.n, mn, cur, cur_bs, cur_map, out, out_bs, out_map, stream);
+    return coarse_once(st, mn, cur, cur_bs, cur_map, out, out_bs, out_map, stream);
 }
 
 static unsigned grid_for(long long total, int threads) {
@@ -600,23 +615,26 @@ static int create(const ac_params* params, const cnn_desc* coarse, int problems,
                   const int* steps, const void* u0, ac_parareal** out) {
     ACPR_CHECK_ARG(out != nullptr, "out is NULL");
     *out = nullptr;
-    ACPR_CHECK_ARG(params && coarse && u0 && slices && steps, "null argument");
+    ACPR_CHECK_ARG(params && u0 && slices && steps, "null argument");
     ACPR_CHECK_ARG(problems >= 1, "need at least one problem");
     int smax = 0;
     for (int p = 0; p < problems; ++p) {
         ACPR_CHECK_ARG(slices[p] >= 1 && steps[p] >= 0, "problem %d: bad slice count or steps", p);
         smax = std::max(smax, slices[p]);
     }
-    ACPR_CHECK_ARG(coarse->precision == params->precision, "coarse and fine precision differ");
-    int rc = check_cnn(coarse);
-    if (rc) return rc;
+    int rc = AC_OK;
+    if (coarse) {
+        ACPR_CHECK_ARG(coarse->precision == params->precision, "coarse and fine precision differ");
+        if ((rc = check_cnn(coarse))) return rc;
+    }
     if (!fine_supported_internal(params->n, params->precision)) {
         set_error("ac_parareal_create: n=%d not supported", params->n);
         return AC_ERR_UNSUPPORTED;
     }
     ac_parareal* st = new ac_parareal();
     st->p = *params;
-    st->g = *coarse;
+    if (coarse) st->g = *coarse;
+    st->has_cnn = coarse != nullptr;
     st->problems = problems;
     st->s = smax;
     st->sp.assign(slices, slices + problems);
@@ -638,9 +656,9 @@ static int create(const ac_params* params, const cnn_desc* coarse, int problems,
     auto alloc = [&](void** p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
     bool ok = alloc(&st->Ua, traj) && alloc(&st->Ub, traj) && alloc(&st->Gold, slc) && alloc(&st->Fres, slc) &&
               alloc(&st->gtmp, fb * problems);
-    const size_t wb = work_bytes_for(coarse, params->n, problems);
-    ok = ok && alloc(&st->work, wb);
-    const size_t pb = cnn_packed_bytes(coarse);
+    const size_t wb = coarse ? work_bytes_for(coarse, params->n, problems) : 0;
+    if (wb) ok = ok && alloc(&st->work, wb);
+    const size_t pb = coarse ? cnn_packed_bytes(coarse) : 0;
     if (ok && pb) ok = alloc(&st->packed, pb);
     ok = ok && alloc(reinterpret_cast<void**>(&st->d_map), sizeof(int) * problems) &&
          alloc(reinterpret_cast<void**>(&st->d_fw), sizeof(int4) * size_t(problems) * smax) &&
@@ -847,6 +865,30 @@ extern "C" int ac_parareal_enable_graphs(ac_parareal* state, int on) {
     using namespace acpr;
     ACPR_CHECK_ARG(state, "null state");
     state->graphs = on != 0;
+    return AC_OK;
+}
+
+extern "C" int ac_parareal_set_coarse_acnn(ac_parareal* state, const acnn_net* net) {
+    using namespace acpr;
+    ACPR_CHECK_ARG(state, "null state");
+    if (net) {
+        ACPR_CHECK_ARG(acnn_precision(net) == state->p.precision, "ACNN precision differs from the handle's");
+        const size_t need = acnn_work_bytes(net, state->p.n, state->problems);
+        if (!need) {
+            set_error("ac_parareal_set_coarse_acnn: n=%d not supported by the ACNN", state->p.n);
+            return AC_ERR_UNSUPPORTED;
+        }
+        if (need > state->acnn_work_bytes) {
+            if (state->acnn_work) cudaFree(state->acnn_work);
+            state->acnn_work = nullptr;
+            state->acnn_work_bytes = 0;
+            ACPR_CUDA(cudaMalloc(&state->acnn_work, need));
+            state->acnn_work_bytes = need;
+        }
+    }
+    state->acnn = net;
+    for (auto& kv : state->graph_cache) cudaGraphExecDestroy(kv.second.first);
+    state->graph_cache.clear();
     return AC_OK;
 }
 

@@ -204,3 +204,24 @@ def test_algorithm1_lowers_the_scheme_loss():
     after = O.loss_acn(p, test, O.acnn_forward(spec, test), grad=False)[0]
     assert after < 0.5 * before
     assert losses[-6:].mean() < losses[:6].mean()
+
+
+def test_parareal_with_acnn_first_sweep_and_exactness():
+    """Algorithm 2 with the ACNN as G: the k = 0 sweep is the network's rollout,
+    and at k = s the trajectory is the sequential fine solve (Sec. 3.3)."""
+    C, R, n, s, c = 4, 2, 16, 5, 4
+    w, b = I.acnn_weights(C, R, seed=15)
+    spec = O.AcnnSpec(C, R, w, b, mass_fix=1)
+    p = O.params(n, eps=0.05, S=2.0, dt=2e-3, variant=1)
+    u0 = I.random_field(n, seed=16, zero_mean=True)
+    r0 = O.parareal(p, spec, s, c, kmax=0, tol=0.0, u0=u0)
+    u = u0
+    for j in range(s):
+        u = O.acnn_forward(spec, u)
+        assert np.array_equal(r0["U"][j + 1], u)
+    r = O.parareal(p, spec, s, c, kmax=s, tol=0.0, u0=u0)
+    seq = [u0]
+    for j in range(s):
+        seq.append(O.fine_propagate(p, c, seq[-1]))
+    assert np.array_equal(r["U"], np.stack(seq))
+    assert r["g_calls"] == (2 * s - s) * (s + 1) // 2
