@@ -291,6 +291,103 @@ def run_train(args):
         "timing": "wall clock per iteration, one host read of the loss per iteration included"}), flush=True)
 
 
+def run_acnn(args):
+    """The paper's light coarse network (Sec. 3.2: ResBlock mACNN, C = 4, two
+    blocks, tanh, mass shift, limiter [-1, 1]) on the benchmark's problems
+    (mass-conserving 256^2 fields, eps = 0.01, fine dt = 5e-5, slices of 200
+    fine steps):
+      1. Algorithm 1 with the scheme-residual loss (Eq. loss_ACN) at the slice
+         step 200 dt: 32 seeded initial conditions disjoint from the
+         benchmark's, subsets of q = 16, 8 coarse steps, 4 inner updates,
+         `--acnn-epochs` epochs; time per update;
+      2. one application of G to the 16 benchmark fields (the fused kernel),
+         CUDA-event time over 200 launches (4 MB of input, L2-resident: the
+         kernel is bound by FP32 issue), with its FP32 roofline;
+      3. the benchmark's Parareal solve (16 problems, 32 slices x 200 steps,
+         tol 1e-6, CUDA graphs) with this G, against the sequential fine solve.
+    Prints one JSON line (not the benchmark line)."""
+    import torch
+    import paper_2510_07672_gb300 as G
+    W = I.MASS_F32_256
+    n, C, R, q, steps, b_inner = W.n, 4, 32, 16, 8, 4
+    fp = G.FineParams(n, W.eps, W.S, W.dt, variant=W.variant, precision=G.AC_F32)
+    coarse = G.FineParams(n, W.eps, 0.0, W.dt * W.steps, variant=W.variant, precision=G.AC_F32)
+    w, b = I.acnn_weights(C, 2, seed=0)
+    net = G.Acnn(C, 2, w, b, mass_fix=1, limiter=1, lo=-1.0, hi=1.0, precision=G.AC_F32)
+    U0s = torch.tensor(np.stack([I.random_field(n, seed=5000 + i, zero_mean=True) for i in range(R)]),
+                       dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(0)
+    epochs = args.acnn_epochs
+    perm = np.stack([rng.permutation(R) for _ in range(epochs)])
+    net.train_alg1(coarse, U0s, perm[:1], q, 1, 1, lr=1e-3)  # warm-up: one update
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = net.train_alg1(coarse, U0s, perm, q, steps, b_inner, lr=1e-3).cpu().numpy()
+    train_s = time.perf_counter() - t0
+    updates = len(losses)
+
+    u0 = torch.tensor(W.ics().astype(np.float32), device="cuda")
+    out = torch.empty_like(u0)
+    for _ in range(10):
+        net(u0, out=out)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 200
+    e0.record(stream)
+    for _ in range(reps):
+        net(u0, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    g_us = e0.elapsed_time(e1) * 1e3 / reps
+    px = W.problems * n * n
+    flops = 2 * px * (9 * C + 4 * 9 * C * C + 9 * C)
+    peaks, src = measured_peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = peak_fp32_tflops(sm_mhz)
+    achieved = flops / (g_us * 1e-6) / 1e12
+
+    pr = G.Parareal(fp, net, u0, W.slices, W.steps)
+    pr.enable_timing(True)
+    pr.enable_graphs(True)
+    pr.solve(tol=W.tol, kmax=W.kmax)
+    pr.reset(u0)
+    pr.reset_stats()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    its, l2 = pr.solve(tol=W.tol, kmax=W.kmax)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    para_ms = s0.elapsed_time(s1)
+    st = pr.stats()
+    a, bb = u0.clone(), torch.empty_like(u0)
+    for _ in range(W.slices):
+        G.ac_fine_propagate_slices(fp, W.steps, a, bb)
+        a, bb = bb, a
+    torch.cuda.synchronize()
+    s0.record(stream)
+    for _ in range(W.slices):
+        G.ac_fine_propagate_slices(fp, W.steps, a, bb)
+        a, bb = bb, a
+    s1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = s0.elapsed_time(s1)
+    print(json.dumps({
+        "metric": "ResBlock mACNN coarse propagator (C = 4, 2 blocks): Algorithm 1 training, G time, Parareal",
+        "workload": "acnn-c4b2-mass-256sq", "config": {"n": n, "eps": W.eps, "fine_dt": W.dt,
+                                                      "coarse_dt": W.dt * W.steps, "channels": C, "blocks": 2},
+        "train": {"R": R, "q": q, "steps": steps, "b_inner": b_inner, "epochs": epochs, "updates": updates,
+                  "ms_per_update": train_s * 1e3 / updates, "loss_first": float(losses[0]),
+                  "loss_last_mean8": float(losses[-8:].mean()), "timing": "host wall clock of one synchronous call"},
+        "g": {"fields": W.problems, "us_per_application": g_us, "flops_per_application": flops,
+              "roofline": {"bound": "alu", "kernel": "acnn_fused_kernel", "achieved": achieved, "peak": peak,
+                           "unit": "TFLOP/s", "frac": achieved / peak,
+                           "peak_source": f"FP32 lanes x 2 x sm_max_mhz {sm_mhz:.0f} from {src} peaks"},
+              },
+        "parareal": {"iterations": its, "final_rel_l2": l2, "ms": para_ms, "sequential_ms": seq_ms,
+                     "coarse_ms": st["coarse_ms"], "fine_ms": st["fine_ms"], "coarse_calls": st["coarse_calls"]},
+    }), flush=True)
+
+
 def run_adjoint(args):
     """The adjoint workload: dE_h(u^2000)/du^0 of one 256^2 classic field
     (eps = 0.01, dt = 5e-5, S = 2) by the checkpointed adjoint (a checkpoint
@@ -392,10 +489,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--weights", default="trained", help="'trained' (the committed G), 'untrained', or a .npz path")
-    ap.add_argument("--workload", default="mass256", choices=["mass256", "uneven", "train", "adjoint"],
+    ap.add_argument("--workload", default="mass256", choices=["mass256", "uneven", "train", "adjoint", "acnn"],
                     help="mass256: the benchmark line; uneven: 64 classic problems of uneven size (batching); "
                          "train: coarse-net training iterations (C = 64, 8 layers); "
-                         "adjoint: checkpointed energy gradient through 2000 steps")
+                         "adjoint: checkpointed energy gradient through 2000 steps; "
+                         "acnn: the paper's ResBlock mACNN (Algorithm 1 training, G time, Parareal)")
+    ap.add_argument("--acnn-epochs", type=int, default=20)
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--coarse-substeps", type=int, default=1,
                     help="mass256 only: M > 1 covers the same time span with slices of M x 200 fine steps "
@@ -416,6 +515,9 @@ def main():
         return
     if args.workload == "adjoint":
         run_adjoint(args)
+        return
+    if args.workload == "acnn":
+        run_acnn(args)
         return
 
     # host-side oracle sample first (before any GPU work in this process)

@@ -3,6 +3,7 @@
     python -m paper_2510_07672_gb300.profile_cases fine   # ac_fine_propagate_slices, 512 x 256^2, 20 steps
     python -m paper_2510_07672_gb300.profile_cases conv   # cnn_coarse_step, 16 x 256^2, 1-32x6-1 gelu bf16
     python -m paper_2510_07672_gb300.profile_cases big    # ac_fine_propagate_slices, 16 x 1024^2, 2 steps
+    python -m paper_2510_07672_gb300.profile_cases acnn   # acnn_forward (fused), 512 x 256^2, C = 4, 2 blocks
 
 Each case runs its call twice (a warm-up launch, then the one to capture) and
 exits 0, so `ncu -s <warm-up launches> -c 1` captures a warm launch.  Inputs
@@ -48,8 +49,16 @@ def main(case: str) -> None:
         out = torch.empty_like(u)
         for _ in range(2):
             G.ac_fine_propagate_slices(fp, 2, u, out)
+    elif case == "acnn":
+        w, b = I.acnn_weights(4, 2, seed=0)
+        net = G.Acnn(4, 2, w, b, mass_fix=1, limiter=1, precision=G.AC_F32)
+        u = torch.tensor(np.stack([I.random_field(W.n, seed=s, zero_mean=True) for s in range(512)]),
+                         dtype=torch.float32, device="cuda")
+        out = torch.empty_like(u)
+        for _ in range(2):
+            net(u, out=out)
     else:
-        raise SystemExit(f"unknown case {case!r} (fine | conv | big)")
+        raise SystemExit(f"unknown case {case!r} (fine | conv | big | acnn)")
     torch.cuda.synchronize()
     print(f"{case}: ok")
 
