@@ -73,32 +73,51 @@ struct FusedShape {
     static constexpr size_t smem = sizeof(T) * (size_t(S0) * S0 + 2 * size_t(S1) * S1 * 4);
 };
 
-// Hidden C -> C conv of block conv index L over frame region [lo, hi)^2 of
-// `src`, output written through `emit(i, j, acc)`.
-template <typename T, int R, int L, typename Emit>
-__device__ __forceinline__ void hidden_conv(const FusedParams<T, R>& P, const T* __restrict__ src, int lo, int hi,
-                                            Emit emit) {
+// Every convolution of the fused kernel covers a square frame region whose
+// side M is a compile-time constant (and even), so the index arithmetic is
+// multiply-shift.  A thread computes two vertically adjacent pixels at a time:
+// it loads a 4 x 3 window of 16-byte pixel vectors (consecutive lanes read
+// consecutive pixels, no bank conflicts) and reuses the constant-bank weights
+// for both.
+
+// Hidden C -> C conv L over frame rows/cols [LO, LO + M) of `src`; emit(i, j, acc)
+// receives each tanh output.
+template <typename T, int R, int L, int LO, int M, typename Emit>
+__device__ __forceinline__ void hidden_conv(const FusedParams<T, R>& P, const T* __restrict__ src, Emit emit) {
     constexpr int S1 = FusedShape<T, R>::S1;
-    const int m = hi - lo;
-    for (int idx = threadIdx.x; idx < m * m; idx += kThreads) {
-        const int i = lo + idx / m, j = lo + idx % m;
-        T acc[4];
+    static_assert(M % 2 == 0, "regions have even sides");
+    for (int idx = threadIdx.x; idx < M * M / 2; idx += kThreads) {
+        const int i = LO + 2 * (idx / M), j = LO + idx % M;
+        T acc0[4], acc1[4];
 #pragma unroll
-        for (int co = 0; co < 4; ++co) acc[co] = P.bb[L][co];
+        for (int co = 0; co < 4; ++co) acc0[co] = acc1[co] = P.bb[L][co];
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
+        for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
                 T v[4];
-                lds4(src + ((i + a - 1) * S1 + (j + e - 1)) * 4, v);
+                lds4(src + ((i + rr - 1) * S1 + (j + e - 1)) * 4, v);
+                if (rr < 3) {
 #pragma unroll
-                for (int ci = 0; ci < 4; ++ci)
+                    for (int ci = 0; ci < 4; ++ci)
 #pragma unroll
-                    for (int co = 0; co < 4; ++co) acc[co] = fma(P.wb[L][co][ci][a * 3 + e], v[ci], acc[co]);
+                        for (int co = 0; co < 4; ++co) acc0[co] = fma(P.wb[L][co][ci][rr * 3 + e], v[ci], acc0[co]);
+                }
+                if (rr > 0) {
+#pragma unroll
+                    for (int ci = 0; ci < 4; ++ci)
+#pragma unroll
+                        for (int co = 0; co < 4; ++co)
+                            acc1[co] = fma(P.wb[L][co][ci][(rr - 1) * 3 + e], v[ci], acc1[co]);
+                }
             }
 #pragma unroll
-        for (int co = 0; co < 4; ++co) acc[co] = acnn_tanh(acc[co]);
-        emit(i, j, acc);
+        for (int co = 0; co < 4; ++co) {
+            acc0[co] = acnn_tanh(acc0[co]);
+            acc1[co] = acnn_tanh(acc1[co]);
+        }
+        emit(i, j, acc0);
+        emit(i + 1, j, acc1);
     }
 }
 
@@ -107,11 +126,11 @@ __device__ __forceinline__ void run_blocks(const FusedParams<T, R>& P, T* X, T* 
     if constexpr (r < R) {
         constexpr int S1 = FusedShape<T, R>::S1;
         // conv1: X valid on [2r, S1-2r) -> Hb on [2r+1, S1-2r-1)
-        hidden_conv<T, R, 2 * r>(P, X, 2 * r + 1, S1 - 2 * r - 1,
-                                 [&](int i, int j, const T (&h)[4]) { sts4(Hb + (i * S1 + j) * 4, h); });
+        hidden_conv<T, R, 2 * r, 2 * r + 1, S1 - 4 * r - 2>(
+            P, X, [&](int i, int j, const T (&h)[4]) { sts4(Hb + (i * S1 + j) * 4, h); });
         __syncthreads();
         // conv2 + skip: X += tanh(conv2(Hb)) on [2r+2, S1-2r-2); conv2 reads Hb only
-        hidden_conv<T, R, 2 * r + 1>(P, Hb, 2 * r + 2, S1 - 2 * r - 2, [&](int i, int j, const T (&t)[4]) {
+        hidden_conv<T, R, 2 * r + 1, 2 * r + 2, S1 - 4 * r - 4>(P, Hb, [&](int i, int j, const T (&t)[4]) {
             T x[4];
             lds4(X + (i * S1 + j) * 4, x);
 #pragma unroll
@@ -146,47 +165,66 @@ __global__ void __launch_bounds__(kThreads) acnn_fused_kernel(const __grid_const
     }
     __syncthreads();
     // input conv 1 -> 4 with tanh: frame (i, j) sits at su (i + 1, j + 1)
-    for (int idx = threadIdx.x; idx < S1 * S1; idx += kThreads) {
-        const int i = idx / S1, j = idx % S1;
-        T acc[4];
+    for (int idx = threadIdx.x; idx < S1 * S1 / 2; idx += kThreads) {
+        const int i = 2 * (idx / S1), j = idx % S1;
+        T acc0[4], acc1[4];
 #pragma unroll
-        for (int co = 0; co < 4; ++co) acc[co] = P.bin[co];
+        for (int co = 0; co < 4; ++co) acc0[co] = acc1[co] = P.bin[co];
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
+        for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
-                const T v = su[(i + a) * S0 + (j + e)];
+                const T v = su[(i + rr) * S0 + (j + e)];
+                if (rr < 3) {
 #pragma unroll
-                for (int co = 0; co < 4; ++co) acc[co] = fma(P.win[co][a * 3 + e], v, acc[co]);
+                    for (int co = 0; co < 4; ++co) acc0[co] = fma(P.win[co][rr * 3 + e], v, acc0[co]);
+                }
+                if (rr > 0) {
+#pragma unroll
+                    for (int co = 0; co < 4; ++co) acc1[co] = fma(P.win[co][(rr - 1) * 3 + e], v, acc1[co]);
+                }
             }
 #pragma unroll
-        for (int co = 0; co < 4; ++co) acc[co] = acnn_tanh(acc[co]);
-        sts4(X + idx * 4, acc);
+        for (int co = 0; co < 4; ++co) {
+            acc0[co] = acnn_tanh(acc0[co]);
+            acc1[co] = acnn_tanh(acc1[co]);
+        }
+        sts4(X + (i * S1 + j) * 4, acc0);
+        sts4(X + ((i + 1) * S1 + j) * 4, acc1);
     }
     __syncthreads();
     run_blocks<T, R, 0>(P, X, Hb);
     // output conv 4 -> 1 on [2R+1, S1-2R-1): exactly the 32 x 32 tile
     constexpr int lo = 2 * R + 1;
     T msum = T(0);
-    for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
-        const int i = lo + (idx >> 5), j = lo + (idx & 31);
-        T acc = P.bout;
+    for (int idx = threadIdx.x; idx < kTile * kTile / 2; idx += kThreads) {
+        const int ii = 2 * (idx >> 5), jj = idx & 31;
+        const int i = lo + ii, j = lo + jj;
+        T acc0 = P.bout, acc1 = P.bout;
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
+        for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
                 T v[4];
-                lds4(X + ((i + a - 1) * S1 + (j + e - 1)) * 4, v);
+                lds4(X + ((i + rr - 1) * S1 + (j + e - 1)) * 4, v);
+                if (rr < 3) {
 #pragma unroll
-                for (int ci = 0; ci < 4; ++ci) acc = fma(P.wout[ci][a * 3 + e], v[ci], acc);
+                    for (int ci = 0; ci < 4; ++ci) acc0 = fma(P.wout[ci][rr * 3 + e], v[ci], acc0);
+                }
+                if (rr > 0) {
+#pragma unroll
+                    for (int ci = 0; ci < 4; ++ci) acc1 = fma(P.wout[ci][(rr - 1) * 3 + e], v[ci], acc1);
+                }
             }
-        const long long g = (long long)(ty * kTile + (idx >> 5)) * n + tx * kTile + (idx & 31);
+        const long long g0 = (long long)(ty * kTile + ii) * n + tx * kTile + jj;
         if (P.mass_fix) {
-            msum += acc - su[(i + 1) * S0 + (j + 1)];
+            msum += (acc0 - su[(i + 1) * S0 + (j + 1)]) + (acc1 - su[(i + 2) * S0 + (j + 1)]);
         } else if (P.limiter) {
-            acc = acc < P.lo ? P.lo : (acc > P.hi ? P.hi : acc);
+            acc0 = acc0 < P.lo ? P.lo : (acc0 > P.hi ? P.hi : acc0);
+            acc1 = acc1 < P.lo ? P.lo : (acc1 > P.hi ? P.hi : acc1);
         }
-        ob[g] = acc;
+        ob[g0] = acc0;
+        ob[g0 + n] = acc1;
     }
     if (P.mass_fix) {
         __shared__ double red[kThreads / 32];
