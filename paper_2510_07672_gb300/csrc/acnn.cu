@@ -75,10 +75,10 @@ struct FusedShape {
 
 // Every convolution of the fused kernel covers a square frame region whose
 // side M is a compile-time constant (and even), so the index arithmetic is
-// multiply-shift.  A thread computes two vertically adjacent pixels at a time:
-// it loads a 4 x 3 window of 16-byte pixel vectors (consecutive lanes read
-// consecutive pixels, no bank conflicts) and reuses the constant-bank weights
-// for both.
+// multiply-shift.  A thread computes two vertically adjacent pixels: it loads
+// their 4 x 3 window of 16-byte pixel vectors once (consecutive lanes read
+// consecutive pixels, no bank conflicts), then walks the weights in the outer
+// loop, each weight feeding both accumulators.
 
 // Hidden C -> C conv L over frame rows/cols [LO, LO + M) of `src`; emit(i, j, acc)
 // receives each tanh output.
@@ -88,36 +88,32 @@ __device__ __forceinline__ void hidden_conv(const FusedParams<T, R>& P, const T*
     static_assert(M % 2 == 0, "regions have even sides");
     for (int idx = threadIdx.x; idx < M * M / 2; idx += kThreads) {
         const int i = LO + 2 * (idx / M), j = LO + idx % M;
-        T acc0[4], acc1[4];
-#pragma unroll
-        for (int co = 0; co < 4; ++co) acc0[co] = acc1[co] = P.bb[L][co];
+        T v[4][3][4];
 #pragma unroll
         for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                T v[4];
-                lds4(src + ((i + rr - 1) * S1 + (j + e - 1)) * 4, v);
-                if (rr < 3) {
+            for (int e = 0; e < 3; ++e) lds4(src + ((i + rr - 1) * S1 + (j + e - 1)) * 4, v[rr][e]);
+        T acc[2][4];
 #pragma unroll
-                    for (int ci = 0; ci < 4; ++ci)
+        for (int co = 0; co < 4; ++co) acc[0][co] = acc[1][co] = P.bb[L][co];
 #pragma unroll
-                        for (int co = 0; co < 4; ++co) acc0[co] = fma(P.wb[L][co][ci][rr * 3 + e], v[ci], acc0[co]);
-                }
-                if (rr > 0) {
+        for (int a = 0; a < 3; ++a)
 #pragma unroll
-                    for (int ci = 0; ci < 4; ++ci)
+            for (int e = 0; e < 3; ++e)
 #pragma unroll
-                        for (int co = 0; co < 4; ++co)
-                            acc1[co] = fma(P.wb[L][co][ci][(rr - 1) * 3 + e], v[ci], acc1[co]);
-                }
-            }
+                for (int ci = 0; ci < 4; ++ci)
 #pragma unroll
-        for (int co = 0; co < 4; ++co) {
-            acc0[co] = acnn_tanh(acc0[co]);
-            acc1[co] = acnn_tanh(acc1[co]);
+                    for (int co = 0; co < 4; ++co) {
+                        const T w = P.wb[L][co][ci][a * 3 + e];
+                        acc[0][co] = fma(w, v[a][e][ci], acc[0][co]);
+                        acc[1][co] = fma(w, v[a + 1][e][ci], acc[1][co]);
+                    }
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+#pragma unroll
+            for (int co = 0; co < 4; ++co) acc[p][co] = acnn_tanh(acc[p][co]);
+            emit(i + p, j, acc[p]);
         }
-        emit(i, j, acc0);
-        emit(i + 1, j, acc1);
     }
 }
 
@@ -164,67 +160,72 @@ __global__ void __launch_bounds__(kThreads) acnn_fused_kernel(const __grid_const
         su[idx] = ub[(long long)((y0 + i) & mask) * n + ((x0 + j) & mask)];
     }
     __syncthreads();
-    // input conv 1 -> 4 with tanh: frame (i, j) sits at su (i + 1, j + 1)
+    // input conv 1 -> 4 with tanh over the whole frame: frame (i, j) sits at
+    // su (i + 1, j + 1); pairs of rows as in hidden_conv
     for (int idx = threadIdx.x; idx < S1 * S1 / 2; idx += kThreads) {
         const int i = 2 * (idx / S1), j = idx % S1;
-        T acc0[4], acc1[4];
-#pragma unroll
-        for (int co = 0; co < 4; ++co) acc0[co] = acc1[co] = P.bin[co];
+        T v[4][3];
 #pragma unroll
         for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                const T v = su[(i + rr) * S0 + (j + e)];
-                if (rr < 3) {
+            for (int e = 0; e < 3; ++e) v[rr][e] = su[(i + rr) * S0 + (j + e)];
+        T acc[2][4];
 #pragma unroll
-                    for (int co = 0; co < 4; ++co) acc0[co] = fma(P.win[co][rr * 3 + e], v, acc0[co]);
+        for (int co = 0; co < 4; ++co) acc[0][co] = acc[1][co] = P.bin[co];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+#pragma unroll
+                for (int co = 0; co < 4; ++co) {
+                    const T w = P.win[co][a * 3 + e];
+                    acc[0][co] = fma(w, v[a][e], acc[0][co]);
+                    acc[1][co] = fma(w, v[a + 1][e], acc[1][co]);
                 }
-                if (rr > 0) {
 #pragma unroll
-                    for (int co = 0; co < 4; ++co) acc1[co] = fma(P.win[co][(rr - 1) * 3 + e], v, acc1[co]);
-                }
-            }
+        for (int p = 0; p < 2; ++p) {
 #pragma unroll
-        for (int co = 0; co < 4; ++co) {
-            acc0[co] = acnn_tanh(acc0[co]);
-            acc1[co] = acnn_tanh(acc1[co]);
+            for (int co = 0; co < 4; ++co) acc[p][co] = acnn_tanh(acc[p][co]);
+            sts4(X + ((i + p) * S1 + j) * 4, acc[p]);
         }
-        sts4(X + (i * S1 + j) * 4, acc0);
-        sts4(X + ((i + 1) * S1 + j) * 4, acc1);
     }
     __syncthreads();
     run_blocks<T, R, 0>(P, X, Hb);
     // output conv 4 -> 1 on [2R+1, S1-2R-1): exactly the 32 x 32 tile
     constexpr int lo = 2 * R + 1;
     T msum = T(0);
-    for (int idx = threadIdx.x; idx < kTile * kTile / 2; idx += kThreads) {
-        const int ii = 2 * (idx >> 5), jj = idx & 31;
+    for (int idx = threadIdx.x; idx < kTile * kTile / 4; idx += kThreads) {
+        const int ii = 4 * (idx >> 5), jj = idx & 31;
         const int i = lo + ii, j = lo + jj;
-        T acc0 = P.bout, acc1 = P.bout;
+        T v[6][3][4];
 #pragma unroll
-        for (int rr = 0; rr < 4; ++rr)
+        for (int rr = 0; rr < 6; ++rr)
 #pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                T v[4];
-                lds4(X + ((i + rr - 1) * S1 + (j + e - 1)) * 4, v);
-                if (rr < 3) {
+            for (int e = 0; e < 3; ++e) lds4(X + ((i + rr - 1) * S1 + (j + e - 1)) * 4, v[rr][e]);
+        T acc[4];
 #pragma unroll
-                    for (int ci = 0; ci < 4; ++ci) acc0 = fma(P.wout[ci][rr * 3 + e], v[ci], acc0);
+        for (int p = 0; p < 4; ++p) acc[p] = P.bout;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+#pragma unroll
+                for (int ci = 0; ci < 4; ++ci) {
+                    const T w = P.wout[ci][a * 3 + e];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) acc[p] = fma(w, v[p + a][e][ci], acc[p]);
                 }
-                if (rr > 0) {
 #pragma unroll
-                    for (int ci = 0; ci < 4; ++ci) acc1 = fma(P.wout[ci][(rr - 1) * 3 + e], v[ci], acc1);
-                }
+        for (int p = 0; p < 4; ++p) {
+            const long long g = (long long)(ty * kTile + ii + p) * n + tx * kTile + jj;
+            T o = acc[p];
+            if (P.mass_fix) {
+                msum += o - su[(i + p + 1) * S0 + (j + 1)];
+            } else if (P.limiter) {
+                o = o < P.lo ? P.lo : (o > P.hi ? P.hi : o);
             }
-        const long long g0 = (long long)(ty * kTile + ii) * n + tx * kTile + jj;
-        if (P.mass_fix) {
-            msum += (acc0 - su[(i + 1) * S0 + (j + 1)]) + (acc1 - su[(i + 2) * S0 + (j + 1)]);
-        } else if (P.limiter) {
-            acc0 = acc0 < P.lo ? P.lo : (acc0 > P.hi ? P.hi : acc0);
-            acc1 = acc1 < P.lo ? P.lo : (acc1 > P.hi ? P.hi : acc1);
+            ob[g] = o;
         }
-        ob[g0] = acc0;
-        ob[g0 + n] = acc1;
     }
     if (P.mass_fix) {
         __shared__ double red[kThreads / 32];
