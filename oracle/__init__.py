@@ -89,6 +89,11 @@ def lib():
             L.or_parareal_rep.argtypes = [C.POINTER(Params), C.POINTER(Cnn), C.c_int, C.c_int, C.c_int, C.c_int,
                                           C.c_int, C.c_double, C.c_int, dp, dp, dp, dp, C.POINTER(C.c_int)]
             L.or_parareal_rep.restype = C.c_long
+            L.or_fft3d_ri.argtypes = [dp, C.c_int, C.c_int]
+            L.or_solve_A3.argtypes = [C.POINTER(Params), dp, dp]
+            L.or_fine3d_step.argtypes = [C.POINTER(Params), dp, dp]
+            L.or_fine3d_propagate.argtypes = [C.POINTER(Params), C.c_int, dp, dp]
+            L.or_lap3.argtypes = [C.c_int, C.c_double, dp, dp]
             L.or_parareal_acnn.argtypes = [C.POINTER(Params), C.POINTER(Acnn), C.c_int, C.c_int, C.c_int, C.c_int,
                                            C.c_double, dp, dp, dp, dp, C.POINTER(C.c_int)]
             L.or_parareal_acnn.restype = C.c_long
@@ -208,6 +213,42 @@ def acnn_train(p: Params, spec: AcnnSpec, U0s, perm, q, steps, b_inner, lr=1e-3,
                         lr, b1, b2, aeps, _dp(state["m"]), _dp(state["v"]), C.byref(t), _dp(losses))
     state["t"] = t.value
     return losses, state
+
+
+# ------------------------------------------------------------------- 3D --
+def fft3(x: np.ndarray, sign: int = -1) -> np.ndarray:
+    z = np.ascontiguousarray(np.asarray(x, dtype=np.complex128)).copy()
+    lib().or_fft3d_ri(_dp(z.view(np.float64)), z.shape[0], sign)
+    return z
+
+
+def solve_A3(p: Params, r) -> np.ndarray:
+    r = _f64(r)
+    v = np.empty_like(r)
+    lib().or_solve_A3(C.byref(p), _dp(r), _dp(v))
+    return v
+
+
+def fine3d_step(p: Params, u) -> np.ndarray:
+    """One stabilised semi-implicit step on the periodic cube (u: [n][n][n])."""
+    u = _f64(u)
+    out = np.empty_like(u)
+    lib().or_fine3d_step(C.byref(p), _dp(u), _dp(out))
+    return out
+
+
+def fine3d_propagate(p: Params, steps: int, u) -> np.ndarray:
+    u = _f64(u)
+    out = np.empty_like(u)
+    lib().or_fine3d_propagate(C.byref(p), int(steps), _dp(u), _dp(out))
+    return out
+
+
+def lap3(u, h: float) -> np.ndarray:
+    u = _f64(u)
+    out = np.empty_like(u)
+    lib().or_lap3(u.shape[0], float(h), _dp(u), _dp(out))
+    return out
 
 
 # ------------------------------------------------------------------ FFT --

@@ -926,3 +926,94 @@ void or_acnn_train(const or_params* p, or_acnn* d, double* w, double* bias, int 
         }
     free(U); free(U1); free(g); free(gw);
 }
+
+/* ---------------------------------------------------------------- 3D ---- */
+/* The model on the periodic cube (d = 3, Sec. 2; the 3D experiments of
+ * Sec. 4): fields u[i][j][k] row-major with k fastest, N^3 points, h = L/N,
+ * Lap_h the periodic 7-point stencil with symbol
+ * -(4/h^2)(sin^2(pi a/N) + sin^2(pi b/N) + sin^2(pi c/N)). */
+
+/* 3D transform: along k (contiguous), then j, then i. */
+void or_fft3d(cplx* x, int n, int sign) {
+    size_t nn = (size_t)n * n;
+    cplx* line = malloc(sizeof(cplx) * n);
+    for (size_t r = 0; r < nn; r++) or_fft1d(x + r * n, n, sign);
+    for (int i = 0; i < n; i++)
+        for (int k = 0; k < n; k++) {
+            for (int j = 0; j < n; j++) line[j] = x[i * nn + (size_t)j * n + k];
+            or_fft1d(line, n, sign);
+            for (int j = 0; j < n; j++) x[i * nn + (size_t)j * n + k] = line[j];
+        }
+    for (size_t jk = 0; jk < nn; jk++) {
+        for (int i = 0; i < n; i++) line[i] = x[i * nn + jk];
+        or_fft1d(line, n, sign);
+        for (int i = 0; i < n; i++) x[i * nn + jk] = line[i];
+    }
+    free(line);
+}
+
+void or_fft3d_ri(double* xri, int n, int sign) { or_fft3d((cplx*)xri, n, sign); }
+
+static double lap_symbol3(int a, int b, int c, int n, double h) {
+    double sa = sin(PI * a / n), sb = sin(PI * b / n), sc = sin(PI * c / n);
+    return -(4.0 / (h * h)) * (sa * sa + sb * sb + sc * sc);
+}
+
+/* Solve ((1 + S dt) I - dt eps^2 Lap_h) v = r on the cube by the 3D DFT. */
+void or_solve_A3(const or_params* p, const double* r, double* v) {
+    int n = p->n;
+    size_t m = (size_t)n * n * n;
+    double h = p->length / n;
+    cplx* z = malloc(sizeof(cplx) * m);
+    for (size_t i = 0; i < m; i++) z[i] = r[i];
+    or_fft3d(z, n, -1);
+    for (int a = 0; a < n; a++)
+        for (int b = 0; b < n; b++)
+            for (int c = 0; c < n; c++) {
+                double D = 1.0 + p->S * p->dt - p->dt * p->eps * p->eps * lap_symbol3(a, b, c, n, h);
+                z[((size_t)a * n + b) * n + c] /= D;
+            }
+    or_fft3d(z, n, +1);
+    for (size_t i = 0; i < m; i++) v[i] = creal(z[i]) / (double)m;
+    free(z);
+}
+
+/* The stabilised semi-implicit step of or_fine_step on the cube. */
+void or_fine3d_step(const or_params* p, const double* u, double* out) {
+    size_t m = (size_t)p->n * p->n * p->n;
+    double beta = 0.0;
+    if (p->variant == 1) {
+        for (size_t i = 0; i < m; i++) beta += f_dw(u[i]);
+        beta /= (double)m;
+    }
+    double* r = malloc(sizeof(double) * m);
+    for (size_t i = 0; i < m; i++) r[i] = (1.0 + p->S * p->dt) * u[i] + p->dt * (f_dw(u[i]) - beta);
+    or_solve_A3(p, r, out);
+    free(r);
+}
+
+void or_fine3d_propagate(const or_params* p, int steps, const double* u, double* out) {
+    size_t m = (size_t)p->n * p->n * p->n;
+    double* a = malloc(sizeof(double) * m);
+    memcpy(a, u, sizeof(double) * m);
+    for (int s = 0; s < steps; s++) {
+        or_fine3d_step(p, a, out);
+        memcpy(a, out, sizeof(double) * m);
+    }
+    if (steps == 0) memcpy(out, u, sizeof(double) * m);
+    free(a);
+}
+
+/* 7-point periodic Laplacian applied directly. */
+void or_lap3(int n, double h, const double* u, double* out) {
+    size_t nn = (size_t)n * n;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++)
+            for (int k = 0; k < n; k++) {
+                size_t c = i * nn + (size_t)j * n + k;
+                double s = u[((i + 1) % n) * nn + (size_t)j * n + k] + u[((i + n - 1) % n) * nn + (size_t)j * n + k] +
+                           u[i * nn + (size_t)((j + 1) % n) * n + k] + u[i * nn + (size_t)((j + n - 1) % n) * n + k] +
+                           u[i * nn + (size_t)j * n + (k + 1) % n] + u[i * nn + (size_t)j * n + (k + n - 1) % n];
+                out[c] = (s - 6.0 * u[c]) / (h * h);
+            }
+}
