@@ -388,6 +388,49 @@ def run_acnn(args):
     }), flush=True)
 
 
+def run_fine3d(args):
+    """The fine step on the periodic cube (the 3D experiments of Sec. 4: eps =
+    0.02, h = 1/128): 16 mass-conserving float32 fields of 128^3 (seeded
+    U(-0.9, 0.9), zero mean), 20 steps of dt = 1e-4 per call, CUDA events over
+    `--steps` calls after `--warmup`.  Prints one JSON line (not the benchmark
+    line)."""
+    import torch
+    import paper_2510_07672_gb300 as G
+    n, F, steps = 128, 16, 20
+    u = torch.tensor(np.stack([(-0.9 + 1.8 * I.uniform01(7000 + f, I.STREAM_IC, n ** 3)).reshape(n, n, n)
+                               for f in range(F)]), dtype=torch.float32, device="cuda")
+    u -= u.mean(dim=(1, 2, 3), keepdim=True)
+    fp = G.FineParams(n, 0.02, 2.0, 1e-4, variant=G.AC_MASS_CONSERVING, precision=G.AC_F32)
+    out = torch.empty_like(u)
+    work = torch.empty(G.load().ac_fine3d_work_bytes(n, F, G.AC_F32), dtype=torch.uint8, device="cuda")
+    for _ in range(max(args.warmup, 1)):
+        G.ac_fine3d_propagate(fp, steps, u, out, work=work)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = G.ac_launch_count()
+    e0.record(stream)
+    for _ in range(args.steps):
+        G.ac_fine3d_propagate(fp, steps, u, out, work=work)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = G.ac_launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    cells = F * n ** 3 * steps
+    peaks, src = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    pass_bytes = 40.0 * cells  # five passes: 80 bytes per complex cell pair and step
+    print(json.dumps({
+        "metric": "3D fine propagation (periodic cube, 7-point Laplacian, FFT solve)",
+        "workload": "fine3d-mass-f32-128cube-16f-20steps", "ms_per_call": ms, "cell_steps_per_s": cells / (ms * 1e-3),
+        "us_per_step": ms * 1e3 / steps, "gpu_launches_per_call": launches / args.steps,
+        "roofline": {"bound": "hbm", "achieved": pass_bytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": pass_bytes / (ms * 1e-3) / 1e9 / hbm,
+                     "traffic_model": "40 B per cell-step (5 passes, complex pairs); the one-read-one-write "
+                                      "minimum is 8 B", "peak_source": src},
+        "mass_drift": float((out.double().mean(dim=(1, 2, 3)) - u.double().mean(dim=(1, 2, 3))).abs().max().item()),
+        "steps": args.steps, "warmup": args.warmup}), flush=True)
+
+
 def run_adjoint(args):
     """The adjoint workload: dE_h(u^2000)/du^0 of one 256^2 classic field
     (eps = 0.01, dt = 5e-5, S = 2) by the checkpointed adjoint (a checkpoint
@@ -489,11 +532,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--weights", default="trained", help="'trained' (the committed G), 'untrained', or a .npz path")
-    ap.add_argument("--workload", default="mass256", choices=["mass256", "uneven", "train", "adjoint", "acnn"],
+    ap.add_argument("--workload", default="mass256", choices=["mass256", "uneven", "train", "adjoint", "acnn", "fine3d"],
                     help="mass256: the benchmark line; uneven: 64 classic problems of uneven size (batching); "
                          "train: coarse-net training iterations (C = 64, 8 layers); "
                          "adjoint: checkpointed energy gradient through 2000 steps; "
-                         "acnn: the paper's ResBlock mACNN (Algorithm 1 training, G time, Parareal)")
+                         "acnn: the paper's ResBlock mACNN (Algorithm 1 training, G time, Parareal); "
+                         "fine3d: the fine step on the 128^3 periodic cube")
     ap.add_argument("--acnn-epochs", type=int, default=20)
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--coarse-substeps", type=int, default=1,
@@ -518,6 +562,9 @@ def main():
         return
     if args.workload == "acnn":
         run_acnn(args)
+        return
+    if args.workload == "fine3d":
+        run_fine3d(args)
         return
 
     # host-side oracle sample first (before any GPU work in this process)

@@ -296,6 +296,29 @@ int mse_loss_grad(const float* pred, const float* target, long long count, doubl
                   acpr_stream stream);
 
 /* ------------------------------------------------------------------------
+ * The fine step on the periodic cube (d = 3; the 3D experiments of Sec. 4):
+ * the stabilised semi-implicit step of ac_params with the periodic 7-point
+ * Laplacian (symbol -(4/h^2)(sin^2(pi a/N) + sin^2(pi b/N) + sin^2(pi c/N))),
+ * solved by a 3D FFT in five passes over L2/HBM per step.  Fields are
+ * [num_fields][n][n][n] row-major (last index fastest), params->n = n per
+ * side.  The mass-conserving variant holds the zero mode at the field's
+ * mean taken when the call starts (the scheme conserves it exactly).
+ * ------------------------------------------------------------------------ */
+
+/* 1 if the 3D step is built for (n, precision): n = 32, 64 or 128. */
+int ac_fine3d_supported(int n, int precision);
+
+/* Device scratch bytes for `num_fields` fields (complex spectra of the field
+ * pairs, tables, mean partials). */
+size_t ac_fine3d_work_bytes(int n, int num_fields, int precision);
+
+/* `steps` fine steps of every field: u_out = F^steps(u_in).  u_in may equal
+ * u_out.  work: ac_fine3d_work_bytes() bytes of device memory.  Asynchronous
+ * on `stream`. */
+int ac_fine3d_propagate(const ac_params* params, int steps, int num_fields, const void* u_in, void* u_out,
+                        void* work, size_t work_bytes, acpr_stream stream);
+
+/* ------------------------------------------------------------------------
  * The paper's ResBlock ACNN / mACNN (Sec. 3.2) and its training with the
  * scheme-residual loss (Eq. loss_ACN, Algorithm 1).
  *

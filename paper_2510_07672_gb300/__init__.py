@@ -16,5 +16,5 @@ from .abi import (  # noqa: F401
     cnn_packed_bytes, cnn_work_bytes, cnn_pack_weights, cnn_coarse_step,
     parareal_residual, parareal_residual_noalloc, ac_launch_count, parareal_solve_many, Parareal, CoarseNet, FineParams,
     TrainableCoarseNet, mse_loss_grad, coarse_step_function,
-    Acnn, acnn_param_count, loss_acn,
+    Acnn, acnn_param_count, loss_acn, ac_fine3d_propagate,
 )

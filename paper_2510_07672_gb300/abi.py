@@ -65,7 +65,8 @@ EXPORTS = ["ac_last_error", "ac_fine_supported", "ac_fine_step", "ac_fine_propag
            "cnn_train_bytes", "cnn_forward_train", "cnn_backward", "cnn_adam_step", "mse_loss_grad",
            "acnn_param_count", "acnn_create", "acnn_destroy", "acnn_work_bytes", "acnn_forward", "acnn_train_bytes",
            "acnn_forward_train", "acnn_backward", "loss_acn_work_bytes", "loss_acn", "acnn_adam_step",
-           "acnn_train_alg1", "ac_parareal_set_coarse_acnn"]
+           "acnn_train_alg1", "ac_parareal_set_coarse_acnn",
+           "ac_fine3d_supported", "ac_fine3d_work_bytes", "ac_fine3d_propagate"]
 
 
 def lib_path() -> str:
@@ -154,6 +155,10 @@ def load(build_if_missing: bool = True):
         L.acnn_train_alg1.argtypes = [P(ac_params), P(acnn_desc), I, S, P(I), I, I, I, I, D, D, D, D, S, S, P(I),
                                       S, S]
         L.ac_parareal_set_coarse_acnn.argtypes = [S, S]
+        L.ac_fine3d_supported.argtypes = [I, I]
+        L.ac_fine3d_work_bytes.argtypes = [I, I, I]
+        L.ac_fine3d_work_bytes.restype = C.c_size_t
+        L.ac_fine3d_propagate.argtypes = [P(ac_params), I, I, S, S, S, C.c_size_t, S]
         _lib = L
         return L
 
@@ -442,6 +447,26 @@ def mse_loss_grad(pred, target, scale, grad=None, grad_accumulate=False, loss=No
                                 pred.numel(), float(scale), g, int(grad_accumulate), _dev(loss, torch.float64, "loss"),
                                 _dev(scratch, torch.float64, "scratch"), int(accumulate), _stream(stream)))
     return loss
+
+
+def ac_fine3d_propagate(params: FineParams, steps: int, u_in, u_out=None, work=None, stream=None):
+    """`steps` fine steps of the fields u_in [F][n][n][n] on the periodic cube."""
+    import torch
+    n = params.n
+    if u_in.shape[-3:] != (n, n, n):
+        raise ValueError(f"fields must be [F][{n}][{n}][{n}]")
+    F = u_in.numel() // (n ** 3)
+    u_out = u_out if u_out is not None else torch.empty_like(u_in)
+    need = load().ac_fine3d_work_bytes(n, F, params.precision)
+    if need == 0:
+        raise AcprError(-2, f"3D fine step not built for n={n}")
+    if work is None or work.numel() < need:
+        work = torch.empty(need, dtype=torch.uint8, device=u_in.device)
+    p = params.c()
+    _check(load().ac_fine3d_propagate(C.byref(p), int(steps), F, _dev(u_in, params.dtype, "u_in"),
+                                      _dev(u_out, params.dtype, "u_out"), _dev(work, None, "work"), need,
+                                      _stream(stream)))
+    return u_out
 
 
 def acnn_param_count(channels: int, blocks: int):
