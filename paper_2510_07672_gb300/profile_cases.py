@@ -4,6 +4,7 @@
     python -m paper_2510_07672_gb300.profile_cases conv   # cnn_coarse_step, 16 x 256^2, 1-32x6-1 gelu bf16
     python -m paper_2510_07672_gb300.profile_cases big    # ac_fine_propagate_slices, 16 x 1024^2, 2 steps
     python -m paper_2510_07672_gb300.profile_cases acnn   # acnn_forward (fused), 512 x 256^2, C = 4, 2 blocks
+    python -m paper_2510_07672_gb300.profile_cases fine3d # ac_fine3d_propagate, 16 x 128^3, 1 step (5 passes)
 
 Each case runs its call twice (a warm-up launch, then the one to capture) and
 exits 0, so `ncu -s <warm-up launches> -c 1` captures a warm launch.  Inputs
@@ -57,8 +58,16 @@ def main(case: str) -> None:
         out = torch.empty_like(u)
         for _ in range(2):
             net(u, out=out)
+    elif case == "fine3d":
+        n = 128
+        u = torch.tensor(np.stack([(-0.9 + 1.8 * I.uniform01(7000 + f, I.STREAM_IC, n ** 3)).reshape(n, n, n)
+                                   for f in range(16)]), dtype=torch.float32, device="cuda")
+        fp = G.FineParams(n, 0.02, 2.0, 1e-4, variant=G.AC_MASS_CONSERVING, precision=G.AC_F32)
+        out = torch.empty_like(u)
+        for _ in range(2):
+            G.ac_fine3d_propagate(fp, 1, u, out)
     else:
-        raise SystemExit(f"unknown case {case!r} (fine | conv | big | acnn)")
+        raise SystemExit(f"unknown case {case!r} (fine | conv | big | acnn | fine3d)")
     torch.cuda.synchronize()
     print(f"{case}: ok")
 
