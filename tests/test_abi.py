@@ -73,3 +73,38 @@ def test_binding_refuses_cpu_tensors():
     fp = G.FineParams(64, 0.01, 2.0, 1e-4)
     with pytest.raises(ValueError, match="CUDA tensor"):
         G.ac_fine_step(fp, torch.zeros(1, 64, 64))
+
+
+def test_acnn_and_3d_host_queries_and_argument_errors():
+    """Host-only entry points of the ResBlock ACNN (Sec. 3.2) and the 3D step:
+    sizes and argument validation, no GPU touched."""
+    L = G.load()
+    nb = C.c_longlong()
+    assert L.acnn_param_count(4, 2, C.byref(nb)) == 36 + 4 * 144 + 36 and nb.value == 21
+    assert L.acnn_param_count(16, 3, None) == 9 * 16 + 6 * 9 * 256 + 9 * 16
+    assert L.acnn_param_count(8, 2, None) == -1          # C = 8 not built
+    assert L.acnn_param_count(4, 5, None) == -1          # at most 4 blocks
+    assert L.loss_acn_work_bytes(256, 4) >= 8 * 256 * 256 * 4
+    assert L.loss_acn_work_bytes(48, 4) == 0
+    d = abi.acnn_desc(8, 2, 0, 0, -1.0, 1.0, 1, 16, 16)
+    h = C.c_void_p()
+    assert L.acnn_create(C.byref(d), C.byref(h)) == -2   # unsupported width
+    d = abi.acnn_desc(4, 2, 0, 1, 1.0, -1.0, 1, 16, 16)
+    assert L.acnn_create(C.byref(d), C.byref(h)) == -1   # limiter lo >= hi
+    d = abi.acnn_desc(4, 2, 0, 0, -1.0, 1.0, 1, None, None)
+    assert L.acnn_forward_train(C.byref(d), 64, 1, None, None, None, None) == -1
+    assert L.acnn_train_bytes(C.byref(d), 64, 1) == 0    # null parameters
+    assert L.acnn_adam_step(1, None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, 1, None) == -1
+    assert L.acnn_adam_step(1, 16, 16, 16, 16, 10, 1e-3, 0.9, 0.999, 1e-8, 0, None) == -1   # t >= 1
+    p = abi.ac_params(64, 1.0, 0.01, 2.0, 1e-2, 1, 1)
+    assert L.loss_acn(C.byref(p), 0, None, None, None, None, None, None) == -1
+    assert L.ac_fine3d_supported(128, G.AC_F32) == 1
+    assert L.ac_fine3d_supported(256, G.AC_F32) == 0
+    assert L.ac_fine3d_work_bytes(128, 3, G.AC_F32) >= 2 * 8 * 128 ** 3   # two complex pairs
+    p3 = abi.ac_params(256, 1.0, 0.02, 2.0, 1e-4, 0, 1)
+    assert L.ac_fine3d_propagate(C.byref(p3), 1, 1, None, None, None, 0, None) == -2
+    p3 = abi.ac_params(64, 1.0, 0.02, 2.0, 1e-4, 0, 1)
+    assert L.ac_fine3d_propagate(C.byref(p3), 1, 0, None, None, None, 0, None) == 0     # no fields
+    assert L.ac_fine3d_propagate(C.byref(p3), 1, 2, None, None, None, 0, None) == -1    # null fields
+    assert L.ac_parareal_set_coarse_acnn(None, None) == -1
+    assert L.ac_parareal_set_coarse_substeps(None, 2) == -1
