@@ -499,6 +499,7 @@ class Acnn:
             raise ValueError(f"ACNN C={channels} blocks={blocks} takes {nw} weights and {nb} biases")
         self.nw, self.nb = nw, nb
         self._h = None
+        self._retired = []   # earlier handles: a Parareal handle may still point at one
         self._work = {}
         self.m = self.v = None
         self.t = 0
@@ -516,10 +517,19 @@ class Acnn:
         return self._h
 
     def invalidate(self):
-        """Drop the inference handle (call after changing w or b in place)."""
+        """Retire the inference handle (call after changing w or b in place);
+        the next use builds a new one.  Retired handles are freed with the
+        object, since a Parareal handle may still point at one until it
+        re-attaches (it does so before every iteration)."""
         if self._h is not None:
-            load().acnn_destroy(self._h)
+            self._retired.append(self._h)
             self._h = None
+
+    def _free_handles(self):
+        L = load()
+        for h in self._retired + ([self._h] if self._h is not None else []):
+            L.acnn_destroy(h)
+        self._retired, self._h = [], None
 
     def __call__(self, u, out=None, stream=None):
         """G(u) for u [batch][n][n] (or [n][n]) through the inference handle."""
@@ -610,7 +620,7 @@ class Acnn:
 
     def __del__(self):
         try:
-            self.invalidate()
+            self._free_handles()
         except Exception:
             pass
 
@@ -688,6 +698,8 @@ def cnn_coarse_step(net: CoarseNet, u_in, u_out=None, stream=None):
 def parareal_solve_many(handles, streams, tol, kmax, allow_unconverged=False):
     """ac_parareal_solve_many over Parareal handles (one stream each)."""
     L = load()
+    for h in handles:
+        h._sync_acnn()
     total = sum(h.problems for h in handles)
     hs = (C.c_void_p * len(handles))(*[h._h.value for h in handles])
     ss = (C.c_void_p * len(handles))(*[s.cuda_stream for s in streams])
@@ -763,14 +775,21 @@ class Parareal:
         self._h = h
         self.k = 0
         self._acnn = None
+        self._acnn_h = None
         if acnn is not None:
             self.set_coarse_acnn(acnn)
 
     def set_coarse_acnn(self, acnn):
         """Use the ResBlock ACNN as G (None: back to the conv stack the handle
-        was created with)."""
-        self._acnn = acnn
-        _check(load().ac_parareal_set_coarse_acnn(self._h, acnn.handle() if acnn is not None else None))
+        was created with).  The net's current parameters are used: after an
+        update of the net the next iteration re-attaches its new handle."""
+        h = acnn.handle() if acnn is not None else None
+        _check(load().ac_parareal_set_coarse_acnn(self._h, h))
+        self._acnn, self._acnn_h = acnn, h
+
+    def _sync_acnn(self):
+        if self._acnn is not None and self._acnn._h is not self._acnn_h:
+            self.set_coarse_acnn(self._acnn)
 
     def enable_graphs(self, on=True):
         _check(load().ac_parareal_enable_graphs(self._h, int(on)))
@@ -786,6 +805,7 @@ class Parareal:
         _check(load().ac_parareal_set_fine_scheme(self._h, int(scheme), float(tol), int(max_iters)))
 
     def iterate(self, stream=None):
+        self._sync_acnn()
         kk = C.c_int(self.k)
         l2 = (C.c_double * self.problems)()
         mx = (C.c_double * self.problems)()
@@ -797,6 +817,7 @@ class Parareal:
         _check(load().ac_parareal_set_active(self._h, int(p), int(active)))
 
     def solve(self, tol: float, kmax: int, stream=None, allow_unconverged=False):
+        self._sync_acnn()
         it = (C.c_int * self.problems)()
         l2 = (C.c_double * self.problems)()
         rc = load().ac_parareal_solve(self._h, float(tol), int(kmax), it, l2, _stream(stream))

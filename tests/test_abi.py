@@ -5,6 +5,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2510_07672_gb300 as G
@@ -108,3 +109,52 @@ def test_acnn_and_3d_host_queries_and_argument_errors():
     assert L.ac_fine3d_propagate(C.byref(p3), 1, 2, None, None, None, 0, None) == -1    # null fields
     assert L.ac_parareal_set_coarse_acnn(None, None) == -1
     assert L.ac_parareal_set_coarse_substeps(None, 2) == -1
+
+
+def test_acnn_handle_lifetime_with_a_parareal_handle(monkeypatch):
+    """Host logic of the binding, with a stand-in library: updating an Acnn
+    attached to a Parareal handle retires (does not free) its inference
+    handle, the Parareal handle re-attaches the new one before the next
+    iteration, and every handle is freed with the Acnn object."""
+    torch = pytest.importorskip("torch")
+
+    class FakeLib:
+        def __init__(self):
+            self.created, self.destroyed, self.attached, self.next = [], [], [], 100
+
+        def acnn_param_count(self, c, b, nb):
+            nb._obj.value = 21
+            return 648
+
+        def acnn_create(self, d, out):
+            out._obj.value = self.next
+            self.created.append(self.next)
+            self.next += 1
+            return 0
+
+        def acnn_destroy(self, h):
+            self.destroyed.append(h.value)
+
+        def ac_parareal_set_coarse_acnn(self, st, h):
+            self.attached.append(None if h is None else h.value)
+            return 0
+
+        def parareal_iterate(self, st, kk, l2, mx, s):
+            return 0
+
+    fake = FakeLib()
+    monkeypatch.setattr(abi, "load", lambda build_if_missing=True: fake)
+    monkeypatch.setattr(abi, "_stream", lambda s: None)
+    net = abi.Acnn(4, 2, np.zeros(648), np.zeros(21), device="cpu")
+    pr = abi.Parareal.__new__(abi.Parareal)
+    pr._h, pr.k, pr.problems, pr._acnn, pr._acnn_h = C.c_void_p(1), 0, 1, None, None
+    pr.set_coarse_acnn(net)
+    assert fake.attached == [100]
+    pr.iterate()
+    assert fake.attached == [100]            # unchanged net: no re-attach
+    net.invalidate()                         # as after an Adam step
+    assert fake.destroyed == []              # the attached handle stays alive
+    pr.iterate()
+    assert fake.attached == [100, 101]       # re-attached to the new handle
+    net._free_handles()
+    assert sorted(fake.destroyed) == [100, 101]
