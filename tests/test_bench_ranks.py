@@ -49,3 +49,22 @@ def test_max_over_ranks_and_job_rate_two_gloo_ranks():
 def test_single_rank_is_identity():
     assert bench.max_over_ranks(3.5, 1, "cpu") == 3.5
     assert bench.job_rate(50.0, 10.0, 1) == pytest.approx(5000.0)
+
+
+def test_cost_model_with_coarse_composition():
+    """Sec. 3.4's T(k) = c k t_num + (2s - k)(k + 1)/2 m t_nn with the unit costs
+    taken from the measured phases: m = 1 reproduces the plain model; composing
+    G m times multiplies the coarse term by m."""
+    s, c, k = 16, 400, 16
+    seq_ms = 57.6
+    t_nn = 0.44
+    calls1 = (2 * s - k) * (k + 1) // 2
+    st = {"coarse_calls": calls1, "coarse_ms": calls1 * t_nn}
+    one = bench.cost_model(st, seq_ms, [k], 1, s, c, 1)
+    t_num = seq_ms / (s * c)
+    assert abs(one["T_k_ms"] - (c * k * t_num + calls1 * t_nn)) < 1e-9
+    st2 = {"coarse_calls": 2 * calls1, "coarse_ms": 2 * calls1 * t_nn}
+    two = bench.cost_model(st2, seq_ms, [k], 1, s, c, 2)
+    assert abs(two["t_nn_ms"] - t_nn) < 1e-12
+    assert abs(two["T_k_ms"] - (c * k * t_num + 2 * calls1 * t_nn)) < 1e-9
+    assert two["S_k"] < one["S_k"]
