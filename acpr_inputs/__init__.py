@@ -132,6 +132,22 @@ def acnn_weights(channels: int, blocks: int, seed: int, gain: float = 1.0):
     return np.concatenate(w), np.concatenate(b)
 
 
+def acnn3d_weights(channels: int, blocks: int, seed: int, gain: float = 1.0):
+    """Initial parameters of the ResBlock ACNN with 3 x 3 x 3 convolutions:
+    uniform in (-gain/sqrt(27 cin), gain/sqrt(27 cin)) per convolution, in
+    the concatenated layout W_l[cout][cin][3][3][3] / b_l[cout]."""
+    dims = acnn_layer_dims(channels, blocks)
+    w, b = [], []
+    ow = ob = 0
+    for ci, co in dims:
+        bound = gain / np.sqrt(27.0 * ci)
+        w.append(bound * (2.0 * uniform01(seed, STREAM_WEIGHTS, ci * co * 27, offset=ow) - 1.0))
+        b.append(bound * (2.0 * uniform01(seed, STREAM_BIAS, co, offset=ob) - 1.0))
+        ow += ci * co * 27
+        ob += co
+    return np.concatenate(w), np.concatenate(b)
+
+
 @dataclasses.dataclass(frozen=True)
 class Workload:
     """One Allen-Cahn Parareal workload (all problems share these settings)."""

@@ -94,6 +94,12 @@ def lib():
             L.or_fine3d_step.argtypes = [C.POINTER(Params), dp, dp]
             L.or_fine3d_propagate.argtypes = [C.POINTER(Params), C.c_int, dp, dp]
             L.or_lap3.argtypes = [C.c_int, C.c_double, dp, dp]
+            L.or_acnn3d_param_counts.argtypes = [C.POINTER(Acnn), C.POINTER(C.c_long)]
+            L.or_acnn3d_param_counts.restype = C.c_long
+            L.or_acnn3d_forward.argtypes = [C.POINTER(Acnn), C.c_int, C.c_int, dp, dp]
+            L.or_parareal3d.argtypes = [C.POINTER(Params), C.POINTER(Acnn), C.c_int, C.c_int, C.c_int, C.c_int,
+                                        C.c_int, C.c_double, dp, dp, dp, dp, C.POINTER(C.c_int)]
+            L.or_parareal3d.restype = C.c_long
             L.or_parareal_acnn.argtypes = [C.POINTER(Params), C.POINTER(Acnn), C.c_int, C.c_int, C.c_int, C.c_int,
                                            C.c_double, dp, dp, dp, dp, C.POINTER(C.c_int)]
             L.or_parareal_acnn.restype = C.c_long
@@ -242,6 +248,47 @@ def fine3d_propagate(p: Params, steps: int, u) -> np.ndarray:
     out = np.empty_like(u)
     lib().or_fine3d_propagate(C.byref(p), int(steps), _dp(u), _dp(out))
     return out
+
+
+class Acnn3dSpec:
+    """The ResBlock ACNN with 3 x 3 x 3 convolutions (parameters
+    W_l[cout][cin][3][3][3] in the 2D network's layer order)."""
+
+    def __init__(self, channels, blocks, w, b, mass_fix=0, limiter=0, lo=-1.0, hi=1.0):
+        self.w = _f64(w).ravel().copy()
+        self.b = _f64(b).ravel().copy()
+        self.s = Acnn(int(channels), int(blocks), int(mass_fix), int(limiter), float(lo), float(hi),
+                      _dp(self.w), _dp(self.b))
+        nb = C.c_long()
+        nw = lib().or_acnn3d_param_counts(C.byref(self.s), C.byref(nb))
+        if self.w.size != nw or self.b.size != nb.value:
+            raise ValueError(f"3D ACNN C={channels} blocks={blocks} takes {nw} weights and {nb.value} biases")
+
+
+def acnn3d_forward(spec: Acnn3dSpec, u) -> np.ndarray:
+    u = _f64(u)
+    out = np.empty_like(u)
+    batch = 1 if u.ndim == 3 else u.shape[0]
+    lib().or_acnn3d_forward(C.byref(spec.s), u.shape[-1], batch, _dp(u), _dp(out))
+    return out
+
+
+def parareal3d(p: Params, coarse, s: int, c: int, kmax: int, tol: float, u0, coarse_steps: int = 0,
+               coarse_repeat: int = 1):
+    """Algorithm 2 on the periodic cube: F = the 3D fine step; G = the 3D
+    ACNN (coarse: Acnn3dSpec) or the 3D fine step over coarse_steps steps
+    (coarse None)."""
+    u0 = _f64(u0)
+    n = u0.shape[-1]
+    U = np.empty((s + 1, n, n, n))
+    rl2 = np.zeros(kmax + 2)
+    rmx = np.zeros(kmax + 2)
+    it = C.c_int()
+    cptr = C.byref(coarse.s) if coarse is not None else None
+    g = lib().or_parareal3d(C.byref(p), cptr, int(coarse_steps), int(coarse_repeat), int(s), int(c), int(kmax),
+                            float(tol), _dp(u0), _dp(U), _dp(rl2), _dp(rmx), C.byref(it))
+    k = it.value
+    return dict(U=U, res_l2=rl2[1:k + 1].copy(), res_max=rmx[1:k + 1].copy(), iters=k, g_calls=g)
 
 
 def lap3(u, h: float) -> np.ndarray:

@@ -508,8 +508,14 @@ void or_cnn_backward(const or_cnn* d, int n, const double* u, const double* gout
 /* ---------------------------------------------------------- Parareal ---- */
 /* Relative L2 and sup-norm increments between two trajectories over slices
  * j = 1..s (Sec. 3.3 convergence test; relative L2 reading of the tolerance). */
+static void or_residual_len(int s, size_t m, const double* Unew, const double* Uold, double* l2, double* mx);
+
 void or_residual(int s, int n, const double* Unew, const double* Uold, double* l2, double* mx) {
-    size_t m = (size_t)n * n;
+    or_residual_len(s, (size_t)n * n, Unew, Uold, l2, mx);
+}
+
+/* The same over slices of m values each (any dimension). */
+static void or_residual_len(int s, size_t m, const double* Unew, const double* Uold, double* l2, double* mx) {
     double num = 0.0, den = 0.0, mxv = 0.0;
     for (int j = 1; j <= s; j++)
         for (size_t i = 0; i < m; i++) {
@@ -532,16 +538,33 @@ void or_residual(int s, int n, const double* Unew, const double* Uold, double* l
  * when `literal` is set. */
 typedef struct or_acnn_s or_acnn;
 void or_acnn_forward(const or_acnn* d, int n, int batch, const double* u, double* out);
+void or_acnn3d_forward(const or_acnn* d, int n, int batch, const double* u, double* out);
+void or_fine3d_propagate(const or_params* p, int steps, const double* u, double* out);
 
 /* The coarse propagator of one solve: the conv stack, the ResBlock ACNN, or
- * (both NULL) F over coarse_steps fine steps. */
-typedef struct { const or_cnn* cnn; const or_acnn* acnn; int coarse_steps; } or_coarse;
+ * (both NULL) F over coarse_steps fine steps; dim 2 (the square) or 3 (the
+ * cube: the ACNN with 3 x 3 x 3 convolutions, or the 3D fine step). */
+typedef struct { const or_cnn* cnn; const or_acnn* acnn; int coarse_steps; int dim; } or_coarse;
+
+static size_t or_field_len(const or_params* p, int dim) {
+    return dim == 3 ? (size_t)p->n * p->n * p->n : (size_t)p->n * p->n;
+}
+
+static void or_fine_any(const or_params* p, int dim, int steps, const double* in, double* out) {
+    if (dim == 3) or_fine3d_propagate(p, steps, in, out);
+    else or_fine_propagate(p, steps, in, out);
+}
 
 /* One application of the coarse propagator. */
 static void or_coarse_once(const or_params* p, const or_coarse* g, const double* in, double* out) {
-    if (g->acnn) or_acnn_forward(g->acnn, p->n, 1, in, out);
-    else if (g->cnn) or_cnn_forward(g->cnn, p->n, in, out);
-    else or_fine_propagate(p, g->coarse_steps, in, out);
+    if (g->acnn) {
+        if (g->dim == 3) or_acnn3d_forward(g->acnn, p->n, 1, in, out);
+        else or_acnn_forward(g->acnn, p->n, 1, in, out);
+    } else if (g->cnn) {
+        or_cnn_forward(g->cnn, p->n, in, out);
+    } else {
+        or_fine_any(p, g->dim, g->coarse_steps, in, out);
+    }
 }
 
 /* The coarse evaluation of a slice: `repeat` applications of the coarse
@@ -549,7 +572,7 @@ static void or_coarse_once(const or_params* p, const or_coarse* g, const double*
  * plain G).  tmp holds one field. */
 static void or_coarse_eval(const or_params* p, const or_coarse* g, int repeat, const double* in, double* out,
                            double* tmp) {
-    size_t m = (size_t)p->n * p->n;
+    size_t m = or_field_len(p, g->dim);
     if (repeat <= 1) { or_coarse_once(p, g, in, out); return; }
     memcpy(tmp, in, sizeof(double) * m);
     for (int r = 0; r < repeat; r++) {
@@ -564,7 +587,7 @@ static long or_parareal_g(const or_params* p, const or_coarse* g, int repeat, in
 long or_parareal(const or_params* p, const or_cnn* coarse, int coarse_steps, int s, int c,
                  int kmax, double tol, int literal, const double* u0, double* U,
                  double* res_l2, double* res_max, int* iters) {
-    or_coarse g = {coarse, NULL, coarse_steps};
+    or_coarse g = {coarse, NULL, coarse_steps, 2};
     return or_parareal_g(p, &g, 1, s, c, kmax, tol, literal, u0, U, res_l2, res_max, iters);
 }
 
@@ -573,21 +596,29 @@ long or_parareal(const or_params* p, const or_cnn* coarse, int coarse_steps, int
 long or_parareal_rep(const or_params* p, const or_cnn* coarse, int coarse_steps, int repeat, int s, int c,
                      int kmax, double tol, int literal, const double* u0, double* U,
                      double* res_l2, double* res_max, int* iters) {
-    or_coarse g = {coarse, NULL, coarse_steps};
+    or_coarse g = {coarse, NULL, coarse_steps, 2};
     return or_parareal_g(p, &g, repeat, s, c, kmax, tol, literal, u0, U, res_l2, res_max, iters);
 }
 
 /* Algorithm 2 with the ResBlock ACNN (Sec. 3.2) as G. */
 long or_parareal_acnn(const or_params* p, const or_acnn* coarse, int repeat, int s, int c, int kmax, double tol,
                       const double* u0, double* U, double* res_l2, double* res_max, int* iters) {
-    or_coarse g = {NULL, coarse, 0};
+    or_coarse g = {NULL, coarse, 0, 2};
+    return or_parareal_g(p, &g, repeat, s, c, kmax, tol, 0, u0, U, res_l2, res_max, iters);
+}
+
+/* Algorithm 2 on the periodic cube: the 3D fine step as F, and as G the
+ * ResBlock ACNN with 3 x 3 x 3 convolutions (coarse != NULL) or the 3D fine
+ * step over coarse_steps steps. */
+long or_parareal3d(const or_params* p, const or_acnn* coarse, int coarse_steps, int repeat, int s, int c, int kmax,
+                   double tol, const double* u0, double* U, double* res_l2, double* res_max, int* iters) {
+    or_coarse g = {NULL, coarse, coarse_steps, 3};
     return or_parareal_g(p, &g, repeat, s, c, kmax, tol, 0, u0, U, res_l2, res_max, iters);
 }
 
 static long or_parareal_g(const or_params* p, const or_coarse* gc, int repeat, int s, int c, int kmax, double tol,
                           int literal, const double* u0, double* U, double* res_l2, double* res_max, int* iters) {
-    int n = p->n;
-    size_t m = (size_t)n * n;
+    size_t m = or_field_len(p, gc->dim);
     double* Uold = malloc(sizeof(double) * m * (s + 1));
     double* Gold = malloc(sizeof(double) * m * s);
     double* Ff = malloc(sizeof(double) * m * s);
@@ -607,7 +638,7 @@ static long or_parareal_g(const or_params* p, const or_coarse* gc, int repeat, i
     for (k = 1; k <= kmax && k <= s; k++) {
         memcpy(Uold, U, sizeof(double) * m * (s + 1));
         /* fine solves, independent over n = k-1 .. s-1 */
-        for (int j = k - 1; j < s; j++) or_fine_propagate(p, c, Uold + j * m, Ff + j * m);
+        for (int j = k - 1; j < s; j++) or_fine_any(p, gc->dim, c, Uold + j * m, Ff + j * m);
         /* sequential correction */
         for (int j = k - 1; j < s; j++) {
             if (literal) {
@@ -629,7 +660,7 @@ static long or_parareal_g(const or_params* p, const or_coarse* gc, int repeat, i
                 }
             }
         }
-        or_residual(s, n, U, Uold, &res_l2[k], &res_max[k]);
+        or_residual_len(s, m, U, Uold, &res_l2[k], &res_max[k]);
         if (res_l2[k] < tol) break;
     }
     if (k > kmax || k > s) k--;
@@ -1016,4 +1047,83 @@ void or_lap3(int n, double h, const double* u, double* out) {
                            u[i * nn + (size_t)j * n + (k + 1) % n] + u[i * nn + (size_t)j * n + (k + n - 1) % n];
                 out[c] = (s - 6.0 * u[c]) / (h * h);
             }
+}
+
+/* ------------------------------------------- ResBlock ACNN on the cube ---- */
+/* The network of or_acnn_forward with 3 x 3 x 3 circular convolutions (the
+ * 3D experiments of Sec. 4): parameters W_l[cout][cin][3][3][3] concatenated
+ * in the same layer order, biases as in 2D.  Fields [n][n][n], last index
+ * fastest. */
+static void acnn3_offsets(const or_acnn* d, int l, int* wo, int* bo) {
+    int w = 0, b = 0;
+    for (int i = 0; i < l; i++) { int ci, co; acnn_dims(d, i, &ci, &co); w += ci * co * 27; b += co; }
+    *wo = w; *bo = b;
+}
+
+long or_acnn3d_param_counts(const or_acnn* d, long* nb) {
+    int wo, bo;
+    acnn3_offsets(d, acnn_convs(d), &wo, &bo);
+    if (nb) *nb = bo;
+    return wo;
+}
+
+/* out[o][i][j][k] = b[o] + sum_{c,a,e,g} W[o][c][a][e][g] in[c][i+a-1][j+e-1][k+g-1] (indices mod n). */
+static void conv3x3x3(int n, int cin, int cout, const double* W, const double* b, const double* in, double* out) {
+    size_t m = (size_t)n * n * n, nn = (size_t)n * n;
+    for (int o = 0; o < cout; o++)
+        for (int i = 0; i < n; i++)
+            for (int j = 0; j < n; j++)
+                for (int k = 0; k < n; k++) {
+                    double acc = b[o];
+                    for (int c = 0; c < cin; c++)
+                        for (int a = 0; a < 3; a++)
+                            for (int e = 0; e < 3; e++)
+                                for (int g = 0; g < 3; g++) {
+                                    size_t ii = (i + a - 1 + n) % n, jj = (j + e - 1 + n) % n, kk = (k + g - 1 + n) % n;
+                                    acc += W[(((o * cin + c) * 3 + a) * 3 + e) * 3 + g] * in[c * m + ii * nn + jj * n + kk];
+                                }
+                    out[o * m + (size_t)i * nn + (size_t)j * n + k] = acc;
+                }
+}
+
+static void acnn3d_one(const or_acnn* d, int n, const double* u, double* out, double* x, double* h, double* t,
+                       double* o) {
+    size_t m = (size_t)n * n * n;
+    int C = d->channels, R = d->blocks;
+    int wo, bo;
+    acnn3_offsets(d, 0, &wo, &bo);
+    conv3x3x3(n, 1, C, d->w + wo, d->b + bo, u, x);
+    for (size_t i = 0; i < (size_t)C * m; i++) x[i] = tanh(x[i]);
+    for (int r = 0; r < R; r++) {
+        acnn3_offsets(d, 1 + 2 * r, &wo, &bo);
+        conv3x3x3(n, C, C, d->w + wo, d->b + bo, x, h);
+        for (size_t i = 0; i < (size_t)C * m; i++) h[i] = tanh(h[i]);
+        acnn3_offsets(d, 2 + 2 * r, &wo, &bo);
+        conv3x3x3(n, C, C, d->w + wo, d->b + bo, h, t);
+        for (size_t i = 0; i < (size_t)C * m; i++) x[i] += tanh(t[i]);
+    }
+    acnn3_offsets(d, 1 + 2 * R, &wo, &bo);
+    conv3x3x3(n, C, 1, d->w + wo, d->b + bo, x, o);
+    double shift = 0.0;
+    if (d->mass_fix) {
+        double su = 0.0, so = 0.0;
+        for (size_t i = 0; i < m; i++) { su += u[i]; so += o[i]; }
+        shift = (su - so) / (double)m;
+    }
+    for (size_t i = 0; i < m; i++) {
+        double v = o[i] + shift;
+        if (d->limiter) v = v < d->lo ? d->lo : (v > d->hi ? d->hi : v);
+        out[i] = v;
+    }
+}
+
+void or_acnn3d_forward(const or_acnn* d, int n, int batch, const double* u, double* out) {
+    size_t m = (size_t)n * n * n;
+    int C = d->channels;
+    double* x = malloc(sizeof(double) * C * m);
+    double* h = malloc(sizeof(double) * C * m);
+    double* t = malloc(sizeof(double) * C * m);
+    double* o = malloc(sizeof(double) * m);
+    for (int p = 0; p < batch; p++) acnn3d_one(d, n, u + p * m, out + p * m, x, h, t, o);
+    free(x); free(h); free(t); free(o);
 }

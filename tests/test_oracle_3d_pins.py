@@ -74,3 +74,59 @@ def test_mass_conservation_and_maximum_principle():
     out0 = O.fine3d_propagate(p0, 20, u)
     assert np.abs(out0).max() <= 1.0
     assert abs(out0.mean() - u.mean()) > 1e-6  # the classic model does not conserve mass
+
+
+# ---------------------------------------------- ResBlock ACNN on the cube --
+def _acnn3(C, R, seed, mass_fix=0):
+    w, b = I.acnn3d_weights(C, R, seed=seed)
+    return w, b, O.Acnn3dSpec(C, R, w, b, mass_fix=mass_fix)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_acnn3d_on_a_field_constant_along_an_axis_is_the_2d_network(axis):
+    """A field constant along one axis stays so through every layer; the 3D
+    network then equals the (pinned) 2D network on the other two axes whose
+    3 x 3 weights are the 3 x 3 x 3 weights summed over that axis's tap index
+    (which fixes the orientation of the other two tap indices)."""
+    C, R, n = 4, 2, 8
+    w3, b3, spec3 = _acnn3(C, R, seed=1 + axis, mass_fix=1)
+    w2 = w3.reshape(-1, 3, 3, 3).sum(axis=1 + axis).ravel()
+    spec2 = O.AcnnSpec(C, R, w2, b3, mass_fix=1)
+    u2 = I.random_field(n, seed=2)
+    u3 = np.repeat(np.expand_dims(u2, axis), n, axis=axis)
+    out3 = O.acnn3d_forward(spec3, u3)
+    out2 = O.acnn_forward(spec2, u2)
+    assert np.abs(out3 - np.expand_dims(out2, axis)).max() < 1e-13
+
+
+def test_acnn3d_translation_and_mass():
+    C, R, n = 4, 1, 8
+    _, _, spec = _acnn3(C, R, seed=3, mass_fix=1)
+    u = rng(4).uniform(-0.9, 0.9, (n, n, n))
+    out = O.acnn3d_forward(spec, u)
+    sh = O.acnn3d_forward(spec, np.roll(u, (1, -2, 3), axis=(0, 1, 2)))
+    assert np.abs(sh - np.roll(out, (1, -2, 3), axis=(0, 1, 2))).max() < 1e-13
+    assert abs(out.mean() - u.mean()) < 1e-15
+
+
+def test_parareal3d_sweep_exactness_and_g_equals_f():
+    """Algorithm 2 on the cube: the k = 0 sweep is the 3D network's rollout;
+    at k = s the trajectory is the sequential 3D fine solve (Sec. 3.3); with
+    G = F the first increment is zero."""
+    C, R, n, s, c = 4, 1, 8, 3, 2
+    _, _, spec = _acnn3(C, R, seed=5, mass_fix=1)
+    p = O.params(n, eps=0.05, S=2.0, dt=2e-3, variant=1)
+    u0 = rng(6).uniform(-0.9, 0.9, (n, n, n))
+    u0 -= u0.mean()
+    r0 = O.parareal3d(p, spec, s, c, kmax=0, tol=0.0, u0=u0)
+    u = u0
+    for j in range(s):
+        u = O.acnn3d_forward(spec, u)
+        assert np.array_equal(r0["U"][j + 1], u)
+    r = O.parareal3d(p, spec, s, c, kmax=s, tol=0.0, u0=u0)
+    seq = [u0]
+    for j in range(s):
+        seq.append(O.fine3d_propagate(p, c, seq[-1]))
+    assert np.array_equal(r["U"], np.stack(seq))
+    rf = O.parareal3d(p, None, s, c, kmax=s, tol=1e-300, u0=u0, coarse_steps=c)
+    assert rf["res_l2"][0] == 0.0 and rf["iters"] == 1
