@@ -281,6 +281,69 @@ def test_conv_stack_matches_scipy(act):
     assert np.abs(O.cnn_forward(spec, u) - _stack_scipy(u, w, b, L, C, act)).max() < 1e-13
 
 
+def _bf16_library(x):
+    """Round to bfloat16 (nearest even) with torch's float32 -> bfloat16 cast;
+    exact for inputs that are float32 values."""
+    torch = pytest.importorskip("torch")
+    t = torch.tensor(np.asarray(x, dtype=np.float32))
+    return t.to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def test_bf16_rounding_matches_the_library_cast():
+    """The oracle's bf16 rounding equals torch's float32 -> bfloat16 cast on
+    float32 inputs of every scale, ties included."""
+    x = np.concatenate([rng(11).standard_normal(4000) * 10.0 ** rng(12).integers(-6, 6, 4000),
+                        1.0 + np.arange(0, 2 ** 9) * 2.0 ** -9])   # every tie pattern just above 1
+    x = x.astype(np.float32).astype(np.float64)
+    mine = np.array([O.round_bf16(v) for v in x])
+    assert np.array_equal(mine, _bf16_library(x))
+
+
+def _bf16_bits(x):
+    """Round float64 values to 8 significant bits, nearest even, on the bit
+    pattern: add half an ulp of the kept part (minus one, plus the kept LSB)
+    and clear the 45 dropped mantissa bits."""
+    bits = np.ascontiguousarray(x, dtype=np.float64).view(np.uint64)
+    lsb = (bits >> np.uint64(45)) & np.uint64(1)
+    bits = (bits + (np.uint64((1 << 44) - 1) + lsb)) & ~np.uint64((1 << 45) - 1)
+    return bits.view(np.float64)
+
+
+@pytest.mark.parametrize("act", [0, 1])
+def test_bf16_stack_matches_library_rounding(act):
+    """The bf16 mode of the conv stack (reading 5: input, weights and hidden
+    activations rounded to bf16; biases, sums and activations exact; the
+    residual adds the unrounded input) against the scipy stack with torch's
+    bf16 cast of the float32-valued input and weights and a bit-level
+    round-to-nearest-even of the float64 hidden activations."""
+    n, L, C = 8, 3, 4
+    w, b = I.cnn_weights(L, C, seed=13, sigma=0.3)
+    w = w.astype(np.float32).astype(np.float64)
+    b = b.astype(np.float32).astype(np.float64)
+    u = I.random_field(n, seed=14).astype(np.float32).astype(np.float64)
+    spec = O.CnnSpec(L, C, w, b, act=act, bf16=1)
+    dims = I.cnn_layer_dims(L, C)
+    wr = _bf16_library(w)
+    a = [_bf16_library(u)]
+    wo = bo = 0
+    for l, (ci, co) in enumerate(dims):
+        W = wr[wo:wo + ci * co * 9].reshape(co, ci, 3, 3)
+        out = []
+        for o in range(co):
+            z = np.full_like(u, b[bo + o])
+            for c in range(ci):
+                z = z + scipy.signal.correlate2d(a[c], W[o, c], mode="same", boundary="wrap")
+            out.append(z)
+        wo += ci * co * 9
+        bo += co
+        if l < L - 1:
+            out = [np.tanh(z) if act == 0 else _gelu(z) for z in out]
+            out = [_bf16_bits(z) for z in out]
+        a = out
+    ref = u + a[0]
+    assert np.abs(O.cnn_forward(spec, u) - ref).max() < 1e-13
+
+
 def test_conv_constant_input_closed_form():
     """A constant input stays constant through every layer: z = b + x * sum W."""
     n, L, C = 8, 3, 4
