@@ -16,13 +16,19 @@
  *     in Sec. 1; the spatial options are in Sec. 3.1).
  *   - Crank-Nicolson fine step with Picard iteration (the paper's own fine
  *     scheme, Sec. 3.1, Eq. (fully-discrete)): or_cn_step, or_cn_propagate.
- *   - Coarse propagator: 3x3 circular-padded conv stack (Sec. 3.2).
- *   - Parareal: Algorithm 2 / Sec. 3.3.
+ *   - Coarse propagator: 3x3 circular-padded conv stack (Sec. 3.2); the
+ *     paper's ResBlock ACNN / mACNN, its scheme-residual loss (Eq. loss_ACN),
+ *     Adam and the training loop of Algorithm 1 (Sec. 3.2).
+ *   - Parareal: Algorithm 2 / Sec. 3.3, with G composed m times per slice (the
+ *     remark after Algorithm 2).
+ *   - The fine step, the ResBlock ACNN (3x3x3) and Algorithm 2 on the periodic
+ *     cube (the 3D experiments of Sec. 4).
  *
  * Parity status: every function here is pinned by the not-gpu tests (naive DFT,
- * dense linear solve, closed forms, invariants, finite differences, brute force)
- * except the bf16-emulating conv mode, whose values are pinned only through the
- * float64 mode it reduces to when rounding is off.
+ * dense linear solve, closed forms, invariants, finite differences, brute force,
+ * library routines) except the straight-through backward of the bf16-emulating
+ * conv mode: parity unpinned there beyond the float64 mode it reduces to when
+ * rounding is off.
  */
 #include <complex.h>
 #include <math.h>
