@@ -499,3 +499,54 @@ def test_residual_definition():
     l2, mx = O.residual(Un, Uo)
     assert mx == 2.0
     assert abs(l2 - 2.0 / 5.0) < 1e-16
+
+
+def _linear_modes_problem(variant):
+    """Two small-amplitude Fourier modes (one along each axis) on a 16^2 grid.
+    At amplitude 1e-9 the cubic term u^3 is ~1e-27, far below float64
+    rounding of u, so one fine step multiplies each mode by the scalar
+    r(m) = (1 + S dt + dt) / D(m), D(m) = 1 + S dt + dt eps^2 (4/h^2) sin^2(pi m/N)
+    (Sec. 3.1 scheme with f(u) = u - u^3 linearised at 0; for the mass variant
+    beta = mean f(u) = -mean u^3 vanishes to the same order)."""
+    n, eps, S, dt = 16, 0.05, 2.0, 2e-3
+    p = O.params(n, eps=eps, S=S, dt=dt, variant=variant)
+    h = 1.0 / n
+    i = np.arange(n)
+    modes = ((1, 1.0e-9, 0), (5, 0.7e-9, 1))   # (wavenumber, amplitude, axis)
+    fields, ratios = [], []
+    for m, amp, axis in modes:
+        line = amp * np.cos(2 * np.pi * m * i / n)
+        fields.append(np.tile(line[:, None], (1, n)) if axis == 0 else np.tile(line[None, :], (n, 1)))
+        D = 1 + S * dt + dt * eps ** 2 * (4 / h ** 2) * math.sin(math.pi * m / n) ** 2
+        ratios.append((1 + S * dt + dt) / D)
+    return p, fields, ratios
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_parareal_linear_closed_form(variant):
+    """Parareal on a linear scalar problem has a closed form (Gander &
+    Vandewalle, SIAM J. Sci. Comput. 29 (2007)): with propagators F = rF,
+    G = rG and U^0_n = rG^n u0, the correction of Sec. 3.3 / Algorithm 2,
+    U^k_{n+1} = G U^k_n + F U^{k-1}_n - G U^{k-1}_n, gives
+        U^k_n = sum_{j=0..min(k,n)} C(n, j) (rF - rG)^j rG^(n-j) u0.
+    Here F is c fine steps and G = F over c' != c steps, both scalar on each
+    Fourier mode of a small-amplitude field.  Slices n > k (not yet exact)
+    pin the sign and the indices of the correction: a flipped (G_new - G_old)
+    changes the j = 1 term by ~1e-2 relative, the tolerance is 1e-12."""
+    p, fields, ratios = _linear_modes_problem(variant)
+    s, c, cg = 6, 5, 2
+    u0 = fields[0] + fields[1]
+    scale = max(np.abs(f).max() for f in fields)
+    for k in (1, 2, 3):
+        r = O.parareal(p, None, s, c, kmax=k, tol=0.0, u0=u0, coarse_steps=cg)
+        assert r["iters"] == k
+        for n_ in range(s + 1):
+            ref = np.zeros_like(u0)
+            for f, rr in zip(fields, ratios):
+                rF, rG = rr ** c, rr ** cg
+                ref += sum(math.comb(n_, j) * (rF - rG) ** j * rG ** (n_ - j)
+                           for j in range(min(k, n_) + 1)) * f
+            assert np.abs(r["U"][n_] - ref).max() < 1e-12 * scale, (k, n_)
+    # the closed form really separates the iterates from the fine solve at n > k
+    rF, rG = ratios[0] ** c, ratios[0] ** cg
+    assert abs(sum(math.comb(4, j) * (rF - rG) ** j * rG ** (4 - j) for j in range(2)) - rF ** 4) > 1e-6
