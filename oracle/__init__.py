@@ -49,7 +49,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
-                               "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"])
+                               "-shared", "-fPIC", "-pthread", _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -60,6 +60,8 @@ def lib():
         if _lib is None:
             L = C.CDLL(build())
             dp = C.POINTER(C.c_double)
+            L.or_set_threads.argtypes = [C.c_int]
+            L.or_get_threads.restype = C.c_int
             L.or_fft2d_ri.argtypes = [dp, C.c_int, C.c_int]
             L.or_dft2d_naive_ri.argtypes = [dp, dp, C.c_int, C.c_int]
             L.or_fine_step.argtypes = [C.POINTER(Params), dp, dp]
@@ -116,6 +118,24 @@ def lib():
                                         C.c_double, C.c_double, C.c_double, dp, dp, C.POINTER(C.c_int), dp]
             _lib = L
     return _lib
+
+
+class threads:
+    """Context manager: run the oracle's conv layers (split by output rows)
+    and Algorithm 2's independent fine solves on `t` threads.  Results are
+    identical for every t; only the wall time changes."""
+
+    def __init__(self, t: int):
+        self.t = int(t)
+
+    def __enter__(self):
+        self.old = lib().or_get_threads()
+        lib().or_set_threads(self.t)
+        return self
+
+    def __exit__(self, *exc):
+        lib().or_set_threads(self.old)
+        return False
 
 
 def _dp(a: np.ndarray):

@@ -24,6 +24,11 @@
  *   - The fine step, the ResBlock ACNN (3x3x3) and Algorithm 2 on the periodic
  *     cube (the 3D experiments of Sec. 4).
  *
+ * Threads: or_set_threads(t) lets conv3x3 split its output rows, and
+ * Algorithm 2 its independent fine solves, over t POSIX threads.  Each output
+ * value is computed by exactly the same loop as with one thread, so results
+ * do not depend on t (this only shortens the wall time of large cases).
+ *
  * Parity status: every function here is pinned by the not-gpu tests (naive DFT,
  * dense linear solve, closed forms, invariants, finite differences, brute force,
  * library routines) except the straight-through backward of the bf16-emulating
@@ -32,6 +37,7 @@
  */
 #include <complex.h>
 #include <math.h>
+#include <pthread.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -60,6 +66,42 @@ typedef struct {
 } or_cnn;
 
 static const double PI = 3.14159265358979323846264338327950288;
+
+/* ------------------------------------------------------------ threads ---- */
+static int g_threads = 1;
+
+void or_set_threads(int t) { g_threads = t < 1 ? 1 : (t > 256 ? 256 : t); }
+int or_get_threads(void) { return g_threads; }
+
+typedef struct {
+    void (*fn)(void* ctx, long lo, long hi);
+    void* ctx;
+    long lo, hi;
+} or_task;
+
+static void* or_task_run(void* a) {
+    or_task* t = (or_task*)a;
+    t->fn(t->ctx, t->lo, t->hi);
+    return NULL;
+}
+
+/* Run fn(ctx, lo, hi) over [0, count) split into g_threads contiguous ranges. */
+static void or_parallel_for(long count, void (*fn)(void*, long, long), void* ctx) {
+    int t = g_threads;
+    if (t > count) t = (int)count;
+    if (t <= 1) { if (count > 0) fn(ctx, 0, count); return; }
+    pthread_t th[256];
+    or_task task[256];
+    int started[256];
+    for (int i = 0; i < t; i++) {
+        task[i].fn = fn; task[i].ctx = ctx;
+        task[i].lo = count * i / t; task[i].hi = count * (i + 1) / t;
+        started[i] = pthread_create(&th[i], NULL, or_task_run, &task[i]) == 0;
+        if (!started[i]) or_task_run(&task[i]);
+    }
+    for (int i = 0; i < t; i++)
+        if (started[i]) pthread_join(th[i], NULL);
+}
 
 /* ------------------------------------------------------------------ FFT -- */
 /* Recursive radix-2 decimation-in-time Cooley-Tukey transform,
@@ -359,20 +401,31 @@ static double act_grad(int act, double x) {
 
 /* One 3x3 cross-correlation with circular padding 1:
  * out[o][i][j] = b[o] + sum_{c,a,e} W[o][c][a][e] in[c][(i+a-1) mod n][(j+e-1) mod n]. */
+typedef struct { int n, cin, cout; const double *W, *b, *in; double* out; } conv3x3_ctx;
+
+/* Output rows r = o * n + i in [lo, hi). */
+static void conv3x3_rows(void* vc, long lo, long hi) {
+    const conv3x3_ctx* q = (const conv3x3_ctx*)vc;
+    const int n = q->n, cin = q->cin;
+    for (long r = lo; r < hi; r++) {
+        const int o = (int)(r / n), i = (int)(r % n);
+        for (int j = 0; j < n; j++) {
+            double acc = q->b[o];
+            for (int c = 0; c < cin; c++)
+                for (int a = 0; a < 3; a++)
+                    for (int e = 0; e < 3; e++) {
+                        int ii = (i + a - 1 + n) % n, jj = (j + e - 1 + n) % n;
+                        acc += q->W[((o * cin + c) * 3 + a) * 3 + e] * q->in[((size_t)c * n + ii) * n + jj];
+                    }
+            q->out[((size_t)o * n + i) * n + j] = acc;
+        }
+    }
+}
+
 static void conv3x3(int n, int cin, int cout, const double* W, const double* b,
                     const double* in, double* out) {
-    for (int o = 0; o < cout; o++)
-        for (int i = 0; i < n; i++)
-            for (int j = 0; j < n; j++) {
-                double acc = b[o];
-                for (int c = 0; c < cin; c++)
-                    for (int a = 0; a < 3; a++)
-                        for (int e = 0; e < 3; e++) {
-                            int ii = (i + a - 1 + n) % n, jj = (j + e - 1 + n) % n;
-                            acc += W[((o * cin + c) * 3 + a) * 3 + e] * in[((size_t)c * n + ii) * n + jj];
-                        }
-                out[((size_t)o * n + i) * n + j] = acc;
-            }
+    conv3x3_ctx q = {n, cin, cout, W, b, in, out};
+    or_parallel_for((long)cout * n, conv3x3_rows, &q);
 }
 
 static void layer_dims(const or_cnn* d, int l, int* cin, int* cout) {
@@ -587,6 +640,17 @@ static void or_coarse_eval(const or_params* p, const or_coarse* g, int repeat, c
     }
 }
 
+typedef struct { const or_params* p; int dim, c, first; size_t m; const double* in; double* out; } fine_slices_ctx;
+
+/* Fine solves of slices first + [lo, hi) (each one independent). */
+static void fine_slices_run(void* vc, long lo, long hi) {
+    const fine_slices_ctx* q = (const fine_slices_ctx*)vc;
+    for (long t = lo; t < hi; t++) {
+        const size_t j = (size_t)(q->first + t);
+        or_fine_any(q->p, q->dim, q->c, q->in + j * q->m, q->out + j * q->m);
+    }
+}
+
 static long or_parareal_g(const or_params* p, const or_coarse* g, int repeat, int s, int c, int kmax, double tol,
                           int literal, const double* u0, double* U, double* res_l2, double* res_max, int* iters);
 
@@ -644,7 +708,8 @@ static long or_parareal_g(const or_params* p, const or_coarse* gc, int repeat, i
     for (k = 1; k <= kmax && k <= s; k++) {
         memcpy(Uold, U, sizeof(double) * m * (s + 1));
         /* fine solves, independent over n = k-1 .. s-1 */
-        for (int j = k - 1; j < s; j++) or_fine_any(p, gc->dim, c, Uold + j * m, Ff + j * m);
+        fine_slices_ctx fq = {p, gc->dim, c, k - 1, m, Uold, Ff};
+        or_parallel_for(s - (k - 1), fine_slices_run, &fq);
         /* sequential correction */
         for (int j = k - 1; j < s; j++) {
             if (literal) {

@@ -128,3 +128,31 @@ def test_gelu_activation_error_bound():
     assert np.all(exact_hit | (err <= ulp * 1.01))
     # one-step flips are rare (about 1% of this ramp, measured)
     assert np.mean(exact_hit) > 0.98
+
+
+def test_cnn_bf16_mass_shift_trained_256():
+    """The coarse net exactly as the benchmark runs it: the committed trained
+    1 -> 32 x 6 GELU stack, bf16 with float32 accumulation and the mACNN mass
+    shift (Sec. 3.2), on 256^2 zero-mean fields.  Against the oracle's
+    bf16-emulating mode with the same shift: the tolerance of the bf16 tests
+    above (bf16 rounding flips bounded by 2e-2 of the stack's contribution,
+    median at float32 level); the shift keeps the output's mean equal to the
+    input's, up to float32 summation over 65536 values."""
+    import os
+    W = I.MASS_F32_256
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    z = np.load(os.path.join(root, "paper_2510_07672_gb300", "weights", "mass256_c32l6_gelu.npz"))
+    w32, b32 = z["w"].astype(np.float32), z["b"].astype(np.float32)
+    net = G.CoarseNet(W.layers, W.channels, w32, b32, act=W.act, precision=G.AC_F32, mass_fix=1)
+    u = W.ics()[:2].astype(np.float32)
+    got = G.cnn_coarse_step(net, torch.tensor(u, device="cuda")).double().cpu().numpy()
+    spec = O.CnnSpec(W.layers, W.channels, w32.astype(np.float64), b32.astype(np.float64), act=W.act,
+                     mass_fix=1, bf16=1)
+    with O.threads(os.cpu_count() or 1):
+        ref = O.cnn_forward(spec, u.astype(np.float64))
+    err = np.abs(got - ref)
+    scale = max(np.abs(ref - u).max(), 1e-3)
+    assert err.max() < 2e-2 * scale + 1e-6
+    assert np.median(err) < 1e-3 * scale + 1e-7
+    for p in range(2):
+        assert abs(got[p].mean() - u[p].astype(np.float64).mean()) < 1e-6

@@ -203,3 +203,47 @@ def test_full_size_mass256_in_the_bench_configuration():
     for p, j in ((0, 0), (7, 13), (15, 31)):
         ref = O.fine_propagate(p_o, W.steps, U[p, j].double().cpu().numpy())
         assert np.abs(U[p, j + 1].double().cpu().numpy() - ref).max() < 2e-5 * np.sqrt(W.steps)
+
+
+def test_full_size_unconverged_iterates_match_oracle():
+    """Unconverged Parareal iterates at the benchmark's full size (256^2,
+    32 slices x 200 steps, mass-conserving, the committed trained bf16 G with
+    the mass shift) for one problem, at k = 1 and k = 2, against the oracle's
+    Algorithm 2 run to the same k from the same initial field (float64 fine
+    solves, conv with the same bf16 roundings).  Every slice n > k carries
+    the correction F(U^{k-1}_n) + G(U^k_n) - G(U^{k-1}_n) (Sec. 3.3), so a
+    wrong sign or slice index fails by O(|F - G|) ~ 1e-2.  The bound allows
+    the float32 fine error (2e-5 sqrt(c) per slice) and bf16 rounding flips
+    of G (up to 2e-2 of the stack's contribution per application) carried
+    along the sweep.  Measured on GB300: max-abs 1.6e-3, relative L2 6.4e-4
+    and 7.4e-4, increments within 1.5%; the bounds below leave a factor 3."""
+    import os
+    W = I.MASS_F32_256
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    z = np.load(os.path.join(root, "paper_2510_07672_gb300", "weights", "mass256_c32l6_gelu.npz"))
+    w32, b32 = z["w"].astype(np.float32), z["b"].astype(np.float32)
+    net = G.CoarseNet(W.layers, W.channels, w32, b32, act=W.act, precision=G.AC_F32, mass_fix=W.mass_fix)
+    fp = G.FineParams(W.n, W.eps, W.S, W.dt, variant=W.variant, precision=G.AC_F32)
+    u0 = W.ics()[:1].astype(np.float32)
+    pr = G.Parareal(fp, net, torch.tensor(u0, device="cuda"), W.slices, W.steps)
+    pr.iterate()  # k = 0
+    got, incs = {}, {}
+    for k in (1, 2):
+        l2, _ = pr.iterate()
+        incs[k] = l2[0]
+        got[k] = pr.trajectory()[0].double().cpu().numpy()
+    spec = O.CnnSpec(W.layers, W.channels, w32.astype(np.float64), b32.astype(np.float64), act=W.act,
+                     mass_fix=W.mass_fix, bf16=1)
+    p_o = O.params(W.n, W.eps, W.S, W.dt, W.variant)
+    with O.threads(os.cpu_count() or 1):
+        for k in (1, 2):
+            ref = O.parareal(p_o, spec, W.slices, W.steps, kmax=k, tol=0.0, u0=u0[0].astype(np.float64))
+            assert ref["iters"] == k
+            err = np.abs(got[k] - ref["U"]).max(axis=(1, 2))
+            rel = np.linalg.norm(got[k] - ref["U"]) / np.linalg.norm(ref["U"])
+            print(f"k={k}: max-abs per slice (first, mid, last) {err[1]:.2e} {err[16]:.2e} {err[-1]:.2e}; "
+                  f"max {err.max():.2e}; rel-L2 {rel:.2e}; increment gpu {incs[k]:.6e} oracle {ref['res_l2'][-1]:.6e}")
+            assert err[: k + 1].max() < 2e-5 * np.sqrt(W.steps * k)   # the exact prefix: fine solves only
+            assert err.max() < 5e-3
+            assert rel < 2e-3
+            assert abs(incs[k] - ref["res_l2"][-1]) < 5e-2 * ref["res_l2"][-1]

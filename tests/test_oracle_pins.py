@@ -550,3 +550,15 @@ def test_parareal_linear_closed_form(variant):
     # the closed form really separates the iterates from the fine solve at n > k
     rF, rG = ratios[0] ** c, ratios[0] ** cg
     assert abs(sum(math.comb(4, j) * (rF - rG) ** j * rG ** (4 - j) for j in range(2)) - rF ** 4) > 1e-6
+
+
+def test_oracle_threads_do_not_change_results():
+    """The oracle's optional threads split conv output rows and independent
+    fine solves only, so every value is bit-identical for any thread count."""
+    p, G, n, s, c, u0 = _small_problem(1)
+    a = O.parareal(p, G, s, c, kmax=3, tol=0.0, u0=u0)
+    with O.threads(3):
+        b = O.parareal(p, G, s, c, kmax=3, tol=0.0, u0=u0)
+        y = O.cnn_forward(G, u0)
+    assert np.array_equal(a["U"], b["U"]) and np.array_equal(a["res_l2"], b["res_l2"])
+    assert np.array_equal(y, O.cnn_forward(G, u0))
