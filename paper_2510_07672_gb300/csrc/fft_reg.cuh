@@ -63,6 +63,44 @@ __device__ __forceinline__ void twiddle32(int m, T& vr, T& vi) {
     vr = r;
 }
 
+// Radix-2 butterfly (u, v) -> (u + w v, u - w v) with w = exp(SIGN 2 pi i m / 32),
+// m a compile-time constant.  Quarter turns are swaps.  A general twiddle is
+// folded into the butterfly with the larger of |cos|, |sin| factored out
+// (the fused multiply-add form of Linzer and Feig, IBM J. Res. Dev. 37
+// (1993)): with q = sin/cos, w v = cos (v_r - q v_i, v_i + q v_r), and the two
+// outputs are u +- cos (...) -- six fused multiply-adds instead of two
+// multiplies, two multiply-adds and four adds.
+template <typename T, int SIGN>
+__device__ __forceinline__ void butterfly32(int m, T& ur, T& ui, T& vr, T& vi) {
+    if (m == 0 || m == 8) {
+        twiddle32<T, SIGN>(m, vr, vi);
+        const T ar = ur, ai = ui;
+        ur = ar + vr;
+        ui = ai + vi;
+        vr = ar - vr;
+        vi = ai - vi;
+        return;
+    }
+    const double cd = cos32(m), sd = double(SIGN) * sin32(m);
+    T a, b, f;
+    if ((cd < 0 ? -cd : cd) >= (sd < 0 ? -sd : sd)) {
+        const T q = T(sd / cd);
+        f = T(cd);
+        a = fma(-q, vi, vr);  // (c v_r - s v_i) / c
+        b = fma(q, vr, vi);   // (s v_r + c v_i) / c
+    } else {
+        const T q = T(cd / sd);
+        f = T(sd);
+        a = fma(q, vr, -vi);  // (c v_r - s v_i) / s
+        b = fma(q, vi, vr);   // (s v_r + c v_i) / s
+    }
+    const T ar = ur, ai = ui;
+    ur = fma(f, a, ar);
+    ui = fma(f, b, ai);
+    vr = fma(-f, a, ar);
+    vi = fma(-f, b, ai);
+}
+
 // One butterfly stage of span LEN, then the next (template recursion keeps
 // every index a compile-time constant so the arrays stay in registers).
 template <typename T, int M, int SIGN, int LEN>
@@ -71,15 +109,9 @@ __device__ __forceinline__ void dit_stages(T (&re)[M], T (&im)[M]) {
 #pragma unroll
         for (int i = 0; i < M; i += LEN) {
 #pragma unroll
-            for (int k = 0; k < LEN / 2; ++k) {
-                T vr = re[i + k + LEN / 2], vi = im[i + k + LEN / 2];
-                twiddle32<T, SIGN>(k * (32 / LEN), vr, vi);
-                const T ur = re[i + k], ui = im[i + k];
-                re[i + k] = ur + vr;
-                im[i + k] = ui + vi;
-                re[i + k + LEN / 2] = ur - vr;
-                im[i + k + LEN / 2] = ui - vi;
-            }
+            for (int k = 0; k < LEN / 2; ++k)
+                butterfly32<T, SIGN>(k * (32 / LEN), re[i + k], im[i + k], re[i + k + LEN / 2],
+                                     im[i + k + LEN / 2]);
         }
         dit_stages<T, M, SIGN, 2 * LEN>(re, im);
     }

@@ -31,10 +31,43 @@
 // once when it is stored.
 #include "common.cuh"
 #include "fft_reg.cuh"
+#include "tc_ptx.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace acpr {
+
+namespace {
+// Set by a fine kernel whose bounded wait on its exchange mbarrier gave up
+// (fine_check_status() reports and clears it).
+__device__ int g_fine_timeout = 0;
+constexpr long long kFineSpin = 20000000LL;  // polls (each try_wait suspends briefly): seconds
+}
+
+// Shared::cluster address of `local_addr` (a shared::cta address) in CTA `rank`.
+__device__ __forceinline__ uint32_t cluster_map(uint32_t local_addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
+    return r;
+}
+
+// Bulk copy of `bytes` (multiple of 16, 16-byte aligned ends) from this CTA's
+// shared memory to a peer's, completing `bytes` transaction bytes on the
+// peer's mbarrier.
+__device__ __forceinline__ void bulk_s2peer(uint32_t dst_cluster, uint32_t src_cta, uint32_t bytes,
+                                            uint32_t mbar_cluster) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst_cluster),
+        "r"(src_cta), "r"(bytes), "r"(mbar_cluster)
+        : "memory");
+}
+
+// Make this thread's generic-proxy shared-memory writes visible to the async
+// proxy (the bulk copies issued after the next barrier).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 
 struct FineArgs {
     const void* in;
@@ -94,7 +127,13 @@ struct FineShape {
     static constexpr int TP = transpose_pitch(L, B);
     static constexpr size_t BUFT = sizeof(vec2_t<T>) * size_t(N) * TP;
     static constexpr size_t BUFX = sizeof(vec2_t<T>) * size_t(L) * XP;
-    static constexpr size_t SMEM = 2 * BUFT + BUFX + sizeof(vec2_t<T>) * N + sizeof(T) * N + 4 * sizeof(double);
+    static constexpr size_t SMEM = 2 * BUFT + BUFX + sizeof(vec2_t<T>) * N + sizeof(T) * N + 4 * sizeof(double) +
+                                   2 * sizeof(uint64_t);
+    // asynchronous exchange: a peer's share of a transpose is L positions of
+    // TP elements per half (2 bulk copies per peer), 16-byte aligned
+    static constexpr uint32_t RUN_BYTES = uint32_t(sizeof(vec2_t<T>) * L * TP);
+    static constexpr bool ASYNC_OK = (RUN_BYTES % 16 == 0) && ((sizeof(vec2_t<T>) * HALF * TP) % 16 == 0) &&
+                                     (BUFT % 16 == 0);
     static_assert(R >= 2 && R % 2 == 0, "need at least two rows per CTA");
     static_assert(B <= 16 && TP >= L, "transpose layout");
 };
@@ -123,7 +162,15 @@ __device__ __forceinline__ V* peer_ptr(V* local, int rank) {
 }
 
 // MINB: CTAs per SM the register allocation must allow (occupancy target).
-template <typename T, int N, int P, int A, int B, int MINB>
+// ASYNC (P > 1, no adjoint mode): the two transposes of a step travel as bulk
+// shared-memory copies to the peers, completing on one mbarrier per receive
+// buffer, instead of direct DSMEM stores ordered by two cluster barriers.  A
+// CTA stages the data for peer d in its own receive buffer's region for data
+// *from* d (that region is next written by d only after d has received this
+// CTA's data, so it is free), and the element for itself directly in the
+// other buffer.  No cluster-wide barrier and no release fence in the step
+// loop: a CTA waits only for the bytes it receives.
+template <typename T, int N, int P, int A, int B, int MINB, bool ASYNC = false>
 __global__ void __launch_bounds__(FineShape<T, N, P, A, B>::THREADS, MINB)
 fine_field_kernel(FineArgs args) {
     using Sh = FineShape<T, N, P, A, B>;
@@ -136,6 +183,9 @@ fine_field_kernel(FineArgs args) {
     V* tw = bufX + L * XP;                             // line_fft twiddle table
     T* lam = reinterpret_cast<T*>(tw + N);             // dt eps^2 mu_k
     double* part = reinterpret_cast<double*>(lam + N); // mass partial, adjoint mean
+    uint64_t* xbar = reinterpret_cast<uint64_t*>(part + 4);  // [0]: bufC received, [1]: bufR received
+    static_assert(!ASYNC || (P > 1 && Sh::ASYNC_OK), "asynchronous exchange layout");
+    constexpr uint32_t XBYTES = uint32_t(P - 1) * 2u * Sh::RUN_BYTES;  // bytes received per transpose
 
     const int tid = threadIdx.x;
     // the B lanes of a line are consecutive lanes of one warp, so the line
@@ -170,6 +220,19 @@ fine_field_kernel(FineArgs args) {
         tw[k].y = T(sn);
         const double s = sinpi(double(k) / N);
         lam[k] = T(args.lam_scale * s * s);
+    }
+    if constexpr (ASYNC) {
+        if (tid == 0) {
+            tc::mbar_init(&xbar[0], 1);
+            tc::mbar_init(&xbar[1], 1);
+            tc::fence_mbar_init();
+            if (nsteps > 0) {
+                tc::mbar_arrive_expect_tx(&xbar[0], XBYTES);
+                tc::mbar_arrive_expect_tx(&xbar[1], XBYTES);
+            }
+        }
+        // every peer's barriers exist before anyone sends
+        cluster_barrier<P>();
     }
 
     // load rows [rank R, rank R + R): line l holds rows l (real) and l + L (imag)
@@ -224,6 +287,33 @@ fine_field_kernel(FineArgs args) {
     // which only the line's lanes (one warp) touch: warp barriers order it.
     // bufR and bufC are only transpose targets (and the load/store staging),
     // ordered by the two cluster barriers.
+    // Asynchronous exchange (ASYNC): `src` holds, at the region of each peer d
+    // (positions h HALF + d L .. + L, h = 0, 1), the data for d; it goes to
+    // d's `dst` at the region of this CTA, completing on d's barrier `bar`.
+    bool xabort = false;  // a bounded wait gave up: skip later waits
+    auto exchange_send = [&](V* src, V* dst, uint64_t* bar) {
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid < 2 * (P - 1)) {
+            const int dd = tid >> 1, h = tid & 1;
+            const int d = dd < rank ? dd : dd + 1;
+            const uint32_t s_addr = tc::smem_u32(src + (h * HALF + d * L) * TP);
+            const uint32_t d_addr = cluster_map(tc::smem_u32(dst + (h * HALF + rank * L) * TP), uint32_t(d));
+            bulk_s2peer(d_addr, s_addr, Sh::RUN_BYTES, cluster_map(tc::smem_u32(bar), uint32_t(d)));
+        }
+    };
+    auto exchange_wait = [&](int b, int stp) {
+        bool ok = xabort;
+        for (long long i = 0; !ok && i < kFineSpin; ++i) ok = tc::mbar_try_wait(&xbar[b], uint32_t(stp & 1));
+        if (!ok) {
+            xabort = true;
+            atomicExch(&g_fine_timeout, 1);
+        }
+        // arm the next phase (its bytes come only after this CTA's next send)
+        if (tid == 0 && stp + 1 < nsteps) tc::mbar_arrive_expect_tx(&xbar[b], XBYTES);
+    };
+    (void)exchange_send;
+    (void)exchange_wait;
     for (int step = 0; step < nsteps; ++step) {
         if (!args.adjoint) {
             // pointwise right-hand side on both rows of the line
@@ -236,15 +326,30 @@ fine_field_kernel(FineArgs args) {
         }
         line_fft<T, N, A, B, -1>(x, tw, myX, j, WMASK);
         // row spectra Z_p[k] -> column min(k, N - k) (k = 0, N/2 -> column 0)
+        if constexpr (ASYNC) {
+            __syncthreads();  // every rebuild read of bufR (now the staging area) is done
 #pragma unroll
-        for (int t = 0; t < A; ++t) {
-            const int k = j + B * t;
-            const int c = (k == HALF) ? 0 : (k < HALF ? k : N - k);
-            const int slot = (k == 0 || k < HALF) ? 0 : 1;
-            V* dst = peer_ptr<P>(bufC, c / L);
-            dst[(slot * HALF + pair) * TP + c % L] = x[t];
+            for (int t = 0; t < A; ++t) {
+                const int k = j + B * t;
+                const int c = (k == HALF) ? 0 : (k < HALF ? k : N - k);
+                const int slot = (k == 0 || k < HALF) ? 0 : 1;
+                const int d = c / L;
+                if (d == rank) bufC[(slot * HALF + pair) * TP + c % L] = x[t];
+                else bufR[(slot * HALF + d * L + line) * TP + c % L] = x[t];
+            }
+            exchange_send(bufR, bufC, &xbar[0]);
+            exchange_wait(0, step);
+        } else {
+#pragma unroll
+            for (int t = 0; t < A; ++t) {
+                const int k = j + B * t;
+                const int c = (k == HALF) ? 0 : (k < HALF ? k : N - k);
+                const int slot = (k == 0 || k < HALF) ? 0 : 1;
+                V* dst = peer_ptr<P>(bufC, c / L);
+                dst[(slot * HALF + pair) * TP + c % L] = x[t];
+            }
+            cluster_barrier<P>();
         }
-        cluster_barrier<P>();
         // split each row pair into its two rows' half spectra
 #pragma unroll
         for (int t = 0; t < A; ++t) {
@@ -316,14 +421,28 @@ fine_field_kernel(FineArgs args) {
         }
         line_fft<T, N, A, B, +1>(x, tw, myX, j, WMASK);
         // column values V_r[c] -> owner of row r, slot (row role) and column c
+        if constexpr (ASYNC) {
+            __syncthreads();  // every split read of bufC (now the staging area) is done
 #pragma unroll
-        for (int t = 0; t < A; ++t) {
-            const int r = j + B * t;
-            const int lr = r % R;
-            V* dst = peer_ptr<P>(bufR, r / R);
-            dst[((lr / L) * HALF + col) * TP + lr % L] = x[t];
+            for (int t = 0; t < A; ++t) {
+                const int r = j + B * t;
+                const int lr = r % R;
+                const int d = r / R;
+                if (d == rank) bufR[((lr / L) * HALF + col) * TP + lr % L] = x[t];
+                else bufC[((lr / L) * HALF + d * L + line) * TP + lr % L] = x[t];
+            }
+            exchange_send(bufC, bufR, &xbar[1]);
+            exchange_wait(1, step);
+        } else {
+#pragma unroll
+            for (int t = 0; t < A; ++t) {
+                const int r = j + B * t;
+                const int lr = r % R;
+                V* dst = peer_ptr<P>(bufR, r / R);
+                dst[((lr / L) * HALF + col) * TP + lr % L] = x[t];
+            }
+            cluster_barrier<P>();
         }
-        cluster_barrier<P>();
         // rebuild each pair's full row spectrum from the half spectra
 #pragma unroll
         for (int t = 0; t < A; ++t) {
@@ -375,6 +494,11 @@ fine_field_kernel(FineArgs args) {
     }
 
     // store rows, coalesced, through bufR
+    if constexpr (ASYNC) {
+        // every CTA has received all its bytes, so no copy of this cluster is
+        // still reading or writing shared memory when its CTAs exit
+        cluster_barrier<P>();
+    }
     __syncthreads();
 #pragma unroll
     for (int t = 0; t < A; ++t) myR[(j + B * t) * TP] = x[t];
@@ -386,10 +510,10 @@ fine_field_kernel(FineArgs args) {
 }
 
 // ---------------------------------------------------------------- launch --
-template <typename T, int N, int P, int A, int B, int MINB>
+template <typename T, int N, int P, int A, int B, int MINB, bool ASYNC = false>
 static int launch_fine(const FineArgs& args, cudaStream_t stream) {
     using Sh = FineShape<T, N, P, A, B>;
-    auto kern = fine_field_kernel<T, N, P, A, B, MINB>;
+    auto kern = fine_field_kernel<T, N, P, A, B, MINB, ASYNC>;
     static bool configured = false;  // per instantiation, once per process
     if (!configured) {
         ACPR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::SMEM)));
@@ -420,9 +544,12 @@ static int launch_fine(const FineArgs& args, cudaStream_t stream) {
 struct FineVariant {
     const char* name;
     int (*launch)(const FineArgs&, cudaStream_t);
+    bool async;  // asynchronous exchange: no adjoint mode
 };
 
-#define ACPR_FV(T, N, P, A, B, M) {"P" #P "_A" #A "_B" #B "_occ" #M, &launch_fine<T, N, P, A, B, M>}
+#define ACPR_FV(T, N, P, A, B, M) {"P" #P "_A" #A "_B" #B "_occ" #M, &launch_fine<T, N, P, A, B, M>, false}
+#define ACPR_FVA(T, N, P, A, B, M) \
+    {"P" #P "_A" #A "_B" #B "_occ" #M "_async", &launch_fine<T, N, P, A, B, M, true>, true}
 
 template <typename T>
 static const FineVariant* fine_variants(int n, int* count) {
@@ -432,22 +559,30 @@ static const FineVariant* fine_variants(int n, int* count) {
     static const FineVariant v64[] = {ACPR_FV(T, 64, 1, 8, 8, 2), ACPR_FV(T, 64, 2, 8, 8, 3)};
     if constexpr (sizeof(T) == 4) {
         static const FineVariant v128[] = {ACPR_FV(T, 128, 2, 16, 8, 2), ACPR_FV(T, 128, 4, 16, 8, 3),
-                                           ACPR_FV(T, 128, 1, 16, 8, 1)};
-        static const FineVariant v256[] = {ACPR_FV(T, 256, 8, 16, 16, 2), ACPR_FV(T, 256, 4, 16, 16, 1),
-                                           ACPR_FV(T, 256, 16, 16, 16, 3), ACPR_FV(T, 256, 8, 16, 16, 1)};
-        static const FineVariant v512[] = {ACPR_FV(T, 512, 16, 32, 16, 1)};
+                                           ACPR_FV(T, 128, 1, 16, 8, 1), ACPR_FVA(T, 128, 4, 16, 8, 3),
+                                           ACPR_FVA(T, 128, 2, 16, 8, 2)};
+        // entry 0 (asynchronous exchange, clusters of 8) measured fastest on
+        // large batches (512 fields: 2.57 ms vs 2.97 ms for 20 steps), entry 1
+        // (clusters of 16) on batches that fill at most one wave of SMs
+        static const FineVariant v256[] = {ACPR_FVA(T, 256, 8, 16, 16, 2), ACPR_FVA(T, 256, 16, 16, 16, 3),
+                                           ACPR_FVA(T, 256, 4, 16, 16, 1), ACPR_FV(T, 256, 8, 16, 16, 2),
+                                           ACPR_FV(T, 256, 4, 16, 16, 1), ACPR_FV(T, 256, 16, 16, 16, 3),
+                                           ACPR_FV(T, 256, 8, 16, 16, 1)};
+        static const FineVariant v512[] = {ACPR_FV(T, 512, 16, 32, 16, 1), ACPR_FVA(T, 512, 16, 32, 16, 1)};
         switch (n) {
-            case 128: *count = 3; return v128;
-            case 256: *count = 4; return v256;
-            case 512: *count = 1; return v512;
+            case 128: *count = 5; return v128;
+            case 256: *count = 7; return v256;
+            case 512: *count = 2; return v512;
             default: break;
         }
     } else {
-        static const FineVariant v128[] = {ACPR_FV(T, 128, 4, 16, 8, 1), ACPR_FV(T, 128, 2, 16, 8, 1)};
-        static const FineVariant v256[] = {ACPR_FV(T, 256, 8, 16, 16, 1), ACPR_FV(T, 256, 16, 16, 16, 2)};
+        static const FineVariant v128[] = {ACPR_FV(T, 128, 4, 16, 8, 1), ACPR_FV(T, 128, 2, 16, 8, 1),
+                                           ACPR_FVA(T, 128, 4, 16, 8, 1)};
+        static const FineVariant v256[] = {ACPR_FV(T, 256, 8, 16, 16, 1), ACPR_FV(T, 256, 16, 16, 16, 2),
+                                           ACPR_FVA(T, 256, 8, 16, 16, 1)};
         switch (n) {
-            case 128: *count = 2; return v128;
-            case 256: *count = 2; return v256;
+            case 128: *count = 3; return v128;
+            case 256: *count = 3; return v256;
             default: break;
         }
     }
@@ -460,9 +595,22 @@ static const FineVariant* fine_variants(int n, int* count) {
     }
 }
 #undef ACPR_FV
+#undef ACPR_FVA
 
 namespace {
-int g_variant[2][11] = {};  // [precision][log2 n]: chosen launch shape
+int g_variant[2][11] = {};      // [precision][log2 n]: chosen launch shape
+bool g_variant_set[2][11] = {};  // chosen explicitly (ac_fine_set_variant / autotune)
+}
+
+static int num_sms_fine() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 1;
+    }
+    return sms;
 }
 
 static const FineVariant* pick_variant(int n, int precision, int* count) {
@@ -478,9 +626,39 @@ static int dispatch_fine(int n, const FineArgs& args, cudaStream_t stream) {
         set_error("ac_fine: n=%d not built for %s", n, sizeof(T) == 8 ? "AC_F64" : "AC_F32");
         return AC_ERR_UNSUPPORTED;
     }
-    int idx = g_variant[sizeof(T) == 8 ? AC_F64 : AC_F32][ilog2(n)];
+    const int pr = sizeof(T) == 8 ? AC_F64 : AC_F32;
+    int idx = g_variant[pr][ilog2(n)];
     if (idx < 0 || idx >= count) idx = 0;
+    if (!g_variant_set[pr][ilog2(n)] && sizeof(T) == 4 && n == 256 && args.num_fields * 8 <= num_sms_fine())
+        idx = 1;  // a batch that fills one wave of 8-CTA clusters: 16-CTA clusters use more SMs
+    // the adjoint's mean broadcast is ordered by cluster barriers: take the
+    // first barrier-exchange shape
+    if (args.adjoint && v[idx].async) {
+        idx = 0;
+        while (idx < count && v[idx].async) ++idx;
+        if (idx == count) {
+            set_error("ac_fine: no barrier-exchange shape for the adjoint at n=%d", n);
+            return AC_ERR_UNSUPPORTED;
+        }
+    }
     return v[idx].launch(args, stream);
+}
+
+// Device-side timeout flag of the fine kernels' bounded exchange waits:
+// AC_ERR_TIMEOUT (and the flag cleared) if one gave up since the last call.
+// Synchronises the stream.
+int fine_check_status(cudaStream_t st) {
+    int flag = 0;
+    ACPR_CUDA(cudaMemcpyFromSymbolAsync(&flag, g_fine_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+    ACPR_CUDA(cudaStreamSynchronize(st));
+    if (flag) {
+        const int zero = 0;
+        ACPR_CUDA(cudaMemcpyToSymbolAsync(g_fine_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st));
+        ACPR_CUDA(cudaStreamSynchronize(st));
+        set_error("fine step: a bounded exchange wait gave up");
+        return AC_ERR_TIMEOUT;
+    }
+    return AC_OK;
 }
 
 bool fine_big_supported(int n, int precision);
@@ -509,9 +687,16 @@ static int check_params(const ac_params* p) {
     return AC_OK;
 }
 
+size_t fine_big_workspace_bytes(int n, int fields);
+
 int fine_run(const ac_params* p, int groups, int per_group, int steps, const void* in, long long in_gs,
              long long in_off, void* out, long long out_gs, long long out_off, const int* map, int adjoint,
-             const void* states, void* traj, cudaStream_t stream) {
+             const void* states, void* traj, cudaStream_t stream, void* big_ws = nullptr,
+             size_t big_ws_bytes = 0);
+
+int fine_run(const ac_params* p, int groups, int per_group, int steps, const void* in, long long in_gs,
+             long long in_off, void* out, long long out_gs, long long out_off, const int* map, int adjoint,
+             const void* states, void* traj, cudaStream_t stream, void* big_ws, size_t big_ws_bytes) {
     int rc = check_params(p);
     if (rc) return rc;
     ACPR_CHECK_ARG(groups >= 0 && per_group >= 0 && steps >= 0, "counts must be >= 0");
@@ -526,7 +711,12 @@ int fine_run(const ac_params* p, int groups, int per_group, int steps, const voi
             set_error("ac_fine: n=%d supports plain propagation only (no trajectory or adjoint mode)", p->n);
             return AC_ERR_UNSUPPORTED;
         }
-        return fine_big_run(p, groups, per_group, steps, in, in_gs, in_off, out, out_gs, out_off, map, nullptr,
+        if (big_ws) {
+            const size_t need = fine_big_workspace_bytes(p->n, groups * per_group);
+            ACPR_CHECK_ARG(big_ws_bytes >= need, "ac_fine: workspace needs %zu bytes", need);
+            ACPR_CHECK_ARG(reinterpret_cast<uintptr_t>(big_ws) % 256 == 0, "workspace must be 256-byte aligned");
+        }
+        return fine_big_run(p, groups, per_group, steps, in, in_gs, in_off, out, out_gs, out_off, map, big_ws,
                             stream);
     }
     FineArgs a{};
@@ -555,9 +745,10 @@ int fine_run(const ac_params* p, int groups, int per_group, int steps, const voi
 
 int fine_propagate_mapped(const ac_params* p, int groups, int per_group, int steps, const void* in,
                           long long in_gs, long long in_off, void* out, long long out_gs,
-                          long long out_off, const int* map, cudaStream_t stream) {
+                          long long out_off, const int* map, cudaStream_t stream, void* big_ws,
+                          size_t big_ws_bytes) {
     return fine_run(p, groups, per_group, steps, in, in_gs, in_off, out, out_gs, out_off, map, 0, nullptr,
-                    nullptr, stream);
+                    nullptr, stream, big_ws, big_ws_bytes);
 }
 
 // Work-list launch: `count` fields, field f = (in field, out field, steps)
@@ -590,7 +781,7 @@ int fine_run_work(const ac_params* p, int count, const int4* work, const void* i
 
 int fine_propagate(const ac_params* p, int num_fields, int steps, const void* in, void* out,
                    cudaStream_t stream) {
-    return fine_propagate_mapped(p, 1, num_fields, steps, in, 0, 0, out, 0, 0, nullptr, stream);
+    return fine_propagate_mapped(p, 1, num_fields, steps, in, 0, 0, out, 0, 0, nullptr, stream, nullptr, 0);
 }
 
 }  // namespace acpr
@@ -608,6 +799,21 @@ extern "C" int ac_fine_propagate_slices(const ac_params* params, int num_fields,
                                         const void* u_starts, void* u_ends, acpr_stream stream) {
     return acpr::fine_propagate(params, num_fields, steps_per_slice, u_starts, u_ends,
                                 reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" size_t ac_fine_workspace_bytes(int n, int num_fields, int precision) {
+    if (num_fields <= 0 || !acpr::fine_big_supported(n, precision)) return 0;
+    return acpr::fine_big_workspace_bytes(n, num_fields);
+}
+
+extern "C" int ac_fine_propagate_slices_ws(const ac_params* params, int num_fields, int steps_per_slice,
+                                           const void* u_starts, void* u_ends, void* workspace,
+                                           size_t workspace_bytes, acpr_stream stream) {
+    using namespace acpr;
+    if (params && fine_big_supported(params->n, params->precision) && num_fields > 0)
+        ACPR_CHECK_ARG(workspace != nullptr, "ac_fine_propagate_slices_ws: n=%d needs a workspace", params->n);
+    return fine_propagate_mapped(params, 1, num_fields, steps_per_slice, u_starts, 0, 0, u_ends, 0, 0, nullptr,
+                                 reinterpret_cast<cudaStream_t>(stream), workspace, workspace_bytes);
 }
 
 extern "C" int ac_fine_trajectory(const ac_params* params, int num_fields, int steps, const void* u0, void* traj,
@@ -654,6 +860,7 @@ extern "C" int ac_fine_set_variant(int n, int precision, int index) {
     ACPR_CHECK_ARG(count > 0, "n=%d precision %d not built", n, precision);
     ACPR_CHECK_ARG(index >= 0 && index < count, "variant %d out of range (%d built)", index, count);
     g_variant[precision][ilog2(n)] = index;
+    g_variant_set[precision][ilog2(n)] = true;
     return AC_OK;
 }
 
@@ -672,6 +879,7 @@ extern "C" int ac_fine_autotune(const ac_params* params, int num_fields, int ste
     float best_ms = 1e30f;
     for (int v = 0; v < count; ++v) {
         g_variant[params->precision][ilog2(params->n)] = v;
+        g_variant_set[params->precision][ilog2(params->n)] = true;
         rc = fine_propagate(params, num_fields, steps, u_in, u_out, st);  // warm-up
         if (rc) break;
         ACPR_CUDA(cudaEventRecord(e0, st));
@@ -687,6 +895,7 @@ extern "C" int ac_fine_autotune(const ac_params* params, int num_fields, int ste
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     g_variant[params->precision][ilog2(params->n)] = best;
+    g_variant_set[params->precision][ilog2(params->n)] = true;
     return rc ? rc : AC_OK;
 }
 
