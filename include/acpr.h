@@ -163,6 +163,19 @@ int ac_fine_propagate_slices(const ac_params* params, int num_fields, int steps_
 int ac_fine_propagate_work(const ac_params* params, int count, const void* work, const void* u_in,
                            void* u_out, acpr_stream stream);
 
+/* ac_fine_propagate_slices with a caller-owned workspace: at n = 1024 the
+ * two-pass path keeps each field's half spectra between passes in
+ * `workspace` (device, 256-byte aligned, at least
+ * ac_fine_workspace_bytes(n, num_fields, precision) bytes) and the call
+ * allocates nothing.  Without a workspace (ac_fine_propagate_slices) the
+ * library keeps its own per-device buffer, allocated on the first n = 1024
+ * call and grown when a call needs more (that call then waits for the device
+ * and allocates).  Other sizes need no workspace (0 bytes; may be NULL). */
+size_t ac_fine_workspace_bytes(int n, int num_fields, int precision);
+int ac_fine_propagate_slices_ws(const ac_params* params, int num_fields, int steps_per_slice,
+                                const void* u_starts, void* u_ends, void* workspace, size_t workspace_bytes,
+                                acpr_stream stream);
+
 /* The fine steps of ac_fine_propagate_slices, also storing every state:
  * traj[s][f] = u^s of field f for s = 0..steps (device [steps+1][num_fields]
  * [n][n]); u0: device [num_fields][n][n]. */
@@ -204,7 +217,11 @@ int ac_energy_gradient_ic(const ac_params* params, int steps, int checkpoint_eve
 /* Bytes of device workspace cnn_desc.packed needs (0 for AC_F64). */
 size_t cnn_packed_bytes(const cnn_desc* desc);
 
-/* Bytes of `work` one cnn_coarse_step call on `batch` n x n fields needs. */
+/* Bytes of `work` one cnn_coarse_step call on `batch` n x n fields needs.
+ * The workspace starts with a 256-byte header whose first int is the status
+ * word of the tensor-core kernels (nonzero after a bounded device wait gave
+ * up); the header must be zero when the workspace is first used, and the
+ * library clears the word when it reports the error. */
 size_t cnn_work_bytes(const cnn_desc* desc, int n, int batch);
 
 /* Convert the float32 master weights into the packed bf16 layout the tensor
@@ -213,9 +230,27 @@ int cnn_pack_weights(const cnn_desc* desc, acpr_stream stream);
 
 /* One application of the coarse propagator G (Sec. 3.2) to each of `batch`
  * fields.  u_in, u_out: device [batch][n][n] (float64 for AC_F64, float32 for
- * AC_F32); they may not overlap.  n: power of two, 8 <= n <= 1024. */
+ * AC_F32); they may not overlap.  n: power of two, 8 <= n <= 1024.
+ * AC_F32 calls synchronise `stream` at the end to read the workspace status
+ * word and return AC_ERR_TIMEOUT if a bounded wait of the tensor-core kernels
+ * gave up (u_out is then not valid); inside a stream capture the check is
+ * skipped and the caller runs ac_conv_status after replaying the graph. */
 int cnn_coarse_step(const cnn_desc* desc, int n, int batch, const void* u_in, void* u_out,
                     acpr_stream stream);
+
+/* Failure detection (no counterpart in the paper): AC_ERR_TIMEOUT if a
+ * tensor-core conv kernel that used `workspace` (a cnn_desc.work buffer or a
+ * cnn_forward_train workspace) gave up a bounded wait since the last check;
+ * the status word is cleared.  Synchronises `stream`. */
+int ac_conv_status(void* workspace, acpr_stream stream);
+
+/* Test hook for the failure detection above: with polls > 0, later launches
+ * of the persistent tensor-core conv kernel (n >= 128) make their MMA issuer
+ * wait, for `polls` polls of about 32 ns, on an mbarrier that nothing arrives
+ * on, so that the bounded-wait path runs: the kernel drains its copies, frees
+ * its tensor memory and stores the status code.  0 switches it off.  Host
+ * state of this process; not thread-safe. */
+int ac_test_conv_stall(int polls);
 
 /* Convergence increment of Algorithm 2 between two trajectories
  * U[num_slices + 1][n][n] (slice 0, the fixed initial datum, is skipped):
@@ -263,7 +298,10 @@ int parareal_residual_noalloc(int num_slices, int n, int precision, const void* 
  * ------------------------------------------------------------------------ */
 
 /* Bytes of the training workspace for `batch` n x n fields (saved layer
- * inputs and pre-activations, gradient buffers, reduction partials). */
+ * inputs and pre-activations, gradient buffers, reduction partials).  Like
+ * cnn_desc.work it starts with the zero-initialised 256-byte status header;
+ * cnn_forward_train and cnn_backward synchronise `stream` at the end to read
+ * it (AC_ERR_TIMEOUT after a bounded wait gave up; skipped inside a capture). */
 size_t cnn_train_bytes(const cnn_desc* desc, int n, int batch);
 
 /* Forward pass that also saves, into train_ws, what cnn_backward needs.
@@ -409,11 +447,18 @@ int acnn_adam_step(int precision, void* w, const void* grad, void* m, void* v, l
  * one Adam step; U then becomes the U1 of the last update.  adam_m, adam_v:
  * device moments (weights then biases, zeroed by the caller before the first
  * call); *t: Adam step count, carried between calls.  losses_dev: device
- * float64[epochs * (R/q) * steps * b_inner], one loss per update.  Allocates
- * its workspace per call; SYNCHRONOUS. */
+ * float64[epochs * (R/q) * steps * b_inner], one loss per update.
+ * workspace: caller-owned device memory, 256-byte aligned, of at least
+ * acnn_train_alg1_bytes(desc, n, q) bytes (the subset's fields, gradients and
+ * the training and loss workspaces); the call allocates nothing.
+ * SYNCHRONOUS. */
 int acnn_train_alg1(const ac_params* params, const acnn_desc* desc, int R, const void* U0s, const int* perm,
                     int epochs, int q, int steps, int b_inner, double lr, double beta1, double beta2, double eps,
-                    void* adam_m, void* adam_v, int* t, double* losses_dev, acpr_stream stream);
+                    void* adam_m, void* adam_v, int* t, double* losses_dev, void* workspace,
+                    size_t workspace_bytes, acpr_stream stream);
+
+/* Bytes of the acnn_train_alg1 workspace for n x n fields and subsets of q. */
+size_t acnn_train_alg1_bytes(const acnn_desc* desc, int n, int q);
 
 /* ------------------------------------------------------------------------
  * Parareal driver (Algorithm 2) for `problems` independent problems that

@@ -60,12 +60,12 @@ EXPORTS = ["ac_last_error", "ac_fine_supported", "ac_fine_step", "ac_fine_propag
            "ac_parareal_solve_many", "ac_parareal_reset", "ac_parareal_enable_timing", "ac_parareal_set_fine_scheme", "ac_parareal_set_coarse_substeps",
            "ac_parareal_get_stats", "ac_parareal_reset_stats", "ac_launch_count", "ac_parareal_destroy",
            "ac_fine_variant_count", "ac_fine_variant_name", "ac_fine_get_variant", "ac_fine_set_variant",
-           "ac_fine_autotune", "ac_fine_propagate_work", "ac_fine_trajectory", "ac_fine_adjoint", "ac_energy", "ac_energy_grad",
+           "ac_fine_autotune", "ac_fine_propagate_work", "ac_fine_workspace_bytes", "ac_fine_propagate_slices_ws", "ac_fine_trajectory", "ac_fine_adjoint", "ac_energy", "ac_energy_grad",
            "ac_energy_gradient_workspace", "ac_energy_gradient_ic",
-           "cnn_train_bytes", "cnn_forward_train", "cnn_backward", "cnn_adam_step", "mse_loss_grad",
+           "ac_conv_status", "ac_test_conv_stall", "cnn_train_bytes", "cnn_forward_train", "cnn_backward", "cnn_adam_step", "mse_loss_grad",
            "acnn_param_count", "acnn_create", "acnn_destroy", "acnn_work_bytes", "acnn_forward", "acnn_train_bytes",
            "acnn_forward_train", "acnn_backward", "loss_acn_work_bytes", "loss_acn", "acnn_adam_step",
-           "acnn_train_alg1", "ac_parareal_set_coarse_acnn",
+           "acnn_train_alg1", "acnn_train_alg1_bytes", "ac_parareal_set_coarse_acnn",
            "ac_fine3d_supported", "ac_fine3d_work_bytes", "ac_fine3d_propagate"]
 
 
@@ -88,6 +88,9 @@ def load(build_if_missing: bool = True):
         L.ac_fine_supported.argtypes = [I, I]
         L.ac_fine_step.argtypes = [P(ac_params), I, S, S, S]
         L.ac_fine_propagate_slices.argtypes = [P(ac_params), I, I, S, S, S]
+        L.ac_fine_workspace_bytes.argtypes = [I, I, I]
+        L.ac_fine_workspace_bytes.restype = C.c_size_t
+        L.ac_fine_propagate_slices_ws.argtypes = [P(ac_params), I, I, S, S, S, C.c_size_t, S]
         L.ac_cn_propagate_slices.argtypes = [P(ac_params), I, I, S, S, D, I, S, S]
         L.cnn_packed_bytes.argtypes = [P(cnn_desc)]
         L.cnn_packed_bytes.restype = C.c_size_t
@@ -128,6 +131,8 @@ def load(build_if_missing: bool = True):
         L.ac_energy_gradient_workspace.argtypes = [P(ac_params), I, I]
         L.ac_energy_gradient_workspace.restype = C.c_size_t
         L.ac_energy_gradient_ic.argtypes = [P(ac_params), I, I, S, S, S, C.c_size_t, S]
+        L.ac_conv_status.argtypes = [S, S]
+        L.ac_test_conv_stall.argtypes = [I]
         L.cnn_train_bytes.argtypes = [P(cnn_desc), I, I]
         L.cnn_train_bytes.restype = C.c_size_t
         L.cnn_forward_train.argtypes = [P(cnn_desc), I, I, S, S, S, S]
@@ -153,7 +158,9 @@ def load(build_if_missing: bool = True):
         L.loss_acn.argtypes = [P(ac_params), I, S, S, S, S, S, S]
         L.acnn_adam_step.argtypes = [I, S, S, S, S, C.c_longlong, D, D, D, D, I, S]
         L.acnn_train_alg1.argtypes = [P(ac_params), P(acnn_desc), I, S, P(I), I, I, I, I, D, D, D, D, S, S, P(I),
-                                      S, S]
+                                      S, S, C.c_size_t, S]
+        L.acnn_train_alg1_bytes.argtypes = [P(acnn_desc), I, I]
+        L.acnn_train_alg1_bytes.restype = C.c_size_t
         L.ac_parareal_set_coarse_acnn.argtypes = [S, S]
         L.ac_fine3d_supported.argtypes = [I, I]
         L.ac_fine3d_work_bytes.argtypes = [I, I, I]
@@ -241,6 +248,22 @@ def ac_fine_propagate_slices(params: FineParams, steps: int, u_in, u_out=None, s
     p = params.c()
     _check(load().ac_fine_propagate_slices(C.byref(p), fields, int(steps), _dev(u_in, params.dtype, "u_in"),
                                            _dev(u_out, params.dtype, "u_out"), _stream(stream)))
+    return u_out
+
+
+def ac_fine_workspace_bytes(n: int, num_fields: int, precision: int) -> int:
+    return int(load().ac_fine_workspace_bytes(int(n), int(num_fields), int(precision)))
+
+
+def ac_fine_propagate_slices_ws(params: FineParams, steps: int, u_in, u_out, workspace, stream=None):
+    """ac_fine_propagate_slices with a caller-owned workspace (uint8 device
+    tensor of ac_fine_workspace_bytes bytes; the call allocates nothing)."""
+    fields = u_in.numel() // (params.n * params.n)
+    p = params.c()
+    ws = _dev(workspace, None, "workspace") if workspace is not None else None
+    nbytes = workspace.numel() if workspace is not None else 0
+    _check(load().ac_fine_propagate_slices_ws(C.byref(p), fields, int(steps), _dev(u_in, params.dtype, "u_in"),
+                                              _dev(u_out, params.dtype, "u_out"), ws, nbytes, _stream(stream)))
     return u_out
 
 
@@ -377,7 +400,8 @@ class CoarseNet:
         d = self.desc()
         need = load().cnn_work_bytes(C.byref(d), int(n), int(batch))
         if self._work is None or self._work.numel() < need:
-            self._work = torch.empty(max(need, 16), dtype=torch.uint8, device=self.w.device)
+            # zeros: the workspace header holds the conv kernels' status word
+            self._work = torch.zeros(max(need, 256), dtype=torch.uint8, device=self.w.device)
 
 
 class TrainableCoarseNet(CoarseNet):
@@ -399,7 +423,8 @@ class TrainableCoarseNet(CoarseNet):
 
     def new_workspace(self, n, batch):
         import torch
-        return torch.empty(self.train_bytes(n, batch), dtype=torch.uint8, device=self.w.device)
+        # zeros: the workspace header holds the conv kernels' status word
+        return torch.zeros(self.train_bytes(n, batch), dtype=torch.uint8, device=self.w.device)
 
     def forward_train(self, u, ws, out=None, stream=None):
         n = u.shape[-1]
@@ -609,11 +634,15 @@ class Acnn:
         p = params.c()
         d = self.desc()
         t = C.c_int(self.t)
+        nbytes = load().acnn_train_alg1_bytes(C.byref(d), int(params.n), int(q))
+        if getattr(self, "_alg1_ws", None) is None or self._alg1_ws.numel() < nbytes:
+            self._alg1_ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.w.device)
         _check(load().acnn_train_alg1(C.byref(p), C.byref(d), R, _dev(U0s, _dtype(self.precision), "U0s"),
                                       perm.ctypes.data_as(C.POINTER(C.c_int)), epochs, int(q), int(steps),
                                       int(b_inner), lr, beta1, beta2, eps, C.c_void_p(self.m.data_ptr()),
                                       C.c_void_p(self.v.data_ptr()), C.byref(t),
-                                      _dev(losses, torch.float64, "losses"), _stream(stream)))
+                                      _dev(losses, torch.float64, "losses"), _dev(self._alg1_ws, None, "ws"),
+                                      self._alg1_ws.numel(), _stream(stream)))
         self.t = t.value
         self.invalidate()
         return losses[: epochs * (R // q) * steps * b_inner]
@@ -669,6 +698,57 @@ def coarse_step_function():
     return CoarseStep
 
 
+def fine_solve_function():
+    """torch.autograd.Function over `steps` fine steps of a batch of fields
+    (the stabilised scheme of ac_params, Sec. 3.1), for gradients of any
+    scalar loss of the final fields through long rollouts.
+
+    forward(u0, params, steps, checkpoint_every): u^steps from u0 [.., n, n],
+    keeping only the fields at every `checkpoint_every`-th step (one segment
+    start each).  backward: for each segment, last first, the library
+    recomputes the segment's states from its checkpoint (ac_fine_trajectory)
+    and runs the transposed steps through them (ac_fine_adjoint), so memory is
+    (steps / checkpoint_every + checkpoint_every) fields per field.  Every
+    step of both passes runs in the library's kernels."""
+    import torch
+
+    class FineSolve(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, u0, params, steps, checkpoint_every=32):
+            if steps < 0 or checkpoint_every < 1:
+                raise ValueError("need steps >= 0 and checkpoint_every >= 1")
+            u = u0.contiguous()
+            ckpts, lens = [], []
+            done = 0
+            while done < steps:
+                seg = min(checkpoint_every, steps - done)
+                ckpts.append(u)
+                lens.append(seg)
+                u = ac_fine_propagate_slices(params, seg, u)
+                done += seg
+            ctx.params, ctx.lens = params, lens
+            ctx.save_for_backward(*ckpts)
+            return u if steps else u.clone()
+
+        @staticmethod
+        def backward(ctx, gout):
+            params, lens = ctx.params, ctx.lens
+            ckpts = ctx.saved_tensors
+            lam = gout.contiguous()
+            for u_start, seg in zip(reversed(ckpts), reversed(lens)):
+                traj = ac_fine_trajectory(params, seg, u_start)
+                lam = ac_fine_adjoint(params, seg, traj[:seg].contiguous(), lam)
+            return lam, None, None, None
+
+    return FineSolve
+
+
+def fine_solve(u0, params: FineParams, steps: int, checkpoint_every: int = 32):
+    """u^steps = F_1^steps(u0), differentiable with respect to u0 (see
+    fine_solve_function)."""
+    return fine_solve_function().apply(u0, params, int(steps), int(checkpoint_every))
+
+
 def cnn_packed_bytes(net: CoarseNet) -> int:
     d = net.desc()
     return load().cnn_packed_bytes(C.byref(d))
@@ -693,6 +773,19 @@ def cnn_coarse_step(net: CoarseNet, u_in, u_out=None, stream=None):
     _check(load().cnn_coarse_step(C.byref(d), n, batch, _dev(u_in, dt, "u_in"), _dev(u_out, dt, "u_out"),
                                   _stream(stream)))
     return u_out
+
+
+def ac_conv_status(workspace, stream=None):
+    """Raise AC_ERR_TIMEOUT if a tensor-core conv kernel that used this
+    workspace (CoarseNet work or a training workspace) gave up a bounded wait
+    since the last check; clears the status word."""
+    _check(load().ac_conv_status(_dev(workspace, None, "workspace"), _stream(stream)))
+
+
+def ac_test_conv_stall(polls: int):
+    """Test hook: polls > 0 makes the persistent tensor-core conv kernels wait,
+    for that many polls, on an mbarrier nothing arrives on (0 turns it off)."""
+    _check(load().ac_test_conv_stall(int(polls)))
 
 
 def parareal_solve_many(handles, streams, tol, kmax, allow_unconverged=False):

@@ -731,10 +731,37 @@ extern "C" int acnn_adam_step(int precision, void* w, const void* grad, void* m,
     return AC_OK;
 }
 
+// Workspace of acnn_train_alg1, 256-byte aligned pieces: U, U1, G ([q][n][n]
+// each), the parameter gradients, the training and the loss workspaces.
+struct Alg1Layout {
+    size_t u, u1, g, gp, ws, lw, total;
+};
+static Alg1Layout alg1_layout(const acnn_desc* desc, int n, int q) {
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t es = elem_size(desc->precision);
+    long long nb = 0;
+    const long long nw = acnn_param_count(desc->channels, desc->blocks, &nb);
+    const size_t field = up(es * size_t(n) * n * q);
+    Alg1Layout L{};
+    L.u = 0;
+    L.u1 = L.u + field;
+    L.g = L.u1 + field;
+    L.gp = L.g + field;
+    L.ws = L.gp + up(es * size_t(nw + nb));
+    L.lw = L.ws + up(acnn_train_bytes_for(desc, n, q));
+    L.total = L.lw + up(loss_acn_work_bytes(n, q));
+    return L;
+}
+
+extern "C" size_t acnn_train_alg1_bytes(const acnn_desc* desc, int n, int q) {
+    if (!desc || n <= 0 || q <= 0) return 0;
+    return alg1_layout(desc, n, q).total;
+}
+
 extern "C" int acnn_train_alg1(const ac_params* params, const acnn_desc* desc, int R, const void* U0s,
                                const int* perm, int epochs, int q, int steps, int b_inner, double lr, double beta1,
                                double beta2, double eps, void* adam_m, void* adam_v, int* t, double* losses_dev,
-                               acpr_stream stream) {
+                               void* workspace, size_t workspace_bytes, acpr_stream stream) {
     int rc = acnn_check(desc);
     if (rc) return rc;
     ACPR_CHECK_ARG(params && U0s && perm && adam_m && adam_v && t && losses_dev, "null acnn_train_alg1 argument");
@@ -754,19 +781,17 @@ extern "C" int acnn_train_alg1(const ac_params* params, const acnn_desc* desc, i
     const long long nn = (long long)n * n;
     long long nb = 0;
     const long long nw = acnn_param_count(desc->channels, desc->blocks, &nb);
-    const size_t field = es * size_t(nn) * q;
-    const size_t tws = acnn_train_bytes_for(desc, n, q), lws = loss_acn_work_bytes(n, q);
-    void *U = nullptr, *U1 = nullptr, *G = nullptr, *gp = nullptr, *ws = nullptr, *lw = nullptr;
-    auto release = [&] {
-        for (void* p : {U, U1, G, gp, ws, lw})
-            if (p) cudaFree(p);
-    };
-    if (cudaMalloc(&U, field) || cudaMalloc(&U1, field) || cudaMalloc(&G, field) ||
-        cudaMalloc(&gp, es * size_t(nw + nb)) || cudaMalloc(&ws, tws) || cudaMalloc(&lw, lws)) {
-        release();
-        set_error("acnn_train_alg1: cudaMalloc failed");
-        return AC_ERR_NOMEM;
-    }
+    const Alg1Layout lay = alg1_layout(desc, n, q);
+    ACPR_CHECK_ARG(workspace && workspace_bytes >= lay.total, "acnn_train_alg1: workspace needs %zu bytes",
+                   lay.total);
+    ACPR_CHECK_ARG(reinterpret_cast<uintptr_t>(workspace) % 256 == 0, "workspace must be 256-byte aligned");
+    char* wsb = static_cast<char*>(workspace);
+    void* U = wsb + lay.u;
+    void* U1 = wsb + lay.u1;
+    void* G = wsb + lay.g;
+    void* gp = wsb + lay.gp;
+    void* ws = wsb + lay.ws;
+    void* lw = wsb + lay.lw;
     char* gw = static_cast<char*>(gp);
     char* gb = gw + es * nw;
     char* mw = static_cast<char*>(adam_m);
@@ -799,7 +824,6 @@ extern "C" int acnn_train_alg1(const ac_params* params, const acnn_desc* desc, i
             }
         }
     cudaError_t e = cudaStreamSynchronize(st);
-    release();
     if (rc) return rc;
     ACPR_CUDA(e);
     return AC_OK;

@@ -332,7 +332,7 @@ static int last_pixels(int n) { return n * n >= kLastThreads ? kLastThreads : n 
 size_t work_bytes_for(const cnn_desc* d, int n, int batch) {
     const size_t act = size_t(batch) * d->channels * n * n * (d->precision == AC_F64 ? 8 : 2);
     const size_t zpart = size_t(batch) * (size_t(n) * n / last_pixels(n)) * sizeof(double);
-    return 2 * act + zpart;
+    return kConvHeader + 2 * act + zpart;
 }
 
 // Last layer and (if d->mass_fix) the mass shift, for the AC_F32 path.
@@ -381,13 +381,15 @@ static int run_f32(const cnn_desc* d, int n, int batch, const float* u, float* o
     const float* W = static_cast<const float*>(d->w);
     const float* Bv = static_cast<const float*>(d->b);
     const size_t act_elems = size_t(batch) * C * n * n;
-    __nv_bfloat16* a0 = static_cast<__nv_bfloat16*>(d->work);
+    unsigned char* wb = static_cast<unsigned char*>(d->work) + kConvHeader;
+    int* status = conv_status(d->work);
+    __nv_bfloat16* a0 = reinterpret_cast<__nv_bfloat16*>(wb);
     __nv_bfloat16* a1 = a0 + act_elems;
     conv_first_bf16_kernel<C><<<blocks, threads, 0, st>>>(u, a0, W, Bv, batch, n, d->act, io);
     ACPR_LAUNCH_CHECK();
     size_t woff = size_t(C) * 9, boff = C;
     for (int l = 1; l < d->layers - 1; ++l) {
-        int rc = hidden_layer_bf16(d, l, n, batch, a0, a1, W + woff, Bv + boff, st);
+        int rc = hidden_layer_bf16(d, l, n, batch, a0, a1, W + woff, Bv + boff, status, st);
         if (rc == AC_ERR_UNSUPPORTED) {
             conv_hidden_bf16_cc_kernel<C><<<blocks, threads, 0, st>>>(a0, a1, W + woff, Bv + boff, batch, n, d->act);
             ACPR_LAUNCH_CHECK();
@@ -398,8 +400,7 @@ static int run_f32(const cnn_desc* d, int n, int batch, const float* u, float* o
         boff += C;
         __nv_bfloat16* t = a0; a0 = a1; a1 = t;
     }
-    double* zpart = reinterpret_cast<double*>(static_cast<unsigned char*>(d->work) +
-                                              2 * act_elems * sizeof(__nv_bfloat16));
+    double* zpart = reinterpret_cast<double*>(wb + 2 * act_elems * sizeof(__nv_bfloat16));
     return last_layer_f32<C>(d, n, batch, a0, out, W + woff, Bv + boff, u, io, zpart, st);
 }
 
@@ -411,7 +412,7 @@ static int run_f64(const cnn_desc* d, int n, int batch, const double* u, double*
     const double* W = static_cast<const double*>(d->w);
     const double* Bv = static_cast<const double*>(d->b);
     const size_t act_elems = size_t(batch) * d->channels * n * n;
-    double* a0 = static_cast<double*>(d->work);
+    double* a0 = reinterpret_cast<double*>(static_cast<unsigned char*>(d->work) + kConvHeader);
     double* a1 = a0 + act_elems;
     size_t woff = 0, boff = 0;
     const double* cur = u;
@@ -514,5 +515,20 @@ extern "C" int cnn_pack_weights(const cnn_desc* desc, acpr_stream stream) {
 
 extern "C" int cnn_coarse_step(const cnn_desc* desc, int n, int batch, const void* u_in, void* u_out,
                                acpr_stream stream) {
-    return acpr::coarse_step(desc, n, batch, u_in, u_out, reinterpret_cast<cudaStream_t>(stream));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int rc = acpr::coarse_step(desc, n, batch, u_in, u_out, st);
+    if (rc || batch <= 0 || desc->precision != AC_F32) return rc;
+    // a bounded wait of the tensor-core kernels that gave up left its code in
+    // the workspace header: report it here (this synchronises the stream)
+    return acpr::conv_check_status_uncaptured(acpr::conv_status(desc->work), st);
+}
+
+extern "C" int ac_conv_status(void* workspace, acpr_stream stream) {
+    ACPR_CHECK_ARG(workspace != nullptr, "workspace is NULL");
+    return acpr::conv_check_status(acpr::conv_status(workspace), reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int ac_test_conv_stall(int polls) {
+    acpr::set_test_stall(polls);
+    return AC_OK;
 }

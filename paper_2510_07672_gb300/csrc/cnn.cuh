@@ -85,19 +85,31 @@ __device__ __forceinline__ T act_grad(int act, T x) {
     return act_grad_gelu(x);
 }
 
-// Device-side timeout flag of the tensor-core kernels: returns AC_ERR_TIMEOUT
-// (and clears the flag) if a bounded wait gave up since the last call.
-// Synchronises the stream.
-int tc_check_status(cudaStream_t st);
+// Every conv workspace (cnn_desc.work and the training workspace) starts
+// with a header of kConvHeader bytes whose first int is the status word of
+// the tensor-core kernels: a bounded wait that gives up stores a nonzero code
+// there.  The header must be zero when the workspace is first used.
+constexpr size_t kConvHeader = 256;
+inline int* conv_status(void* ws) { return static_cast<int*>(ws); }
+
+// AC_ERR_TIMEOUT (and the word cleared) if a bounded wait gave up since the
+// last check of this status word.  Synchronises the stream.
+int conv_check_status(int* status, cudaStream_t st);
+// The same, unless `st` is being captured into a graph (then AC_OK: the
+// graph's owner checks after a replay).
+int conv_check_status_uncaptured(int* status, cudaStream_t st);
+// Test hook: with polls > 0 the persistent tensor-core kernels' MMA issuer
+// waits on an mbarrier that nothing arrives on, for `polls` polls.
+void set_test_stall(int polls);
 
 int hidden_layer_bf16(const cnn_desc* d, int l, int n, int batch, const __nv_bfloat16* in,
-                      __nv_bfloat16* out, const float* w_master, const float* bias, cudaStream_t st,
+                      __nv_bfloat16* out, const float* w_master, const float* bias, int* status, cudaStream_t st,
                       float* zsave = nullptr);
 
 // Backward through hidden layer l+1 into layer l's pre-activation gradient:
 // dz_out = bf16(conv(dz_next, w_t) * act'(z_prev)), w_t from pack_hidden_t.
 int hidden_dgrad_bf16(int C, int act, int n, int batch, const __nv_bfloat16* dz_next, __nv_bfloat16* dz_out,
-                      const __nv_bfloat16* w_t, const float* z_prev, cudaStream_t st);
+                      const __nv_bfloat16* w_t, const float* z_prev, int* status, cudaStream_t st);
 int pack_hidden_t(int C, const float* w_layer, __nv_bfloat16* out, cudaStream_t st);
 
 }  // namespace acpr

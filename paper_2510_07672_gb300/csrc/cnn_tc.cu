@@ -17,7 +17,8 @@
 // and its two wrap pixels), completing on an mbarrier.  The epilogue reads
 // TMEM with tcgen05.ld, adds the float32 bias, applies the activation, rounds
 // to bf16 and stores 16-byte channel chunks.  All waits are bounded; a timeout
-// sets a device flag that tc_check_status() reports as AC_ERR_TIMEOUT.
+// sets the caller's status word (the first int of the conv workspace), which
+// conv_check_status() reports as AC_ERR_TIMEOUT.
 // Fields with n >= 128 take the persistent, warp-specialised kernel below.
 #include "cnn.cuh"
 #include "tc_ptx.cuh"
@@ -25,9 +26,35 @@
 namespace acpr {
 
 namespace {
-__device__ int g_tc_timeout = 0;
 constexpr int kTcThreads = 256;
 constexpr long long kTcSpin = 4000000;  // ~0.2 s of polls with 32 ns sleeps
+// Test hook (ac_test_conv_stall): > 0 makes the next persistent conv launches'
+// MMA issuer wait, with this poll limit, on an mbarrier nothing arrives on.
+int g_test_stall = 0;
+}
+
+void set_test_stall(int polls) { g_test_stall = polls > 0 ? polls : 0; }
+
+int conv_check_status_uncaptured(int* status, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    ACPR_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return AC_OK;
+    return conv_check_status(status, st);
+}
+
+int conv_check_status(int* status, cudaStream_t st) {
+    if (!status) return AC_OK;
+    int flag = 0;
+    ACPR_CUDA(cudaMemcpyAsync(&flag, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ACPR_CUDA(cudaStreamSynchronize(st));
+    if (flag) {
+        ACPR_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+        ACPR_CUDA(cudaStreamSynchronize(st));
+        set_error("tensor-core conv: bounded wait gave up (%s)",
+                  flag == 1 ? "operand loads" : flag == 2 ? "MMA completion" : "pipeline wait");
+        return AC_ERR_TIMEOUT;
+    }
+    return AC_OK;
 }
 
 // float32 master W[cout][cin][3][3] -> bf16 [tap][cin/8][cout][8]
@@ -109,7 +136,8 @@ template <int C>
 __global__ void __launch_bounds__(kTcThreads)
 conv_hidden_tc_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ out,
                       const __nv_bfloat16* __restrict__ wpk, const float* __restrict__ bias, int n, int TY,
-                      int n_mt, int plane_px, int ncols, int act, int mode, float* __restrict__ zio) {
+                      int n_mt, int plane_px, int ncols, int act, int mode, float* __restrict__ zio,
+                      int* __restrict__ status) {
     constexpr int KC = C / 8;
     extern __shared__ __align__(128) unsigned char smem[];
     const int W = n + 2;
@@ -175,11 +203,11 @@ conv_hidden_tc_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __res
         ok = tc::mbar_wait_bounded(&bars[1], 0, kTcSpin);
         ok = __syncthreads_and(ok);
         if (!ok) {
-            if (tid == 0) atomicExch(&g_tc_timeout, 2);
+            if (tid == 0) atomicExch(status, 2);
             tc::mbar_wait_bounded(&bars[1], 0, kTcSpin);  // let the MMAs drain
         }
     } else {
-        if (tid == 0) atomicExch(&g_tc_timeout, 1);
+        if (tid == 0) atomicExch(status, 1);
         tc::mbar_wait_bounded(&bars[0], 0, kTcSpin);  // let in-flight copies land
     }
     if (ok) {
@@ -291,6 +319,7 @@ static PShape p_shape(int n, int C) {
 }
 
 struct PCtl {
+    uint64_t never;  // test hook: nothing ever arrives here
     uint64_t full[kPMaxRing];
     uint64_t empty[kPMaxRing];
     uint64_t accf[kPStages];
@@ -302,14 +331,15 @@ struct PCtl {
     alignas(16) float bias[64];
 };
 
-__device__ __forceinline__ bool p_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-    for (long long i = 0; i < kTcSpin; ++i) {
+__device__ __forceinline__ bool p_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                       long long limit = kTcSpin) {
+    for (long long i = 0; i < limit; ++i) {
         if (tc::mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
         __nanosleep(32);
     }
     *abort_flag = 1;
-    atomicExch(&g_tc_timeout, 3);
+    atomicExch(status, 3);
     return false;
 }
 
@@ -317,7 +347,8 @@ template <int C, int MG>
 __global__ void __launch_bounds__(kPThreads, 1)
 conv_hidden_tc_persistent(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ out,
                           const __nv_bfloat16* __restrict__ wpk, const float* __restrict__ bias, int n,
-                          int batch, int RING, uint32_t slot_bytes, int act, int mode, float* __restrict__ zio) {
+                          int batch, int RING, uint32_t slot_bytes, int act, int mode, float* __restrict__ zio,
+                          int* __restrict__ status, int stall) {
     constexpr int KC = C / 8;
     constexpr int TY = kPStageCols / (MG * C);
     constexpr int NACC = TY * MG;
@@ -348,6 +379,7 @@ conv_hidden_tc_persistent(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* _
         }
         tc::mbar_init(&ctl->wbar, 1);
         tc::mbar_init(&ctl->fin, 1);
+        tc::mbar_init(&ctl->never, 1);
         ctl->abort = 0;
         tc::fence_mbar_init();
     }
@@ -378,7 +410,7 @@ conv_hidden_tc_persistent(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* _
                 yin = yin < 0 ? yin + n : (yin >= n ? yin - n : yin);
                 const int slot = int(s % RING);
                 const long long k = s / RING;
-                if (k >= 1 && !p_wait(&ctl->empty[slot], uint32_t((k - 1) & 1), abort_flag)) {
+                if (k >= 1 && !p_wait(&ctl->empty[slot], uint32_t((k - 1) & 1), abort_flag, status)) {
                     ok = false;
                     break;
                 }
@@ -403,7 +435,9 @@ conv_hidden_tc_persistent(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* _
         tc::mbar_wait_bounded(&ctl->wbar, 0, kTcSpin);
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer
-        bool ok = p_wait(&ctl->wbar, 0, abort_flag);
+        bool ok = p_wait(&ctl->wbar, 0, abort_flag, status);
+        // test hook: a wait that cannot succeed, so the bounded-wait path runs
+        if (ok && stall > 0) ok = p_wait(&ctl->never, 0, abort_flag, status, stall);
         const uint32_t idesc = tc::idesc_bf16_f32(128, C);
         const uint64_t a_hi = tc::smem_desc(0, plane_b, 128);
         const uint64_t b_hi = tc::smem_desc(0, C * 16, 128);
@@ -424,10 +458,10 @@ conv_hidden_tc_persistent(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* _
             }
             const int stage = i & 1;
             const int kk = i >> 1;
-            if (kk >= 1 && !p_wait(&ctl->acce[stage], uint32_t((kk - 1) & 1), abort_flag)) break;
+            if (kk >= 1 && !p_wait(&ctl->acce[stage], uint32_t((kk - 1) & 1), abort_flag, status)) break;
             const int aslot = a % RING;
             for (int d = 0; d < TY + 2 && ok; ++d)
-                ok = p_wait(&ctl->full[(a + d) % RING], uint32_t(((a + d) / RING) & 1), abort_flag);
+                ok = p_wait(&ctl->full[(a + d) % RING], uint32_t(((a + d) / RING) & 1), abort_flag, status);
             if (!ok) break;
             tc::fence_after_sync();
             const uint32_t dbase = tmem + uint32_t(stage * kPStageCols);
@@ -480,7 +514,7 @@ conv_hidden_tc_persistent(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* _
             const int cb = int(t % NB);
             const long long f = t / NB;
             const int stage = i & 1;
-            if (!p_wait(&ctl->accf[stage], uint32_t((i >> 1) & 1), abort_flag)) break;
+            if (!p_wait(&ctl->accf[stage], uint32_t((i >> 1) & 1), abort_flag, status)) break;
             tc::fence_after_sync();
             const size_t base =
                 (size_t(f) * KC * nn + size_t(yb * TY) * n + size_t(cb * CW + q * 32 + lane)) * 8;
@@ -553,7 +587,7 @@ static int num_sms() {
 template <int C, int MG>
 static int launch_persistent_mg(const PShape& s, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
                                 const __nv_bfloat16* w, const float* bias, int act, int mode, float* zio,
-                                cudaStream_t st) {
+                                int* status, cudaStream_t st) {
     auto kern = conv_hidden_tc_persistent<C, MG>;
     static bool configured = false;
     if (!configured) {
@@ -562,7 +596,8 @@ static int launch_persistent_mg(const PShape& s, int n, int batch, const __nv_bf
     }
     const long long units = (long long)batch * (n / s.CW) * (n / s.TY);
     const int grid = int(units < num_sms() ? units : num_sms());
-    kern<<<grid, kPThreads, s.smem, st>>>(in, out, w, bias, n, batch, s.RING, s.slot_bytes, act, mode, zio);
+    kern<<<grid, kPThreads, s.smem, st>>>(in, out, w, bias, n, batch, s.RING, s.slot_bytes, act, mode, zio, status,
+                                          g_test_stall);
     ACPR_LAUNCH_CHECK();
     return AC_OK;
 }
@@ -570,19 +605,24 @@ static int launch_persistent_mg(const PShape& s, int n, int batch, const __nv_bf
 template <int C>
 static int launch_persistent(const PShape& s, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
                              const __nv_bfloat16* w, const float* bias, int act, int mode, float* zio,
-                             cudaStream_t st) {
-    if (s.MG == 1) return launch_persistent_mg<C, 1>(s, n, batch, in, out, w, bias, act, mode, zio, st);
-    if constexpr (C < 64) return launch_persistent_mg<C, 2>(s, n, batch, in, out, w, bias, act, mode, zio, st);
+                             int* status, cudaStream_t st) {
+    if (s.MG == 1) return launch_persistent_mg<C, 1>(s, n, batch, in, out, w, bias, act, mode, zio, status, st);
+    if constexpr (C < 64)
+        return launch_persistent_mg<C, 2>(s, n, batch, in, out, w, bias, act, mode, zio, status, st);
     set_error("conv: no persistent kernel for C=%d, MG=%d", C, s.MG);
     return AC_ERR_UNSUPPORTED;
 }
 
 template <int C>
 static int launch_hidden(int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out, const __nv_bfloat16* w,
-                         const float* bias, int act, int mode, float* zio, cudaStream_t st) {
+                         const float* bias, int act, int mode, float* zio, int* status, cudaStream_t st) {
     if (batch <= 0) return AC_OK;
+    if (!status) {
+        set_error("tensor-core conv: no status word");
+        return AC_ERR_ARG;
+    }
     const PShape ps = p_shape(n, C);
-    if (ps.RING) return launch_persistent<C>(ps, n, batch, in, out, w, bias, act, mode, zio, st);
+    if (ps.RING) return launch_persistent<C>(ps, n, batch, in, out, w, bias, act, mode, zio, status, st);
     const TcShape s = pick_shape(n, C);
     if (s.TY == 0) return AC_ERR_UNSUPPORTED;
     auto kern = conv_hidden_tc_kernel<C>;
@@ -593,32 +633,32 @@ static int launch_hidden(int n, int batch, const __nv_bfloat16* in, __nv_bfloat1
     }
     const long long blocks = (long long)batch * (n / s.TY);
     kern<<<unsigned(blocks), kTcThreads, s.smem, st>>>(in, out, w, bias, n, s.TY, s.n_mt, s.plane_px, s.ncols, act,
-                                                       mode, zio);
+                                                       mode, zio, status);
     ACPR_LAUNCH_CHECK();
     return AC_OK;
 }
 
 int hidden_layer_bf16(const cnn_desc* d, int l, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
-                      const float* /*w_master*/, const float* bias, cudaStream_t st, float* zsave) {
+                      const float* /*w_master*/, const float* bias, int* status, cudaStream_t st, float* zsave) {
     if (n < 8) return AC_ERR_UNSUPPORTED;
     const int C = d->channels;
     const __nv_bfloat16* w = static_cast<const __nv_bfloat16*>(d->packed) + size_t(l - 1) * 9 * C * C;
     switch (C) {
-        case 16: return launch_hidden<16>(n, batch, in, out, w, bias, d->act, kFwd, zsave, st);
-        case 32: return launch_hidden<32>(n, batch, in, out, w, bias, d->act, kFwd, zsave, st);
-        case 64: return launch_hidden<64>(n, batch, in, out, w, bias, d->act, kFwd, zsave, st);
+        case 16: return launch_hidden<16>(n, batch, in, out, w, bias, d->act, kFwd, zsave, status, st);
+        case 32: return launch_hidden<32>(n, batch, in, out, w, bias, d->act, kFwd, zsave, status, st);
+        case 64: return launch_hidden<64>(n, batch, in, out, w, bias, d->act, kFwd, zsave, status, st);
         default: return AC_ERR_UNSUPPORTED;
     }
 }
 
 int hidden_dgrad_bf16(int C, int act, int n, int batch, const __nv_bfloat16* dz_next, __nv_bfloat16* dz_out,
-                      const __nv_bfloat16* w_t, const float* z_prev, cudaStream_t st) {
+                      const __nv_bfloat16* w_t, const float* z_prev, int* status, cudaStream_t st) {
     if (n < 8) return AC_ERR_UNSUPPORTED;
     float* zp = const_cast<float*>(z_prev);
     switch (C) {
-        case 16: return launch_hidden<16>(n, batch, dz_next, dz_out, w_t, nullptr, act, kDgrad, zp, st);
-        case 32: return launch_hidden<32>(n, batch, dz_next, dz_out, w_t, nullptr, act, kDgrad, zp, st);
-        case 64: return launch_hidden<64>(n, batch, dz_next, dz_out, w_t, nullptr, act, kDgrad, zp, st);
+        case 16: return launch_hidden<16>(n, batch, dz_next, dz_out, w_t, nullptr, act, kDgrad, zp, status, st);
+        case 32: return launch_hidden<32>(n, batch, dz_next, dz_out, w_t, nullptr, act, kDgrad, zp, status, st);
+        case 64: return launch_hidden<64>(n, batch, dz_next, dz_out, w_t, nullptr, act, kDgrad, zp, status, st);
         default: return AC_ERR_UNSUPPORTED;
     }
 }
@@ -640,20 +680,6 @@ __global__ void pack_hidden_t_kernel(const float* __restrict__ w, __nv_bfloat16*
 int pack_hidden_t(int C, const float* w_layer, __nv_bfloat16* out, cudaStream_t st) {
     pack_hidden_t_kernel<<<64, 256, 0, st>>>(w_layer, out, C);
     ACPR_LAUNCH_CHECK();
-    return AC_OK;
-}
-
-int tc_check_status(cudaStream_t st) {
-    int flag = 0;
-    ACPR_CUDA(cudaMemcpyFromSymbolAsync(&flag, g_tc_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
-    ACPR_CUDA(cudaStreamSynchronize(st));
-    if (flag) {
-        const int zero = 0;
-        ACPR_CUDA(cudaMemcpyToSymbolAsync(g_tc_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st));
-        ACPR_CUDA(cudaStreamSynchronize(st));
-        set_error("tensor-core conv: bounded wait gave up (%s)", flag == 1 ? "operand loads" : "MMA completion");
-        return AC_ERR_TIMEOUT;
-    }
     return AC_OK;
 }
 

@@ -46,7 +46,7 @@ static TrainLayout train_layout(const cnn_desc* d, int n, int batch) {
     const int L = d->layers;
     t.a_bytes = act * 2;
     t.z_bytes = act * 4;
-    t.off_a = 0;
+    t.off_a = kConvHeader;  // the header holds the tensor-core kernels' status word
     t.off_z = t.off_a + t.a_bytes * (L - 1);
     t.off_dz = t.off_z + t.z_bytes * (L - 1);
     t.off_wt = t.off_dz + 2 * t.a_bytes;
@@ -343,7 +343,7 @@ static int forward_train(const cnn_desc* d, int n, int batch, const float* u, fl
     ACPR_LAUNCH_CHECK();
     size_t woff = size_t(C) * 9, boff = C;
     for (int l = 1; l < d->layers - 1; ++l) {
-        int rc = hidden_layer_bf16(d, l, n, batch, A(l), A(l + 1), W + woff, Bv + boff, st, Z(l));
+        int rc = hidden_layer_bf16(d, l, n, batch, A(l), A(l + 1), W + woff, Bv + boff, conv_status(ws), st, Z(l));
         if (rc) return rc;
         woff += size_t(C) * C * 9;
         boff += C;
@@ -398,7 +398,7 @@ static int backward(const cnn_desc* d, int n, int batch, const float* u, const f
         __nv_bfloat16* wl = wt + size_t(l - 1) * 9 * C * C;
         rc = pack_hidden_t(C, W + woffs[l], wl, st);
         if (rc) return rc;
-        rc = hidden_dgrad_bf16(C, d->act, n, batch, dz[cur], dz[cur ^ 1], wl, Z(l - 1), st);
+        rc = hidden_dgrad_bf16(C, d->act, n, batch, dz[cur], dz[cur ^ 1], wl, Z(l - 1), conv_status(ws), st);
         if (rc) return rc;
         cur ^= 1;
     }
@@ -476,10 +476,12 @@ extern "C" int cnn_forward_train(const cnn_desc* desc, int n, int batch, const f
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     unsigned char* ws = static_cast<unsigned char*>(train_ws);
     switch (desc->channels) {
-        case 16: return forward_train<16>(desc, n, batch, u_in, u_out, ws, st);
-        case 32: return forward_train<32>(desc, n, batch, u_in, u_out, ws, st);
-        default: return forward_train<64>(desc, n, batch, u_in, u_out, ws, st);
+        case 16: rc = forward_train<16>(desc, n, batch, u_in, u_out, ws, st); break;
+        case 32: rc = forward_train<32>(desc, n, batch, u_in, u_out, ws, st); break;
+        default: rc = forward_train<64>(desc, n, batch, u_in, u_out, ws, st); break;
     }
+    // a bounded tensor-core wait that gave up is reported here (synchronises)
+    return rc ? rc : conv_check_status_uncaptured(conv_status(train_ws), st);
 }
 
 extern "C" int cnn_backward(const cnn_desc* desc, int n, int batch, const float* u_in, const float* grad_out,
@@ -494,10 +496,11 @@ extern "C" int cnn_backward(const cnn_desc* desc, int n, int batch, const float*
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     unsigned char* ws = static_cast<unsigned char*>(train_ws);
     switch (desc->channels) {
-        case 16: return backward<16>(desc, n, batch, u_in, grad_out, grad_in, grad_w, grad_b, accumulate, ws, st);
-        case 32: return backward<32>(desc, n, batch, u_in, grad_out, grad_in, grad_w, grad_b, accumulate, ws, st);
-        default: return backward<64>(desc, n, batch, u_in, grad_out, grad_in, grad_w, grad_b, accumulate, ws, st);
+        case 16: rc = backward<16>(desc, n, batch, u_in, grad_out, grad_in, grad_w, grad_b, accumulate, ws, st); break;
+        case 32: rc = backward<32>(desc, n, batch, u_in, grad_out, grad_in, grad_w, grad_b, accumulate, ws, st); break;
+        default: rc = backward<64>(desc, n, batch, u_in, grad_out, grad_in, grad_w, grad_b, accumulate, ws, st); break;
     }
+    return rc ? rc : conv_check_status_uncaptured(conv_status(train_ws), st);
 }
 
 extern "C" int cnn_adam_step(float* w, const float* grad, float* m, float* v, long long count, double lr,

@@ -14,7 +14,7 @@ namespace acpr {
 
 int fine_run(const ac_params* p, int groups, int per_group, int steps, const void* in, long long in_gs,
              long long in_off, void* out, long long out_gs, long long out_off, const int* map, int adjoint,
-             const void* states, void* traj, cudaStream_t stream);
+             const void* states, void* traj, cudaStream_t stream, void* big_ws = nullptr, size_t big_ws_bytes = 0);
 
 constexpr int kEnergyThreads = 1024;
 

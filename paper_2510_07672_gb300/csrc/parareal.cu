@@ -11,7 +11,9 @@
 //      Ub[k]   = Fres[k-1] + (Gold[k-1] - Gold[k-1])  (U^k_{k-1} = U^{k-1}_{k-1})
 //   3. for n = k..s-1 in order: g = G(Ub[n]);
 //      Ub[n+1] = Fres[n] + (g - Gold[n]);  Gold[n] = g
-//   4. increment of Ub against Ua over slices 1..s, float64
+//   4. increment of Ub against Ua over slices 1..s, float64: the corrections
+//      of steps 2 and 3 leave per-block partial sums of the slices they write,
+//      one small kernel adds them up (no second pass over the trajectories)
 // The frozen prefix Ub[0..k-2] already equals Ua[0..k-2] (both hold the exact
 // fine values), so step 2 copies one slice only.  The summation order
 // F + (G_new - G_old) keeps U^k_k bitwise equal to the fine result.
@@ -29,12 +31,16 @@ namespace acpr {
 
 int fine_propagate_mapped(const ac_params* p, int groups, int per_group, int steps, const void* in,
                           long long in_gs, long long in_off, void* out, long long out_gs,
-                          long long out_off, const int* map, cudaStream_t stream);
+                          long long out_off, const int* map, cudaStream_t stream, void* big_ws,
+                          size_t big_ws_bytes);
+size_t fine_big_workspace_bytes(int n, int fields);
+bool fine_big_supported(int n, int precision);
 int fine_run_work(const ac_params* p, int count, const int4* work, const void* in, void* out, cudaStream_t stream);
 int cn_run_work(const ac_params* p, int count, const int4* work, const void* in, void* out, double tol,
                 int max_iters, cudaStream_t st);
 bool cn_supported(int n, int precision);
 bool fine_supported_internal(int n, int precision);
+int fine_check_status(cudaStream_t st);
 
 // ------------------------------------------------------------- kernels ----
 constexpr int kResThreads = 256;
@@ -100,24 +106,158 @@ __global__ void increment_finish_kernel(const double* __restrict__ part, int blo
     res[4 * p + 3] = den;
 }
 
-// Ub[n+1] = Fres[n] + (g - Gold[n]) and optionally Gold[n] = g, for the mapped
-// problems.  g = G(Ub[n]) is compact [batch][nn]; if g is NULL, Gold[n] is used
-// in its place (the exact slice) and Gold is left alone.
+// ------------------------------------------- correction fused with the increment --
+// The correction kernel also accumulates, for the slice it writes, the three
+// sums of the convergence test against the previous iterate: sum (U - U_old)^2,
+// sum U^2 and max |U - U_old|, per (problem, slice, block) in float64, so the
+// increment needs no second pass over the trajectories.
+//
+// float32 fields: each thread accumulates without rounding error that
+// matters, in float32 arithmetic (float64 arithmetic is scarce on this GPU):
+// d = a - b is split exactly into s + e (Knuth's TwoSum), d^2 = s^2 + (2 s e
+// + e^2) with s^2 split exactly by a fused multiply-add (Dekker's product),
+// and the sums are carried as unevaluated float pairs (hi + lo); the exact
+// max |d| is tracked as the pair (|s|, sign(s) e), compared
+// lexicographically (rounding is monotone).  The pairs become float64 once
+// per thread.  Relative error of the sums about 2^-44.
+// (The _rn intrinsics are never contracted into fused multiply-adds, which
+// the error-free transformations below rely on.)
+__device__ __forceinline__ void acc_two_sum(float& hi, float& lo, float p, float t) {
+    const float x = __fadd_rn(hi, p);
+    const float bv = __fsub_rn(x, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(x, bv)), __fsub_rn(p, bv));
+    hi = x;
+    lo = __fadd_rn(lo, __fadd_rn(err, t));
+}
+
+struct IncAcc32 {
+    float nh = 0.f, nl = 0.f, dh = 0.f, dl = 0.f, ms = 0.f, me = 0.f;
+    bool bad = false;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float s = __fsub_rn(a, b);
+        const float bb = __fsub_rn(s, a);
+        const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(-b, bb));
+        const float p = __fmul_rn(s, s);
+        float t = fmaf(s, s, -p);
+        t = fmaf(__fmul_rn(2.0f, s), e, t);
+        t = fmaf(e, e, t);
+        acc_two_sum(nh, nl, p, t);
+        const float q = __fmul_rn(a, a);
+        acc_two_sum(dh, dl, q, fmaf(a, a, -q));
+        const float as = fabsf(s), ae = s < 0.f ? -e : e;
+        if (as > ms || (as == ms && ae > me)) { ms = as; me = ae; }
+        if (!(s - s == 0.f)) bad = true;  // NaN or Inf
+    }
+    __device__ __forceinline__ void result(double& num, double& den, double& mx) const {
+        num = double(nh) + double(nl);
+        den = double(dh) + double(dl);
+        mx = bad ? __longlong_as_double(0x7ff8000000000000LL) : double(ms) + double(me);
+    }
+};
+
+struct IncAcc64 {
+    double num = 0.0, den = 0.0, mx = 0.0;
+    __device__ __forceinline__ void add(double a, double b) {
+        const double d = a - b;
+        num += d * d;
+        den += a * a;
+        mx = fmax(mx, fabs(d));
+        if (!(d == d)) mx = d;
+    }
+    __device__ __forceinline__ void result(double& n, double& d, double& m) const { n = num; d = den; m = mx; }
+};
+
+template <typename T> struct IncAccT;
+template <> struct IncAccT<float> { using type = IncAcc32; };
+template <> struct IncAccT<double> { using type = IncAcc64; };
+
+// Block sum of (num, den) and max (NaN kept) in a fixed order; thread 0 writes.
+__device__ __forceinline__ void block_partials(double num, double den, double mx, double* out) {
+    __shared__ double sh[3][kResThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+        const double m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = (m2 != m2) ? m2 : fmax(mx, m2);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { sh[0][w] = num; sh[1][w] = den; sh[2][w] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double n0 = 0.0, d0 = 0.0, m0 = 0.0;
+        for (int i = 0; i < kResThreads / 32; ++i) {
+            n0 += sh[0][i];
+            d0 += sh[1][i];
+            m0 = (sh[2][i] != sh[2][i]) ? sh[2][i] : fmax(m0, sh[2][i]);
+        }
+        out[0] = n0; out[1] = d0; out[2] = m0;
+    }
+}
+
+// Ub[n+1] = Fres[n] + (g - Gold[n]) (and Gold[n] = g; if g is NULL, Gold[n] is
+// used in its place: the exact slice) for batch entry blockIdx.y, plus the
+// block's increment partials of slice n + 1 against Ua into
+// part[((p s + n) NB + blockIdx.x) * 3].
 template <typename T>
-__global__ void correct_kernel(T* __restrict__ Ub, T* __restrict__ Gold, const T* __restrict__ Fres,
-                               const T* __restrict__ g, int slice, int s, long long nn, int batch,
-                               const int* __restrict__ map) {
-    const long long total = nn * batch;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int b = int(idx / nn);
-        const long long i = idx % nn;
-        const long long p = map ? map[b] : b;
-        T* go = Gold + (p * s + slice) * nn + i;
-        const T gold = *go;
-        const T gn = g ? g[(long long)b * nn + i] : gold;
-        Ub[(p * (s + 1) + slice + 1) * nn + i] = Fres[(p * s + slice) * nn + i] + (gn - gold);
-        if (g) *go = gn;
+__global__ void __launch_bounds__(kResThreads)
+correct_inc_kernel(T* __restrict__ Ub, const T* __restrict__ Ua, T* __restrict__ Gold, const T* __restrict__ Fres,
+                   const T* __restrict__ g, int slice, int s, long long nn, const int* __restrict__ map,
+                   double* __restrict__ part) {
+    const int b = blockIdx.y;
+    const long long p = map ? map[b] : b;
+    T* go = Gold + (p * s + slice) * nn;
+    const T* fr = Fres + (p * s + slice) * nn;
+    const T* gb = g ? g + (long long)b * nn : nullptr;
+    T* ub = Ub + (p * (s + 1) + slice + 1) * nn;
+    const T* ua = Ua + (p * (s + 1) + slice + 1) * nn;
+    typename IncAccT<T>::type acc;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nn;
+         i += (long long)gridDim.x * blockDim.x) {
+        const T gold = go[i];
+        const T gn = gb ? gb[i] : gold;
+        const T u = fr[i] + (gn - gold);
+        ub[i] = u;
+        if (gb) go[i] = gn;
+        acc.add(u, ua[i]);
+    }
+    double num, den, mx;
+    acc.result(num, den, mx);
+    block_partials(num, den, mx, part + ((p * s + slice) * gridDim.x + blockIdx.x) * 3);
+}
+
+// Increment of iteration k for the mapped problems: slices k..s from this
+// iteration's partials, slices 1..k-1 (frozen: U^k_j = U^{k-1}_j) contribute
+// only sum U^2, kept from the iteration that last wrote them.  One warp per
+// problem; lane t takes the slices j = t + 1, t + 33, ... in order, then a
+// fixed shuffle tree: deterministic.  res[4 i + 0..3] = rel_l2, max, num, den.
+__global__ void increment_fused_finish_kernel(const double* __restrict__ part, int nb, int s, int k,
+                                              const int* __restrict__ map, int problems, double* __restrict__ res) {
+    const int i = blockIdx.x;
+    if (i >= problems) return;
+    const long long p = map ? map[i] : i;
+    const int lane = threadIdx.x;
+    double num = 0.0, den = 0.0, mx = 0.0;
+    for (int j = 1 + lane; j <= s; j += 32) {
+        const double* q = part + (p * s + (j - 1)) * (long long)nb * 3;
+        for (int bl = 0; bl < nb; ++bl) {
+            den += q[bl * 3 + 1];
+            if (j >= k) {
+                num += q[bl * 3];
+                mx = (q[bl * 3 + 2] != q[bl * 3 + 2]) ? q[bl * 3 + 2] : fmax(mx, q[bl * 3 + 2]);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+        const double m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = (m2 != m2) ? m2 : fmax(mx, m2);
+    }
+    if (lane == 0) {
+        res[4 * i + 0] = den > 0.0 ? sqrt(num) / sqrt(den) : sqrt(num);
+        res[4 * i + 1] = mx;
+        res[4 * i + 2] = num;
+        res[4 * i + 3] = den;
     }
 }
 
@@ -266,7 +406,12 @@ int residual_noalloc(int num_slices, int n, int precision, const void* U_new, co
 struct GraphKey {
     int k;
     std::vector<int> active;
-    bool operator<(const GraphKey& o) const { return k != o.k ? k < o.k : active < o.active; }
+    bool swapped;  // the trajectory buffers' roles (a graph holds their addresses)
+    bool operator<(const GraphKey& o) const {
+        if (k != o.k) return k < o.k;
+        if (swapped != o.swapped) return swapped < o.swapped;
+        return active < o.active;
+    }
 };
 
 struct ac_parareal {
@@ -279,6 +424,9 @@ struct ac_parareal {
     long long nn = 0;
     void* Ua = nullptr;
     void* Ub = nullptr;
+    void* Ua0 = nullptr;    // Ua as allocated (Ua and Ub swap every iteration)
+    void* big_ws = nullptr; // workspace of the two-pass fine path (n = 1024)
+    size_t big_ws_bytes = 0;
     void* Gold = nullptr;
     void* Fres = nullptr;
     void* gtmp = nullptr;   // [problems][nn] coarse output of one sweep step
@@ -319,6 +467,7 @@ namespace acpr {
 static void free_state(ac_parareal* st) {
     if (!st) return;
     for (void* ptr : {st->Ua, st->Ub, st->Gold, st->Fres, st->gtmp, st->work, st->packed, st->gsub[0], st->gsub[1],
+                      st->big_ws,
                       st->acnn_work,
                       static_cast<void*>(st->d_map), static_cast<void*>(st->d_fw), static_cast<void*>(st->d_part),
                       static_cast<void*>(st->d_res)})
@@ -368,11 +517,21 @@ static unsigned grid_for(long long total, int threads) {
     return unsigned(want < 152 * 16 ? want : 152 * 16);
 }
 
+// Blocks per problem of the fused correction (at most 1024 elements per
+// block, at most kIncBlocks blocks).
+constexpr int kIncBlocks = 64;
+static int inc_blocks(long long nn) {
+    const long long want = (nn + 1023) / 1024;
+    return int(want < kIncBlocks ? want : kIncBlocks);
+}
+
 template <typename T>
 static int launch_correct(ac_parareal* st, void* Ub, int slice, const void* g, int m, cudaStream_t stream) {
-    correct_kernel<T><<<grid_for(st->nn * m, 256), 256, 0, stream>>>(
-        static_cast<T*>(Ub), static_cast<T*>(st->Gold), static_cast<const T*>(st->Fres), static_cast<const T*>(g),
-        slice, st->s, st->nn, m, st->d_map);
+    // Ub is U^k; the other trajectory buffer holds U^{k-1}
+    const void* Uold = Ub == st->Ub ? st->Ua : st->Ub;
+    correct_inc_kernel<T><<<dim3(unsigned(inc_blocks(st->nn)), unsigned(m)), kResThreads, 0, stream>>>(
+        static_cast<T*>(Ub), static_cast<const T*>(Uold), static_cast<T*>(st->Gold),
+        static_cast<const T*>(st->Fres), static_cast<const T*>(g), slice, st->s, st->nn, st->d_map, st->d_part);
     ACPR_LAUNCH_CHECK();
     return AC_OK;
 }
@@ -457,7 +616,7 @@ static int enqueue(ac_parareal* st, int k, int m, int nwork, cudaStream_t stream
     if (st->uniform && st->p.n >= 1024) {
         // large fields: the two-pass path runs uniform launches only
         rc = fine_propagate_mapped(&st->p, m, s - k + 1, st->cp[0], st->Ua, s + 1, k - 1, st->Fres, s, k - 1,
-                                   st->d_map, stream);
+                                   st->d_map, stream, st->big_ws, st->big_ws_bytes);
     } else if (st->fine_scheme == 1) {
         rc = cn_run_work(&st->p, nwork, st->d_fw, st->Ua, st->Fres, st->cn_tol, st->cn_max_iters, stream);
     } else {
@@ -478,10 +637,9 @@ static int enqueue(ac_parareal* st, int k, int m, int nwork, cudaStream_t stream
         if ((rc = correct(st, st->Ub, n, st->gtmp, mn, stream))) return rc;
     }
     if ((rc = mark(2))) return rc;
-    // 4. increments over slices 1..s
-    rc = increment(st->p.precision, st->Ub, st->Ua, nn * (s + 1), nn * (s + 1), nn, nn * s, st->d_map, m,
-                   st->d_part, st->d_res, stream);
-    if (rc) return rc;
+    // 4. increments over slices 1..s from the partials of the corrections
+    increment_fused_finish_kernel<<<m, 32, 0, stream>>>(st->d_part, inc_blocks(nn), s, k, st->d_map, m, st->d_res);
+    ACPR_LAUNCH_CHECK();
     return mark(3);
 }
 
@@ -523,7 +681,7 @@ static int launch(ac_parareal* st, int k, cudaStream_t stream) {
     if (nwork) ACPR_CUDA(cudaMemcpyAsync(st->d_fw, st->h_fw, sizeof(int4) * nwork, cudaMemcpyHostToDevice, stream));
     int rc;
     if (st->graphs) {
-        GraphKey key{k, std::vector<int>(st->h_map, st->h_map + m)};
+        GraphKey key{k, std::vector<int>(st->h_map, st->h_map + m), st->Ua != st->Ua0};
         auto it = st->graph_cache.find(key);
         if (it == st->graph_cache.end()) {
             // capture on a private stream (the caller's may be the legacy
@@ -569,7 +727,8 @@ static int launch(ac_parareal* st, int k, cudaStream_t stream) {
 static int finish(ac_parareal* st, int k, double* l2_out, double* mx_out) {
     const int m = st->m_launched;
     if (m) ACPR_CUDA(cudaEventSynchronize(st->done));
-    int rc = tc_check_status(st->stream_launched);
+    int rc = st->work ? conv_check_status(conv_status(st->work), st->stream_launched) : AC_OK;
+    if (!rc) rc = fine_check_status(st->stream_launched);
     if (rc) return rc;
     if (st->timing && m) {
         float a = 0.f, b = 0.f, c = 0.f;
@@ -660,9 +819,13 @@ static int create(const ac_params* params, const cnn_desc* coarse, int problems,
     if (wb) ok = ok && alloc(&st->work, wb);
     const size_t pb = coarse ? cnn_packed_bytes(coarse) : 0;
     if (ok && pb) ok = alloc(&st->packed, pb);
+    if (ok && fine_big_supported(params->n, params->precision)) {
+        st->big_ws_bytes = fine_big_workspace_bytes(params->n, problems * smax);
+        ok = alloc(&st->big_ws, st->big_ws_bytes);
+    }
     ok = ok && alloc(reinterpret_cast<void**>(&st->d_map), sizeof(int) * problems) &&
          alloc(reinterpret_cast<void**>(&st->d_fw), sizeof(int4) * size_t(problems) * smax) &&
-         alloc(reinterpret_cast<void**>(&st->d_part), sizeof(double) * 3 * kResBlocksPerProblem * problems) &&
+         alloc(reinterpret_cast<void**>(&st->d_part), sizeof(double) * 3 * inc_blocks(st->nn) * problems * size_t(smax)) &&
          alloc(reinterpret_cast<void**>(&st->d_res), sizeof(double) * 4 * problems);
     ok = ok && cudaMallocHost(&st->h_map, sizeof(int) * problems) == cudaSuccess &&
          cudaMallocHost(&st->h_fw, sizeof(int4) * size_t(problems) * smax) == cudaSuccess &&
@@ -674,6 +837,7 @@ static int create(const ac_params* params, const cnn_desc* coarse, int problems,
         set_error("ac_parareal_create: device allocation failed");
         return AC_ERR_NOMEM;
     }
+    st->Ua0 = st->Ua;
     st->g.work = st->work;
     st->g.work_bytes = wb;
     st->g.packed = st->packed;
@@ -681,8 +845,11 @@ static int create(const ac_params* params, const cnn_desc* coarse, int problems,
         rc = cnn_pack_weights(&st->g, nullptr);
         if (rc) { free_state(st); return rc; }
     }
-    // zero trajectories (slices past s_p stay zero), then U[p][0] = u0[p]
-    if (cudaMemset(st->Ua, 0, traj) != cudaSuccess || cudaMemset(st->Ub, 0, traj) != cudaSuccess ||
+    // zero trajectories (slices past s_p stay zero), then U[p][0] = u0[p];
+    // the conv workspace's status header starts at zero
+    if ((st->work && cudaMemset(st->work, 0, kConvHeader) != cudaSuccess) ||
+        cudaMemset(st->d_part, 0, sizeof(double) * 3 * inc_blocks(st->nn) * problems * size_t(smax)) != cudaSuccess ||
+        cudaMemset(st->Ua, 0, traj) != cudaSuccess || cudaMemset(st->Ub, 0, traj) != cudaSuccess ||
         cudaMemcpy2D(st->Ua, fb * (smax + 1), u0, fb, fb, problems, cudaMemcpyDeviceToDevice) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
         set_error("ac_parareal_create: initialisation failed: %s", cudaGetErrorString(cudaGetLastError()));

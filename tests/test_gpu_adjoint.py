@@ -94,3 +94,44 @@ def test_energy_gradient_float32_close_to_float64():
                                   dev(u0, torch.float32))
     rel = (torch.linalg.norm(g32.double() - g64) / torch.linalg.norm(g64)).item()
     assert rel < 5e-4
+
+
+def _energy_torch(u, eps, h):
+    """E_h(u) = h^2 sum eps^2/2 (|D+x u|^2 + |D+y u|^2) + (u^2 - 1)^2 / 4 on the
+    periodic grid (Sec. 2, Eq. energy, forward differences), in torch so that
+    autograd differentiates it."""
+    dx = (torch.roll(u, -1, dims=-2) - u) / h
+    dy = (torch.roll(u, -1, dims=-1) - u) / h
+    return h * h * (0.5 * eps * eps * (dx * dx + dy * dy) + 0.25 * (u * u - 1.0) ** 2).sum()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_fine_solve_autograd_function(variant):
+    """torch.autograd.Function over 100 fine steps with a checkpoint every 32
+    (segments 32, 32, 32, 4, each recomputed in the backward pass), float64:
+    (1) an arbitrary scalar loss of u^N, sum w u^N + 0.5 |u^N|^2, against
+    central differences (h = 1e-6) along random directions, 1e-7 relative;
+    (2) the energy loss E_h(u^N) against the oracle's gradient through the
+    solve (every state stored, no checkpoints), 1e-10 relative."""
+    n, steps, every, eps, dt = 32, 100, 32, 0.05, 1e-3
+    fp = G.FineParams(n, eps, 2.0, dt, variant=variant, precision=G.AC_F64)
+    u0 = I.random_field(n, seed=11, zero_mean=bool(variant))[None]
+    w = dev(np.random.default_rng(12).standard_normal((1, n, n)))
+
+    def loss(x):
+        uN = G.fine_solve(x, fp, steps, every)
+        return (w * uN).sum() + 0.5 * (uN * uN).sum()
+
+    x = dev(u0).requires_grad_(True)
+    loss(x).backward()
+    g = x.grad.detach()
+    hh = 1e-6
+    for k in range(3):
+        d = dev(np.random.default_rng(20 + k).standard_normal((1, n, n)))
+        with torch.no_grad():
+            fd = (loss(dev(u0) + hh * d) - loss(dev(u0) - hh * d)).item() / (2 * hh)
+        assert abs(fd - (g * d).sum().item()) < 1e-7 * max(1.0, abs(fd))
+    x = dev(u0).requires_grad_(True)
+    _energy_torch(G.fine_solve(x, fp, steps, every), eps, 1.0 / n).backward()
+    ref = O.energy_gradient_through_solve(O.params(n, eps, 2.0, dt, variant), steps, u0[0])
+    assert np.abs(x.grad[0].cpu().numpy() - ref).max() < 1e-10 * np.abs(ref).max()

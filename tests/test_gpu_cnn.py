@@ -156,3 +156,27 @@ def test_cnn_bf16_mass_shift_trained_256():
     assert np.median(err) < 1e-3 * scale + 1e-7
     for p in range(2):
         assert abs(got[p].mean() - u[p].astype(np.float64).mean()) < 1e-6
+
+
+def test_bounded_wait_timeout_is_reported_and_cleared():
+    """Failure detection without a fault: the test hook makes the persistent
+    tensor-core kernel's MMA issuer wait on an mbarrier that nothing arrives
+    on, with a short poll limit.  The kernel gives up, drains its copies,
+    frees its tensor memory and stores the code in the workspace status word;
+    cnn_coarse_step reports AC_ERR_TIMEOUT and clears the word, and the next
+    call (hook off) is correct again: equal to a fresh net's output."""
+    n, L, C = 256, 4, 32
+    w, b = I.cnn_weights(L, C, seed=7, sigma=0.05)
+    w32, b32 = w.astype(np.float32), b.astype(np.float32)
+    net = G.CoarseNet(L, C, w32, b32, act=1, precision=G.AC_F32)
+    u = torch.tensor(np.stack([I.random_field(n, seed=s) for s in range(2)]), dtype=torch.float32, device="cuda")
+    G.ac_test_conv_stall(2000)
+    try:
+        with pytest.raises(G.AcprError, match="AC_ERR_TIMEOUT"):
+            G.cnn_coarse_step(net, u)
+    finally:
+        G.ac_test_conv_stall(0)
+    G.ac_conv_status(net._work)  # cleared: no error now
+    got = G.cnn_coarse_step(net, u)
+    ref = G.cnn_coarse_step(G.CoarseNet(L, C, w32, b32, act=1, precision=G.AC_F32), u)
+    assert torch.equal(got, ref)

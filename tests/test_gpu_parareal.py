@@ -247,3 +247,31 @@ def test_full_size_unconverged_iterates_match_oracle():
             assert err.max() < 5e-3
             assert rel < 2e-3
             assert abs(incs[k] - ref["res_l2"][-1]) < 5e-2 * ref["res_l2"][-1]
+
+
+@pytest.mark.parametrize("prec", [G.AC_F32, G.AC_F64])
+def test_fused_increment_equals_standalone_residual(prec):
+    """The corrections leave the increment's partial sums of the slices they
+    write; slices frozen at iteration k contribute only sum U^2.  After every
+    iteration the driver's increments must equal parareal_residual (a
+    separate float64 pass over both trajectories) on the same trajectories:
+    relative L2 to 1e-12 and the sup norm exactly (float32 fields: the
+    differences are split exactly into float pairs)."""
+    n, s, c = 64, 6, 30
+    dt_ = torch.float64 if prec == G.AC_F64 else torch.float32
+    fp = G.FineParams(n, 0.04, 2.0, 1e-4, variant=G.AC_MASS_CONSERVING, precision=prec)
+    wt, bs = I.cnn_weights(4, 16, seed=0)
+    net = G.CoarseNet(4, 16, wt, bs, act=1, precision=prec)
+    u0 = torch.tensor(np.stack([I.random_field(n, 7 + p, zero_mean=True) for p in range(3)]), dtype=dt_,
+                      device="cuda")
+    pr = G.Parareal(fp, net, u0, s, c)
+    pr.enable_graphs(True)
+    pr.iterate()  # k = 0
+    for k in range(1, 5):
+        prev = pr.trajectory().clone()
+        l2, mx = pr.iterate()
+        cur = pr.trajectory()
+        for p in range(3):
+            rl2, rmx = G.parareal_residual(cur[p].contiguous(), prev[p].contiguous())
+            assert abs(l2[p] - rl2) <= 1e-12 * rl2, (k, p)
+            assert mx[p] == rmx, (k, p)
