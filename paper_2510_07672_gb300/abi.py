@@ -62,7 +62,8 @@ EXPORTS = ["ac_last_error", "ac_fine_supported", "ac_fine_step", "ac_fine_propag
            "ac_fine_variant_count", "ac_fine_variant_name", "ac_fine_get_variant", "ac_fine_set_variant",
            "ac_fine_autotune", "ac_fine_propagate_work", "ac_fine_workspace_bytes", "ac_fine_propagate_slices_ws", "ac_fine_trajectory", "ac_fine_adjoint", "ac_energy", "ac_energy_grad",
            "ac_energy_gradient_workspace", "ac_energy_gradient_ic",
-           "ac_conv_status", "ac_test_conv_stall", "cnn_train_bytes", "cnn_forward_train", "cnn_backward", "cnn_adam_step", "mse_loss_grad",
+           "ac_conv_status", "ac_test_conv_stall", "cnn_conv_variant_count", "cnn_conv_variant_shape",
+           "cnn_conv_set_variant", "cnn_conv_get_variant", "cnn_autotune", "cnn_train_bytes", "cnn_forward_train", "cnn_backward", "cnn_adam_step", "mse_loss_grad",
            "acnn_param_count", "acnn_create", "acnn_destroy", "acnn_work_bytes", "acnn_forward", "acnn_train_bytes",
            "acnn_forward_train", "acnn_backward", "loss_acn_work_bytes", "loss_acn", "acnn_adam_step",
            "acnn_train_alg1", "acnn_train_alg1_bytes", "ac_parareal_set_coarse_acnn",
@@ -132,6 +133,11 @@ def load(build_if_missing: bool = True):
         L.ac_energy_gradient_workspace.restype = C.c_size_t
         L.ac_energy_gradient_ic.argtypes = [P(ac_params), I, I, S, S, S, C.c_size_t, S]
         L.ac_conv_status.argtypes = [S, S]
+        L.cnn_conv_variant_count.argtypes = [I, I]
+        L.cnn_conv_variant_shape.argtypes = [I, I, I, P(I), P(I), P(I)]
+        L.cnn_conv_set_variant.argtypes = [I, I, I]
+        L.cnn_conv_get_variant.argtypes = [I, I]
+        L.cnn_autotune.argtypes = [P(cnn_desc), I, I, S, S, P(C.c_float), S]
         L.ac_test_conv_stall.argtypes = [I]
         L.cnn_train_bytes.argtypes = [P(cnn_desc), I, I]
         L.cnn_train_bytes.restype = C.c_size_t
@@ -773,6 +779,37 @@ def cnn_coarse_step(net: CoarseNet, u_in, u_out=None, stream=None):
     _check(load().cnn_coarse_step(C.byref(d), n, batch, _dev(u_in, dt, "u_in"), _dev(u_out, dt, "u_out"),
                                   _stream(stream)))
     return u_out
+
+
+def cnn_conv_variants(n: int, channels: int):
+    """[(M-tiles per row segment, rows per unit, ring depth)] of the
+    persistent tensor-core conv for (n, channels)."""
+    L = load()
+    out = []
+    for i in range(L.cnn_conv_variant_count(int(n), int(channels))):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        _check(L.cnn_conv_variant_shape(int(n), int(channels), i, C.byref(a), C.byref(b), C.byref(c)))
+        out.append((a.value, b.value, c.value))
+    return out
+
+
+def cnn_conv_set_variant(n: int, channels: int, index: int):
+    _check(load().cnn_conv_set_variant(int(n), int(channels), int(index)))
+
+
+def cnn_autotune(net, u_in, u_out=None, stream=None):
+    """Time every conv tile shape on this problem, keep the fastest; returns
+    {shape: ms per call} and the chosen index."""
+    n = u_in.shape[-1]
+    batch = u_in.numel() // (n * n)
+    net.ensure_work(n, batch)
+    u_out = u_out if u_out is not None else u_in.new_empty(u_in.shape)
+    shapes = cnn_conv_variants(n, net.channels)
+    ms = (C.c_float * max(len(shapes), 1))()
+    d = net.desc()
+    _check(load().cnn_autotune(C.byref(d), n, batch, _dev(u_in, None, "u_in"), _dev(u_out, None, "u_out"), ms,
+                               _stream(stream)))
+    return {shapes[i]: ms[i] for i in range(len(shapes))}, int(load().cnn_conv_get_variant(n, net.channels))
 
 
 def ac_conv_status(workspace, stream=None):

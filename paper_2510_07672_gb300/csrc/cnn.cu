@@ -78,41 +78,53 @@ __global__ void conv_f64_kernel(const double* __restrict__ in, double* __restric
 // ------------------------------------------------------------ bf16 / f32 --
 // First layer: float32 field -> bf16 chunked activations (K = 9 on CUDA cores).
 // The bf16-rounded weights and the biases are staged in shared memory once per
-// block (every thread reads the same entry: broadcast).
-template <int C>
+// block (every thread reads the same entry: broadcast).  A thread computes two
+// horizontally adjacent pixels (one weight load serves both), each output as
+// the sum over taps in order, then the bias.
+constexpr int kFirstPx = 2;
+template <int C, int ACT>
 __global__ void conv_first_bf16_kernel(const float* __restrict__ u, __nv_bfloat16* __restrict__ act,
                                        const float* __restrict__ W, const float* __restrict__ bias,
-                                       int batch, int n, int act_kind, BatchIO io) {
+                                       int batch, int n, BatchIO io) {
     __shared__ float ws[C * 9], bs[C];
     for (int i = threadIdx.x; i < C * 9; i += blockDim.x) ws[i] = bf16r(W[i]);
     for (int i = threadIdx.x; i < C; i += blockDim.x) bs[i] = bias[i];
     __syncthreads();
-    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long pix = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * kFirstPx;
     const long long nn = (long long)n * n;
     if (pix >= nn * batch) return;
     const int lg = __ffs(n) - 1;  // n is a power of two
     const int b = int(pix >> (2 * lg));
     const int y = int(pix >> lg) & (n - 1), x = int(pix) & (n - 1);
     const float* f = u + bsel(io.in_map, b) * io.in_bs;
-    float v[9];
+    float v[3][kFirstPx + 2];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int e = 0; e < 3; ++e) v[a * 3 + e] = bf16r(f[(long long)wrap(y + a - 1, n) * n + wrap(x + e - 1, n)]);
+        for (int e = 0; e < kFirstPx + 2; ++e)
+            v[a][e] = bf16r(f[(long long)wrap(y + a - 1, n) * n + wrap(x + e - 1, n)]);
 #pragma unroll
     for (int kc = 0; kc < C / 8; ++kc) {
-        __align__(16) __nv_bfloat16 o8[8];
+        __align__(16) __nv_bfloat16 o8[kFirstPx][8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int o = kc * 8 + i;
-            float s = 0.f;
+            float s[kFirstPx];
 #pragma unroll
-            for (int t = 0; t < 9; ++t) s = fmaf(ws[o * 9 + t], v[t], s);
-            s += bs[o];
-            o8[i] = __float2bfloat16_rn(act_apply<float>(act_kind, s));
+            for (int px = 0; px < kFirstPx; ++px) s[px] = 0.f;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const float wt = ws[o * 9 + t];
+#pragma unroll
+                for (int px = 0; px < kFirstPx; ++px) s[px] = fmaf(wt, v[t / 3][px + t % 3], s[px]);
+            }
+#pragma unroll
+            for (int px = 0; px < kFirstPx; ++px) o8[px][i] = __float2bfloat16_rn(act_c<ACT>(s[px] + bs[o]));
         }
-        *reinterpret_cast<uint4*>(act + ((((long long)b * (C / 8) + kc) * nn) + (pix & (nn - 1))) * 8) =
-            *reinterpret_cast<const uint4*>(o8);
+#pragma unroll
+        for (int px = 0; px < kFirstPx; ++px)
+            *reinterpret_cast<uint4*>(act + ((((long long)b * (C / 8) + kc) * nn) + ((pix + px) & (nn - 1))) * 8) =
+                *reinterpret_cast<const uint4*>(o8[px]);
     }
 }
 
@@ -249,6 +261,47 @@ static size_t last_smem(int n) {
     return sizeof(float) * (C * 9 + kLastThreads) + sizeof(uint4) * size_t(nr + 2) * (C / 8) * (w + 2);
 }
 
+// Last layer C -> 1 from the nine tap maps of the fused last hidden layer:
+// z = (sum over taps (dy, dx) of maps[tap] at (y + dy - 1, x + dx - 1), wrapped)
+// + bias, out = z (+ u), and the block's float64 sum of z when zpart != NULL
+// (one block = last_pixels(n) pixels of one field, as conv_last_bf16_kernel).
+__global__ void __launch_bounds__(kLastThreads)
+last_stencil_kernel(const float* __restrict__ maps, float* __restrict__ out, const float* __restrict__ bias,
+                    const float* __restrict__ u, int batch, int n, int residual, BatchIO io,
+                    double* __restrict__ zpart) {
+    __shared__ float zsh[kLastThreads];
+    const long long nn = (long long)n * n;
+    const int ppb = int(nn < kLastThreads ? nn : kLastThreads);
+    const long long p0 = (long long)blockIdx.x * ppb;
+    const int b = int(p0 / nn);
+    const int tp = threadIdx.x;
+    const bool valid = tp < ppb;
+    float zs = 0.f;
+    if (valid) {
+        const long long q = p0 % nn + tp;
+        const int y = int(q / n), x = int(q % n);
+        const float* mb = maps + (long long)b * 9 * nn;
+        float acc = 0.f;
+#pragma unroll
+        for (int t = 0; t < 9; ++t)
+            acc += mb[t * nn + (long long)wrap(y + t / 3 - 1, n) * n + wrap(x + t % 3 - 1, n)];
+        zs = acc + bias[0];
+        float z = zs;
+        if (residual) z += u[bsel(io.in_map, b) * io.in_bs + q];
+        out[bsel(io.out_map, b) * io.out_bs + q] = z;
+    }
+    if (zpart) {
+        zsh[tp] = valid ? zs : 0.f;
+        __syncthreads();
+        if (tp < 32) {
+            double v = 0.0;
+            for (int i = tp; i < ppb; i += 32) v += double(zsh[i]);
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (tp == 0) zpart[blockIdx.x] = v;
+        }
+    }
+}
+
 // mACNN mass shift from the stack-output sums: out += -(sum z) / n^2 per
 // field.  Grid (chunks, batch); each block forms the field's sum from its
 // `bpf` block partials in a fixed order (deterministic), then shifts a chunk.
@@ -372,6 +425,28 @@ int last_layer_bf16(const cnn_desc* d, int n, int batch, const __nv_bfloat16* a,
     }
 }
 
+static int last_stencil_io(const cnn_desc* d, int n, int batch, const float* maps, float* out, const float* Bv,
+                           const float* u, const BatchIO& io, double* zpart, cudaStream_t st) {
+    const int ppb = last_pixels(n);
+    const unsigned blocks = unsigned((long long)n * n * batch / ppb);
+    last_stencil_kernel<<<blocks, kLastThreads, 0, st>>>(maps, out, Bv, u, batch, n, d->residual, io,
+                                                         d->mass_fix ? zpart : nullptr);
+    ACPR_LAUNCH_CHECK();
+    if (d->mass_fix) {
+        const int bpf = int((long long)n * n / ppb);
+        const long long chunks = ((long long)n * n + kMassThreads * 8 - 1) / (kMassThreads * 8);
+        mass_apply_kernel<<<dim3(unsigned(chunks), unsigned(batch)), kMassThreads, 0, st>>>(out, zpart, bpf, n, io);
+        ACPR_LAUNCH_CHECK();
+    }
+    return AC_OK;
+}
+
+int last_stencil_f32(const cnn_desc* d, int n, int batch, const float* maps, float* out, const float* Bv,
+                     const float* u, double* zpart, cudaStream_t st) {
+    BatchIO io{nullptr, nullptr, (long long)n * n, (long long)n * n, 1, 1};
+    return last_stencil_io(d, n, batch, maps, out, Bv, u, io, zpart, st);
+}
+
 template <int C>
 static int run_f32(const cnn_desc* d, int n, int batch, const float* u, float* out, const BatchIO& io,
                    cudaStream_t st) {
@@ -385,10 +460,24 @@ static int run_f32(const cnn_desc* d, int n, int batch, const float* u, float* o
     int* status = conv_status(d->work);
     __nv_bfloat16* a0 = reinterpret_cast<__nv_bfloat16*>(wb);
     __nv_bfloat16* a1 = a0 + act_elems;
-    conv_first_bf16_kernel<C><<<blocks, threads, 0, st>>>(u, a0, W, Bv, batch, n, d->act, io);
+    const unsigned fblocks = unsigned((pixels / kFirstPx + threads - 1) / threads);
+    if (d->act == AC_ACT_TANH)
+        conv_first_bf16_kernel<C, AC_ACT_TANH><<<fblocks, threads, 0, st>>>(u, a0, W, Bv, batch, n, io);
+    else
+        conv_first_bf16_kernel<C, AC_ACT_GELU><<<fblocks, threads, 0, st>>>(u, a0, W, Bv, batch, n, io);
     ACPR_LAUNCH_CHECK();
     size_t woff = size_t(C) * 9, boff = C;
+    double* zpart = reinterpret_cast<double*>(wb + 2 * act_elems * sizeof(__nv_bfloat16));
     for (int l = 1; l < d->layers - 1; ++l) {
+        if (l == d->layers - 2 && hidden_last_fused_supported(n, C)) {
+            // the last hidden layer also forms the last layer's nine tap maps
+            // (in the other activation buffer: 36 B per pixel <= 2 C B)
+            float* maps = reinterpret_cast<float*>(a1);
+            const float* w_last = W + woff + size_t(C) * C * 9;
+            int rc = hidden_last_fused(d, l, n, batch, a0, nullptr, Bv + boff, w_last, maps, status, st);
+            if (rc) return rc;
+            return last_stencil_io(d, n, batch, maps, out, Bv + boff + C, u, io, zpart, st);
+        }
         int rc = hidden_layer_bf16(d, l, n, batch, a0, a1, W + woff, Bv + boff, status, st);
         if (rc == AC_ERR_UNSUPPORTED) {
             conv_hidden_bf16_cc_kernel<C><<<blocks, threads, 0, st>>>(a0, a1, W + woff, Bv + boff, batch, n, d->act);
@@ -400,7 +489,6 @@ static int run_f32(const cnn_desc* d, int n, int batch, const float* u, float* o
         boff += C;
         __nv_bfloat16* t = a0; a0 = a1; a1 = t;
     }
-    double* zpart = reinterpret_cast<double*>(wb + 2 * act_elems * sizeof(__nv_bfloat16));
     return last_layer_f32<C>(d, n, batch, a0, out, W + woff, Bv + boff, u, io, zpart, st);
 }
 
@@ -521,6 +609,58 @@ extern "C" int cnn_coarse_step(const cnn_desc* desc, int n, int batch, const voi
     // a bounded wait of the tensor-core kernels that gave up left its code in
     // the workspace header: report it here (this synchronises the stream)
     return acpr::conv_check_status_uncaptured(acpr::conv_status(desc->work), st);
+}
+
+extern "C" int cnn_conv_variant_count(int n, int channels) { return acpr::conv_variant_count(n, channels); }
+
+extern "C" int cnn_conv_variant_shape(int n, int channels, int index, int* mtiles, int* rows, int* ring) {
+    using namespace acpr;
+    ACPR_CHECK_ARG(mtiles && rows && ring, "null output");
+    const int rc = conv_variant_describe(n, channels, index, mtiles, rows, ring);
+    if (rc) set_error("cnn_conv_variant_shape: index %d out of range", index);
+    return rc;
+}
+
+extern "C" int cnn_conv_set_variant(int n, int channels, int index) {
+    return acpr::conv_set_variant(n, channels, index);
+}
+
+extern "C" int cnn_conv_get_variant(int n, int channels) { return acpr::conv_get_variant(n, channels); }
+
+extern "C" int cnn_autotune(const cnn_desc* desc, int n, int batch, const void* u_in, void* u_out, float* ms_out,
+                            acpr_stream stream) {
+    using namespace acpr;
+    int rc = check_cnn(desc);
+    if (rc) return rc;
+    ACPR_CHECK_ARG(desc->precision == AC_F32, "cnn_autotune: the tensor-core path is AC_F32 only");
+    ACPR_CHECK_ARG(batch >= 1 && u_in && u_out, "bad autotune arguments");
+    const int count = conv_variant_count(n, desc->channels);
+    ACPR_CHECK_ARG(count > 0, "cnn_autotune: no persistent tile shape for n=%d, C=%d", n, desc->channels);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    ACPR_CUDA(cudaEventCreate(&e0));
+    ACPR_CUDA(cudaEventCreate(&e1));
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int v = 0; v < count && !rc; ++v) {
+        conv_set_variant(n, desc->channels, v);
+        rc = coarse_step(desc, n, batch, u_in, u_out, st);  // warm-up
+        if (rc) break;
+        ACPR_CUDA(cudaEventRecord(e0, st));
+        for (int rep = 0; rep < 3 && !rc; ++rep) rc = coarse_step(desc, n, batch, u_in, u_out, st);
+        ACPR_CUDA(cudaEventRecord(e1, st));
+        ACPR_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        ACPR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        ms /= 3.f;
+        if (ms_out) ms_out[v] = ms;
+        if (ms < best_ms) { best_ms = ms; best = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    conv_set_variant(n, desc->channels, rc ? -1 : best);
+    if (!rc) rc = conv_check_status(conv_status(desc->work), st);
+    return rc;
 }
 
 extern "C" int ac_conv_status(void* workspace, acpr_stream stream) {

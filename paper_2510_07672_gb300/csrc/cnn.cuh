@@ -44,6 +44,14 @@ __device__ __forceinline__ T act_apply(int act, T x) {
     return act_apply_gelu(x);
 }
 
+// The activation fixed at compile time (kernels instantiated per activation,
+// so that no code of the other one sits in their loops).
+template <int ACT>
+__device__ __forceinline__ float act_c(float x) {
+    if constexpr (ACT == AC_ACT_TANH) return tanhf(x);
+    else return act_apply_gelu(x);
+}
+
 int check_cnn(const cnn_desc* d);
 int coarse_step(const cnn_desc* d, int n, int batch, const void* u_in, void* u_out, cudaStream_t st);
 // Batch entry b reads the field at u_in + in_map[b] * in_bs and writes the
@@ -85,6 +93,16 @@ __device__ __forceinline__ T act_grad(int act, T x) {
     return act_grad_gelu(x);
 }
 
+template <int ACT>
+__device__ __forceinline__ float act_grad_c(float x) {
+    if constexpr (ACT == AC_ACT_TANH) {
+        const float t = tanhf(x);
+        return 1.0f - t * t;
+    } else {
+        return act_grad_gelu(x);
+    }
+}
+
 // Every conv workspace (cnn_desc.work and the training workspace) starts
 // with a header of kConvHeader bytes whose first int is the status word of
 // the tensor-core kernels: a bounded wait that gives up stores a nonzero code
@@ -105,6 +123,29 @@ void set_test_stall(int polls);
 int hidden_layer_bf16(const cnn_desc* d, int l, int n, int batch, const __nv_bfloat16* in,
                       __nv_bfloat16* out, const float* w_master, const float* bias, int* status, cudaStream_t st,
                       float* zsave = nullptr);
+
+// The last hidden layer (l = layers - 2) fused with the last layer's
+// per-pixel projection (persistent tensor-core kernel, C = 32 or 64, n a
+// multiple of 128): maps [batch][9][n][n] float32 receives, per pixel, the
+// nine tap sums of W_last (bf16-rounded) with the layer's bf16 activations;
+// act_out gets the activations and zsave the pre-activations only when zsave
+// is not NULL (training).  AC_ERR_UNSUPPORTED for other shapes.
+// Tile shapes of the persistent tensor-core kernel for (n, C) that a tuner
+// may choose (M-tiles per row segment, rows per unit, input-ring depth).
+int conv_variant_count(int n, int C);
+int conv_variant_describe(int n, int C, int index, int* mg, int* ty, int* ring);
+int conv_set_variant(int n, int C, int index);  // -1: automatic
+int conv_get_variant(int n, int C);
+
+bool hidden_last_fused_supported(int n, int C);
+int hidden_last_fused(const cnn_desc* d, int l, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* act_out,
+                      const float* bias, const float* w_last, float* maps, int* status, cudaStream_t st,
+                      float* zsave = nullptr);
+// The last layer from those maps: out = bias + sum_tap maps[tap](shifted) (+ u
+// with the residual), the mass-shift block partials into zpart as
+// last_layer_bf16, then (d->mass_fix) the shift itself.
+int last_stencil_f32(const cnn_desc* d, int n, int batch, const float* maps, float* out, const float* Bv,
+                     const float* u, double* zpart, cudaStream_t st);
 
 // Backward through hidden layer l+1 into layer l's pre-activation gradient:
 // dz_out = bf16(conv(dz_next, w_t) * act'(z_prev)), w_t from pack_hidden_t.

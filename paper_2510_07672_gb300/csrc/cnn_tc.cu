@@ -130,13 +130,19 @@ static TcShape pick_shape(int n, int C) {
 // bf16(acc * act'(zio)) (backward through a hidden layer: acc is the
 // transposed-and-flipped conv of the next layer's gradient, zio the saved
 // pre-activation of this layer's input).  zio is float32 [f][C/8][n][n][8].
-enum { kFwd = 0, kDgrad = 1 };
+// kFwdLast (persistent kernel, the last hidden layer): as kFwd, and the
+// epilogue also projects each pixel's bf16 activations onto the last
+// layer's nine taps, maps[f][tap][pixel] = sum_c W_last[tap][c] a(pixel, c)
+// (float32, bf16-rounded weights, channels in order); the C -> 1 conv is then
+// a nine-point stencil of these maps (last_stencil).  The activations
+// themselves are stored only when zio != NULL (training needs them).
+enum { kFwd = 0, kDgrad = 1, kFwdLast = 2 };
 
-template <int C>
+template <int C, int ACT>
 __global__ void __launch_bounds__(kTcThreads)
 conv_hidden_tc_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ out,
                       const __nv_bfloat16* __restrict__ wpk, const float* __restrict__ bias, int n, int TY,
-                      int n_mt, int plane_px, int ncols, int act, int mode, float* __restrict__ zio,
+                      int n_mt, int plane_px, int ncols, int mode, float* __restrict__ zio,
                       int* __restrict__ status) {
     constexpr int KC = C / 8;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -232,7 +238,7 @@ conv_hidden_tc_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __res
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
                             z8[i] = __uint_as_float(v[i]) + __ldg(bias + kc * 8 + i);
-                            o8[i] = __float2bfloat16_rn(act_apply<float>(act, z8[i]));
+                            o8[i] = __float2bfloat16_rn(act_c<ACT>(z8[i]));
                         }
                         if (zio) {
                             reinterpret_cast<float4*>(zio + off)[0] = *reinterpret_cast<const float4*>(z8);
@@ -244,7 +250,7 @@ conv_hidden_tc_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __res
                         const float zz[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
 #pragma unroll
                         for (int i = 0; i < 8; ++i)
-                            o8[i] = __float2bfloat16_rn(__uint_as_float(v[i]) * act_grad<float>(act, zz[i]));
+                            o8[i] = __float2bfloat16_rn(__uint_as_float(v[i]) * act_grad_c<ACT>(zz[i]));
                     }
                     *reinterpret_cast<uint4*>(out + off) = *reinterpret_cast<const uint4*>(o8);
                 }
@@ -294,21 +300,26 @@ struct PShape {
     size_t smem = 0;
 };
 
-static PShape p_shape(int n, int C) {
+// Tile shape: mg = M-tiles per row segment (0: automatic), ring_mode = depth
+// of the input-row ring (0: one unit of prefetch, 2 TY + 2 rows; 1: no
+// prefetch, TY + 2; 2: as deep as shared memory allows, up to kPMaxRing).
+static PShape p_shape_with(int n, int C, int mg, int ring_mode) {
     PShape s;
     if (n < 128 || n % 128) return s;
     // C = 64 keeps one M-tile per row so that a ring slot stays small
-    s.MG = (C >= 64 || n < 256) ? 1 : 2;
+    s.MG = mg ? mg : ((C >= 64 || n < 256) ? 1 : 2);
+    if (s.MG < 1 || s.MG > 2 || (s.MG == 2 && (C >= 64 || n < 256))) return PShape{};
     s.CW = 128 * s.MG;
     s.TY = kPStageCols / (s.MG * C);
     if (s.TY < 1 || n % s.TY) return PShape{};
     s.slot_bytes = uint32_t(C / 8) * uint32_t(s.CW + 2) * 16u;
     const size_t wbytes = size_t(9) * C * C * 2;
-    const size_t ctrl = 1024;
+    const size_t ctrl = 4096;  // PCtl
     const size_t avail = size_t(227) * 1024 - wbytes - ctrl;
     int ring = int(avail / s.slot_bytes);
     if (ring > kPMaxRing) ring = kPMaxRing;
-    if (ring > 2 * s.TY + 2) ring = 2 * s.TY + 2;  // one unit of prefetch is enough
+    if (ring_mode == 0 && ring > 2 * s.TY + 2) ring = 2 * s.TY + 2;  // one unit of prefetch
+    if (ring_mode == 1 && ring > s.TY + 2) ring = s.TY + 2;
     if (ring < s.TY + 2) return PShape{};
     s.RING = ring;
     s.smem = wbytes + size_t(ring) * s.slot_bytes + ctrl;
@@ -316,6 +327,78 @@ static PShape p_shape(int n, int C) {
     // the CTAs' TMEM stages (all 512 columns) never contend
     if (s.smem < size_t(116) * 1024) s.smem = size_t(116) * 1024;
     return s;
+}
+
+// Tile shapes a tuner may pick, per (channels, log2 n): index into
+// conv_variants() (-1: automatic).
+namespace {
+int g_conv_pick[3][11] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
+                          {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
+                          {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1}};
+int cidx(int C) { return C == 16 ? 0 : (C == 32 ? 1 : 2); }
+int lg2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+struct ConvVariant { int mg, ring_mode; };
+constexpr ConvVariant kConvVariants[] = {{0, 0}, {1, 0}, {2, 0}, {1, 1}, {2, 1}, {1, 2}, {2, 2}};
+constexpr int kConvVariantCount = int(sizeof(kConvVariants) / sizeof(kConvVariants[0]));
+}  // namespace
+
+// The valid, distinct shapes for (n, C), in kConvVariants order.
+static int conv_variants(int n, int C, int* out) {
+    int cnt = 0;
+    PShape seen[kConvVariantCount];
+    for (int i = 0; i < kConvVariantCount; ++i) {
+        const PShape s = p_shape_with(n, C, kConvVariants[i].mg, kConvVariants[i].ring_mode);
+        if (!s.RING) continue;
+        bool dup = false;
+        for (int k = 0; k < cnt; ++k) dup = dup || (seen[k].MG == s.MG && seen[k].RING == s.RING);
+        if (dup) continue;
+        seen[cnt] = s;
+        out[cnt++] = i;
+    }
+    return cnt;
+}
+
+static PShape p_shape(int n, int C) {
+    const int pick = (C == 16 || C == 32 || C == 64) && n >= 1 && n <= 1024 ? g_conv_pick[cidx(C)][lg2(n)] : -1;
+    if (pick >= 0) {
+        int idx[kConvVariantCount];
+        const int cnt = conv_variants(n, C, idx);
+        if (pick < cnt) {
+            const ConvVariant v = kConvVariants[idx[pick]];
+            return p_shape_with(n, C, v.mg, v.ring_mode);
+        }
+    }
+    return p_shape_with(n, C, 0, 0);
+}
+
+int conv_variant_count(int n, int C) {
+    if (!(C == 16 || C == 32 || C == 64) || n < 1 || n > 1024) return 0;
+    int idx[kConvVariantCount];
+    return conv_variants(n, C, idx);
+}
+
+int conv_variant_describe(int n, int C, int index, int* mg, int* ty, int* ring) {
+    int idx[kConvVariantCount];
+    const int cnt = conv_variant_count(n, C) ? conv_variants(n, C, idx) : 0;
+    if (index < 0 || index >= cnt) return AC_ERR_ARG;
+    const PShape s = p_shape_with(n, C, kConvVariants[idx[index]].mg, kConvVariants[idx[index]].ring_mode);
+    *mg = s.MG;
+    *ty = s.TY;
+    *ring = s.RING;
+    return AC_OK;
+}
+
+int conv_set_variant(int n, int C, int index) {
+    ACPR_CHECK_ARG(C == 16 || C == 32 || C == 64, "channels must be 16, 32 or 64");
+    ACPR_CHECK_ARG(n >= 1 && n <= 1024 && (n & (n - 1)) == 0, "n must be a power of two <= 1024");
+    ACPR_CHECK_ARG(index >= -1 && index < conv_variant_count(n, C), "variant %d out of range", index);
+    g_conv_pick[cidx(C)][lg2(n)] = index;
+    return AC_OK;
+}
+
+int conv_get_variant(int n, int C) {
+    if (!(C == 16 || C == 32 || C == 64) || n < 1 || n > 1024) return -1;
+    return g_conv_pick[cidx(C)][lg2(n)];
 }
 
 struct PCtl {
@@ -329,6 +412,7 @@ struct PCtl {
     uint32_t tmem;
     int abort;
     alignas(16) float bias[64];
+    alignas(16) float wl[64 * 9];  // kFwdLast: bf16-rounded last-layer weights [kc][tap][8]
 };
 
 __device__ __forceinline__ bool p_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
@@ -343,12 +427,13 @@ __device__ __forceinline__ bool p_wait(uint64_t* bar, uint32_t parity, volatile 
     return false;
 }
 
-template <int C, int MG>
+template <int C, int MG, int ACT>
 __global__ void __launch_bounds__(kPThreads, 1)
 conv_hidden_tc_persistent(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ out,
                           const __nv_bfloat16* __restrict__ wpk, const float* __restrict__ bias, int n,
-                          int batch, int RING, uint32_t slot_bytes, int act, int mode, float* __restrict__ zio,
-                          int* __restrict__ status, int stall) {
+                          int batch, int RING, uint32_t slot_bytes, int mode, float* __restrict__ zio,
+                          int* __restrict__ status, int stall, const float* __restrict__ wlast,
+                          float* __restrict__ maps) {
     constexpr int KC = C / 8;
     constexpr int TY = kPStageCols / (MG * C);
     constexpr int NACC = TY * MG;
@@ -383,7 +468,14 @@ conv_hidden_tc_persistent(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* _
         ctl->abort = 0;
         tc::fence_mbar_init();
     }
-    if (tid < C) ctl->bias[tid] = (mode == kFwd) ? bias[tid] : 0.f;
+    static_assert(sizeof(PCtl) <= 4096, "control block");
+    if (tid < C) ctl->bias[tid] = (mode != kDgrad) ? bias[tid] : 0.f;
+    if (mode == kFwdLast)
+        for (int e = tid; e < 9 * C; e += blockDim.x) {
+            // wl[kc][tap][i] = bf16(W_last[0][kc 8 + i][tap])
+            const int i = e % 8, tap = (e / 8) % 9, kc = e / 72;
+            ctl->wl[e] = bf16r(wlast[(kc * 8 + i) * 9 + tap]);
+        }
     __syncthreads();
     if (warp == 1) tc::tmem_alloc(&ctl->tmem, uint32_t(kPStages * kPStageCols));
     tc::fence_before_sync();
@@ -498,12 +590,14 @@ conv_hidden_tc_persistent(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* _
         tc::mbar_wait_bounded(&ctl->fin, 0, kTcSpin);
     } else if (warp >= 2) {
         // ---- epilogue: kPEpiWarps warps in kPEpiWarps / 4 groups; a warp
-        // reads TMEM lanes 32 (warp % 4) .. + 31 (positions of an M-tile) and
-        // its group's (accumulator, chunk) pairs j = grp, grp + NG, ...; the
-        // TMEM load of the next pair is in flight while the current one is
-        // stored.
+        // reads TMEM lanes 32 (warp % 4) .. + 31 (one pixel per lane of an
+        // M-tile) and owns its group's accumulators acc = grp, grp + NG, ...:
+        // all C channels of its pixel come in W-column TMEM loads (one wait
+        // per W channels), then bias + activation (or the act' product),
+        // bf16, 16-byte stores per 8-channel chunk.  kFwdLast also projects
+        // the pixel's activations onto the last layer's nine taps.
         constexpr int NG = kPEpiWarps / 4;
-        constexpr int NPAIRS = NACC * KC;
+        constexpr int W = 16;
         const int grp = (warp - 2) >> 2;
         const int q = warp & 3;
         const float4* bias4 = reinterpret_cast<const float4*>(ctl->bias);
@@ -516,52 +610,83 @@ conv_hidden_tc_persistent(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* _
             const int stage = i & 1;
             if (!p_wait(&ctl->accf[stage], uint32_t((i >> 1) & 1), abort_flag, status)) break;
             tc::fence_after_sync();
-            const size_t base =
-                (size_t(f) * KC * nn + size_t(yb * TY) * n + size_t(cb * CW + q * 32 + lane)) * 8;
+            const size_t pix0 = size_t(yb * TY) * n + size_t(cb * CW + q * 32 + lane);
             const uint32_t trow = tmem + (uint32_t(q * 32) << 16) + uint32_t(stage * kPStageCols);
-            uint32_t v[8], w[8];
-            // pair j: accumulator j / KC (row r = acc / MG, M-tile m = acc % MG), chunk j % KC
-            if (grp < NPAIRS) tc::tmem_ld8(trow + uint32_t((grp / KC) * C + (grp % KC) * 8), v);
-            tc::tmem_wait_ld();
-            for (int j = grp; j < NPAIRS; j += NG) {
-                const int jn = j + NG;
-                if (jn < NPAIRS) tc::tmem_ld8(trow + uint32_t((jn / KC) * C + (jn % KC) * 8), w);
-                const int acc = j / KC, kc = j % KC;
+            for (int acc = grp; acc < NACC; acc += NG) {
                 const int r = acc / MG, m = acc % MG;
-                const size_t off = base + (size_t(kc) * nn + size_t(r) * n + size_t(m) * 128) * 8;
-                uint32_t packed[4];
-                if (mode == kFwd) {
-                    const float4 b0 = bias4[kc * 2], b1 = bias4[kc * 2 + 1];
-                    __align__(16) float z8[8] = {__uint_as_float(v[0]) + b0.x, __uint_as_float(v[1]) + b0.y,
-                                                 __uint_as_float(v[2]) + b0.z, __uint_as_float(v[3]) + b0.w,
-                                                 __uint_as_float(v[4]) + b1.x, __uint_as_float(v[5]) + b1.y,
-                                                 __uint_as_float(v[6]) + b1.z, __uint_as_float(v[7]) + b1.w};
+                const size_t pix = pix0 + size_t(r) * n + size_t(m) * 128;
+                float pt[9];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const __nv_bfloat162 h = __floats2bfloat162_rn(act_apply<float>(act, z8[2 * e]),
-                                                                       act_apply<float>(act, z8[2 * e + 1]));
-                        packed[e] = *reinterpret_cast<const uint32_t*>(&h);
-                    }
-                    if (zio) {
-                        reinterpret_cast<float4*>(zio + off)[0] = *reinterpret_cast<const float4*>(z8);
-                        reinterpret_cast<float4*>(zio + off)[1] = *reinterpret_cast<const float4*>(z8 + 4);
-                    }
-                } else {
-                    const float4 za = reinterpret_cast<const float4*>(zio + off)[0];
-                    const float4 zb = reinterpret_cast<const float4*>(zio + off)[1];
-                    const float zz[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+                for (int tp = 0; tp < 9; ++tp) pt[tp] = 0.f;
+#pragma unroll 1
+                for (int kc0 = 0; kc0 < KC; kc0 += W / 8) {
+                    uint32_t v[W];
+                    tc::tmem_ldw<W>(trow + uint32_t(acc * C + kc0 * 8), v);
+                    tc::tmem_wait_ld();
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const __nv_bfloat162 h =
-                            __floats2bfloat162_rn(__uint_as_float(v[2 * e]) * act_grad<float>(act, zz[2 * e]),
-                                                  __uint_as_float(v[2 * e + 1]) * act_grad<float>(act, zz[2 * e + 1]));
-                        packed[e] = *reinterpret_cast<const uint32_t*>(&h);
+                    for (int h = 0; h < W / 8; ++h) {
+                        const int kc = kc0 + h;
+                        const size_t off = ((size_t(f) * KC + kc) * nn + pix) * 8;
+                        uint32_t packed[4];
+                        if (mode != kDgrad) {
+                            const float4 b0 = bias4[kc * 2], b1 = bias4[kc * 2 + 1];
+                            __align__(16) float z8[8] = {
+                                __uint_as_float(v[h * 8 + 0]) + b0.x, __uint_as_float(v[h * 8 + 1]) + b0.y,
+                                __uint_as_float(v[h * 8 + 2]) + b0.z, __uint_as_float(v[h * 8 + 3]) + b0.w,
+                                __uint_as_float(v[h * 8 + 4]) + b1.x, __uint_as_float(v[h * 8 + 5]) + b1.y,
+                                __uint_as_float(v[h * 8 + 6]) + b1.z, __uint_as_float(v[h * 8 + 7]) + b1.w};
+                            float a8[8];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const __nv_bfloat162 hh = __floats2bfloat162_rn(act_c<ACT>(z8[2 * e]),
+                                                                                act_c<ACT>(z8[2 * e + 1]));
+                                packed[e] = *reinterpret_cast<const uint32_t*>(&hh);
+                                a8[2 * e] = __low2float(hh);
+                                a8[2 * e + 1] = __high2float(hh);
+                            }
+                            if (zio) {
+                                reinterpret_cast<float4*>(zio + off)[0] = *reinterpret_cast<const float4*>(z8);
+                                reinterpret_cast<float4*>(zio + off)[1] = *reinterpret_cast<const float4*>(z8 + 4);
+                            }
+                            if (mode == kFwdLast) {
+                                const float4* wl4 = reinterpret_cast<const float4*>(ctl->wl + kc * 72);
+#pragma unroll
+                                for (int tp = 0; tp < 9; ++tp) {
+                                    const float4 w0 = wl4[tp * 2], w1 = wl4[tp * 2 + 1];
+                                    float s_ = pt[tp];
+                                    s_ = fmaf(w0.x, a8[0], s_);
+                                    s_ = fmaf(w0.y, a8[1], s_);
+                                    s_ = fmaf(w0.z, a8[2], s_);
+                                    s_ = fmaf(w0.w, a8[3], s_);
+                                    s_ = fmaf(w1.x, a8[4], s_);
+                                    s_ = fmaf(w1.y, a8[5], s_);
+                                    s_ = fmaf(w1.z, a8[6], s_);
+                                    s_ = fmaf(w1.w, a8[7], s_);
+                                    pt[tp] = s_;
+                                }
+                            }
+                        } else {
+                            const float4 za = reinterpret_cast<const float4*>(zio + off)[0];
+                            const float4 zb = reinterpret_cast<const float4*>(zio + off)[1];
+                            const float zz[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const __nv_bfloat162 hh = __floats2bfloat162_rn(
+                                    __uint_as_float(v[h * 8 + 2 * e]) * act_grad_c<ACT>(zz[2 * e]),
+                                    __uint_as_float(v[h * 8 + 2 * e + 1]) * act_grad_c<ACT>(zz[2 * e + 1]));
+                                packed[e] = *reinterpret_cast<const uint32_t*>(&hh);
+                            }
+                        }
+                        // kFwdLast stores the activations only for training (zio)
+                        if (mode != kFwdLast || zio)
+                            *reinterpret_cast<uint4*>(out + off) =
+                                make_uint4(packed[0], packed[1], packed[2], packed[3]);
                     }
                 }
-                *reinterpret_cast<uint4*>(out + off) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                tc::tmem_wait_ld();
+                if (mode == kFwdLast) {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = w[e];
+                    for (int tp = 0; tp < 9; ++tp) maps[(size_t(f) * 9 + tp) * nn + pix] = pt[tp];
+                }
             }
             tc::fence_before_sync();
             __syncwarp();
@@ -584,11 +709,11 @@ static int num_sms() {
     return sms;
 }
 
-template <int C, int MG>
-static int launch_persistent_mg(const PShape& s, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
-                                const __nv_bfloat16* w, const float* bias, int act, int mode, float* zio,
-                                int* status, cudaStream_t st) {
-    auto kern = conv_hidden_tc_persistent<C, MG>;
+template <int C, int MG, int ACT>
+static int launch_persistent_act(const PShape& s, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
+                                 const __nv_bfloat16* w, const float* bias, int mode, float* zio, int* status,
+                                 cudaStream_t st, const float* wlast, float* maps) {
+    auto kern = conv_hidden_tc_persistent<C, MG, ACT>;
     static bool configured = false;
     if (!configured) {
         ACPR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(227 * 1024)));
@@ -596,19 +721,31 @@ static int launch_persistent_mg(const PShape& s, int n, int batch, const __nv_bf
     }
     const long long units = (long long)batch * (n / s.CW) * (n / s.TY);
     const int grid = int(units < num_sms() ? units : num_sms());
-    kern<<<grid, kPThreads, s.smem, st>>>(in, out, w, bias, n, batch, s.RING, s.slot_bytes, act, mode, zio, status,
-                                          g_test_stall);
+    kern<<<grid, kPThreads, s.smem, st>>>(in, out, w, bias, n, batch, s.RING, s.slot_bytes, mode, zio, status,
+                                          g_test_stall, wlast, maps);
     ACPR_LAUNCH_CHECK();
     return AC_OK;
+}
+
+template <int C, int MG>
+static int launch_persistent_mg(const PShape& s, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
+                                const __nv_bfloat16* w, const float* bias, int act, int mode, float* zio,
+                                int* status, cudaStream_t st, const float* wlast = nullptr, float* maps = nullptr) {
+    if (act == AC_ACT_TANH)
+        return launch_persistent_act<C, MG, AC_ACT_TANH>(s, n, batch, in, out, w, bias, mode, zio, status, st, wlast,
+                                                         maps);
+    return launch_persistent_act<C, MG, AC_ACT_GELU>(s, n, batch, in, out, w, bias, mode, zio, status, st, wlast,
+                                                     maps);
 }
 
 template <int C>
 static int launch_persistent(const PShape& s, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
                              const __nv_bfloat16* w, const float* bias, int act, int mode, float* zio,
-                             int* status, cudaStream_t st) {
-    if (s.MG == 1) return launch_persistent_mg<C, 1>(s, n, batch, in, out, w, bias, act, mode, zio, status, st);
+                             int* status, cudaStream_t st, const float* wlast = nullptr, float* maps = nullptr) {
+    if (s.MG == 1)
+        return launch_persistent_mg<C, 1>(s, n, batch, in, out, w, bias, act, mode, zio, status, st, wlast, maps);
     if constexpr (C < 64)
-        return launch_persistent_mg<C, 2>(s, n, batch, in, out, w, bias, act, mode, zio, status, st);
+        return launch_persistent_mg<C, 2>(s, n, batch, in, out, w, bias, act, mode, zio, status, st, wlast, maps);
     set_error("conv: no persistent kernel for C=%d, MG=%d", C, s.MG);
     return AC_ERR_UNSUPPORTED;
 }
@@ -625,15 +762,15 @@ static int launch_hidden(int n, int batch, const __nv_bfloat16* in, __nv_bfloat1
     if (ps.RING) return launch_persistent<C>(ps, n, batch, in, out, w, bias, act, mode, zio, status, st);
     const TcShape s = pick_shape(n, C);
     if (s.TY == 0) return AC_ERR_UNSUPPORTED;
-    auto kern = conv_hidden_tc_kernel<C>;
-    static size_t configured = 0;
-    if (configured < s.smem) {
+    auto kern = act == AC_ACT_TANH ? conv_hidden_tc_kernel<C, AC_ACT_TANH> : conv_hidden_tc_kernel<C, AC_ACT_GELU>;
+    static bool configured[2] = {false, false};
+    if (!configured[act == AC_ACT_TANH]) {
         ACPR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(227 * 1024)));
-        configured = 227 * 1024;
+        configured[act == AC_ACT_TANH] = true;
     }
     const long long blocks = (long long)batch * (n / s.TY);
-    kern<<<unsigned(blocks), kTcThreads, s.smem, st>>>(in, out, w, bias, n, s.TY, s.n_mt, s.plane_px, s.ncols, act,
-                                                       mode, zio, status);
+    kern<<<unsigned(blocks), kTcThreads, s.smem, st>>>(in, out, w, bias, n, s.TY, s.n_mt, s.plane_px, s.ncols, mode,
+                                                       zio, status);
     ACPR_LAUNCH_CHECK();
     return AC_OK;
 }
@@ -649,6 +786,27 @@ int hidden_layer_bf16(const cnn_desc* d, int l, int n, int batch, const __nv_bfl
         case 64: return launch_hidden<64>(n, batch, in, out, w, bias, d->act, kFwd, zsave, status, st);
         default: return AC_ERR_UNSUPPORTED;
     }
+}
+
+bool hidden_last_fused_supported(int n, int C) { return C >= 32 && C <= 64 && p_shape(n, C).RING > 0; }
+
+int hidden_last_fused(const cnn_desc* d, int l, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* act_out,
+                      const float* bias, const float* w_last, float* maps, int* status, cudaStream_t st,
+                      float* zsave) {
+    const int C = d->channels;
+    if (batch <= 0) return AC_OK;
+    if (!hidden_last_fused_supported(n, C)) return AC_ERR_UNSUPPORTED;
+    if (!status) {
+        set_error("tensor-core conv: no status word");
+        return AC_ERR_ARG;
+    }
+    const __nv_bfloat16* w = static_cast<const __nv_bfloat16*>(d->packed) + size_t(l - 1) * 9 * C * C;
+    const PShape ps = p_shape(n, C);
+    if (C == 32)
+        return launch_persistent<32>(ps, n, batch, in, act_out, w, bias, d->act, kFwdLast, zsave, status, st, w_last,
+                                     maps);
+    return launch_persistent<64>(ps, n, batch, in, act_out, w, bias, d->act, kFwdLast, zsave, status, st, w_last,
+                                 maps);
 }
 
 int hidden_dgrad_bf16(int C, int act, int n, int batch, const __nv_bfloat16* dz_next, __nv_bfloat16* dz_out,

@@ -37,7 +37,7 @@ __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >
 
 struct TrainLayout {
     size_t a_bytes, z_bytes;    // one layer
-    size_t off_a, off_z, off_dz, off_wt, off_part, off_gc, off_zpart, total;
+    size_t off_a, off_z, off_dz, off_wt, off_part, off_gc, off_zpart, off_maps, total;
 };
 
 static TrainLayout train_layout(const cnn_desc* d, int n, int batch) {
@@ -54,7 +54,8 @@ static TrainLayout train_layout(const cnn_desc* d, int n, int batch) {
     t.off_part = (t.off_wt + wt + 255) / 256 * 256;
     t.off_gc = t.off_part + size_t(kChunks) * 9 * (size_t(d->channels) * d->channels + d->channels) * 4;
     t.off_zpart = t.off_gc + size_t(batch) * n * n * 4;
-    t.total = t.off_zpart + size_t(batch) * n * n * sizeof(double);  // >= the last layer's block partials
+    t.off_maps = t.off_zpart + size_t(batch) * n * n * sizeof(double);  // >= the last layer's block partials
+    t.total = t.off_maps + size_t(batch) * 9 * n * n * sizeof(float);
     return t;
 }
 
@@ -354,6 +355,36 @@ static int forward_train(const cnn_desc* d, int n, int batch, const float* u, fl
     return last_layer_bf16(d, n, batch, A(d->layers - 1), out, W + woff, Bv + boff, u, zpart, st);
 }
 
+// The same forward pass where the inference path fuses the last hidden layer
+// with the last layer's projection (see hidden_last_fused).
+template <int C>
+static int forward_train_fused(const cnn_desc* d, int n, int batch, const float* u, float* out, unsigned char* ws,
+                               cudaStream_t st) {
+    const TrainLayout t = train_layout(d, n, batch);
+    const long long pixels = (long long)n * n * batch;
+    const unsigned blocks = unsigned((pixels + 127) / 128);
+    const float* W = static_cast<const float*>(d->w);
+    const float* Bv = static_cast<const float*>(d->b);
+    auto A = [&](int l) { return reinterpret_cast<__nv_bfloat16*>(ws + t.off_a + t.a_bytes * (l - 1)); };
+    auto Z = [&](int l) { return reinterpret_cast<float*>(ws + t.off_z + t.z_bytes * l); };
+    first_fwd_save_kernel<C><<<blocks, 128, 0, st>>>(u, A(1), Z(0), W, Bv, batch, n, d->act);
+    ACPR_LAUNCH_CHECK();
+    size_t woff = size_t(C) * 9, boff = C;
+    const int L = d->layers;
+    for (int l = 1; l < L - 2; ++l) {
+        int rc = hidden_layer_bf16(d, l, n, batch, A(l), A(l + 1), W + woff, Bv + boff, conv_status(ws), st, Z(l));
+        if (rc) return rc;
+        woff += size_t(C) * C * 9;
+        boff += C;
+    }
+    float* maps = reinterpret_cast<float*>(ws + t.off_maps);
+    int rc = hidden_last_fused(d, L - 2, n, batch, A(L - 2), A(L - 1), Bv + boff, W + woff + size_t(C) * C * 9, maps,
+                               conv_status(ws), st, Z(L - 2));
+    if (rc) return rc;
+    double* zpart = reinterpret_cast<double*>(ws + t.off_zpart);
+    return last_stencil_f32(d, n, batch, maps, out, Bv + boff + C, u, zpart, st);
+}
+
 template <int C>
 static int backward(const cnn_desc* d, int n, int batch, const float* u, const float* g, float* du, float* gw,
                     float* gb, int accumulate, unsigned char* ws, cudaStream_t st) {
@@ -475,10 +506,17 @@ extern "C" int cnn_forward_train(const cnn_desc* desc, int n, int batch, const f
     ACPR_CHECK_ARG(u_in && u_out && train_ws && desc->packed, "null pointer");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     unsigned char* ws = static_cast<unsigned char*>(train_ws);
+    const bool fused = desc->layers >= 3 && hidden_last_fused_supported(n, desc->channels);
     switch (desc->channels) {
         case 16: rc = forward_train<16>(desc, n, batch, u_in, u_out, ws, st); break;
-        case 32: rc = forward_train<32>(desc, n, batch, u_in, u_out, ws, st); break;
-        default: rc = forward_train<64>(desc, n, batch, u_in, u_out, ws, st); break;
+        case 32:
+            rc = fused ? forward_train_fused<32>(desc, n, batch, u_in, u_out, ws, st)
+                       : forward_train<32>(desc, n, batch, u_in, u_out, ws, st);
+            break;
+        default:
+            rc = fused ? forward_train_fused<64>(desc, n, batch, u_in, u_out, ws, st)
+                       : forward_train<64>(desc, n, batch, u_in, u_out, ws, st);
+            break;
     }
     // a bounded tensor-core wait that gave up is reported here (synchronises)
     return rc ? rc : conv_check_status_uncaptured(conv_status(train_ws), st);

@@ -113,3 +113,42 @@ def test_parareal_1024_exact_at_k_equals_s():
     for j in range(s):
         seq.append(G.ac_fine_propagate_slices(fp, c, seq[-1]))
     assert torch.equal(pr.trajectory()[0], torch.cat(seq))
+
+
+def test_uneven_grid_sizes_together_match_oracle():
+    """Three handles of classic problems on 128^2, 256^2 and 512^2 grids
+    (eps = 2.5 h, uneven slice counts and steps), iterated together by
+    ac_parareal_solve_many on three streams with CUDA graphs, to k = 2: one
+    problem of each grid size against the oracle's Algorithm 2 at the same k
+    (float64 fine solves, the conv with the same bf16 roundings).  The
+    bound is the float32 fine error 2e-5 sqrt(c) per slice times the slices
+    the error is carried through, with a factor 2 for its growth along the
+    sweep (the G here, N(0, 0.05^2) weights with 16 channels, adds bf16 flips
+    far below that).  Measured on GB300 at 512^2: 1.9e-4 against 3.8e-4."""
+    import os
+    import oracle as O
+    w, b = I.cnn_weights(4, 16, seed=0, sigma=0.05)
+    w32, b32 = w.astype(np.float32), b.astype(np.float32)
+    net = G.CoarseNet(4, 16, w32, b32, act=1, precision=G.AC_F32)
+    spec = O.CnnSpec(4, 16, w32.astype(np.float64), b32.astype(np.float64), act=1, bf16=1)
+    cases = [(128, [4, 3], [30, 20]), (256, [3, 5], [20, 10]), (512, [3, 2], [10, 15])]
+    handles, streams, inputs = [], [], []
+    for n, sl, st in cases:
+        fp = G.FineParams(n, 2.5 / n, 2.0, 5e-5, variant=G.AC_CLASSIC, precision=G.AC_F32)
+        u0 = fields(n, [100 + n + i for i in range(len(sl))])
+        h = G.Parareal(fp, net, u0, sl, st)
+        h.enable_graphs(True)
+        handles.append(h)
+        streams.append(torch.cuda.Stream())
+        inputs.append((fp, u0, sl, st))
+    G.parareal_solve_many(handles, streams, tol=0.0, kmax=2, allow_unconverged=True)
+    torch.cuda.synchronize()
+    with O.threads(os.cpu_count() or 1):
+        for h, (fp, u0, sl, st) in zip(handles, inputs):
+            n = fp.n
+            U = h.trajectory()[0].double().cpu().numpy()
+            ref = O.parareal(O.params(n, 2.5 / n, 2.0, 5e-5, 0), spec, sl[0], st[0], kmax=min(2, sl[0]), tol=0.0,
+                             u0=u0[0].double().cpu().numpy())
+            err = np.abs(U[: sl[0] + 1] - ref["U"]).max()
+            print(f"n={n}: max-abs {err:.2e}")
+            assert err < 2 * 2e-5 * np.sqrt(st[0]) * sl[0], n

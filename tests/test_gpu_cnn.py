@@ -180,3 +180,29 @@ def test_bounded_wait_timeout_is_reported_and_cleared():
     got = G.cnn_coarse_step(net, u)
     ref = G.cnn_coarse_step(G.CoarseNet(L, C, w32, b32, act=1, precision=G.AC_F32), u)
     assert torch.equal(got, ref)
+
+
+@pytest.mark.parametrize("n,C", [(256, 32), (128, 64)])
+def test_conv_tile_shapes_identical_and_autotune(n, C):
+    """Every tile shape of the persistent tensor-core kernel (M-tiles per row,
+    rows per unit, ring depth) forms each output with the same sums in the
+    same order, so G is bitwise the same under every shape; cnn_autotune
+    times them all and keeps the fastest."""
+    L = 6
+    w, b = I.cnn_weights(L, C, seed=9, sigma=0.05)
+    net = G.CoarseNet(L, C, w.astype(np.float32), b.astype(np.float32), act=1, precision=G.AC_F32, mass_fix=1)
+    u = torch.tensor(np.stack([I.random_field(n, seed=s) for s in range(3)]), dtype=torch.float32, device="cuda")
+    shapes = G.cnn_conv_variants(n, C)
+    assert len(shapes) >= 2
+    outs = []
+    for i in range(len(shapes)):
+        G.cnn_conv_set_variant(n, C, i)
+        outs.append(G.cnn_coarse_step(net, u))
+    G.cnn_conv_set_variant(n, C, -1)
+    for i in range(1, len(shapes)):
+        assert torch.equal(outs[i], outs[0]), shapes[i]
+    times, best = G.cnn_autotune(net, u)
+    assert len(times) == len(shapes) and all(t > 0 for t in times.values())
+    assert times[shapes[best]] == min(times.values())
+    assert torch.equal(G.cnn_coarse_step(net, u), outs[0])
+    G.cnn_conv_set_variant(n, C, -1)
