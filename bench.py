@@ -189,11 +189,25 @@ def run_uneven(args):
     Wc = I.cnn_weights(6, 32, seed=0)
     net = G.CoarseNet(6, 32, Wc[0].astype(np.float32), Wc[1].astype(np.float32), act=1, precision=G.AC_F32)
     handles, streams, groups = [], [], []
+    tuned = {}
     for n in classes:
         grp = [p for p in probs if p["n"] == n]
         fp = G.FineParams(n, 2.5 / n, 2.0, 5e-5, variant=G.AC_CLASSIC, precision=G.AC_F32)
         u0 = torch.tensor(np.stack([I.random_field(n, seed=p["seed"]) for p in grp]), dtype=torch.float32,
                           device="cuda")
+        # the tuners pick the fine launch shape (on a batch of the size a fine
+        # phase launches) and the conv tile (on the problems' fields) before
+        # the handle exists, so no solve changes shape midway
+        reps = max(1, 256 // len(grp))
+        fb = u0.repeat(reps, 1, 1).contiguous()
+        f_ms, f_idx = G.ac_fine_autotune(fp, 20, fb, torch.empty_like(fb))
+        c_choice = None
+        if G.cnn_conv_variants(n, 32):
+            c_ms, c_idx = G.cnn_autotune(net, u0)
+            c_choice = {"shape_mtiles_rows_ring": list(G.cnn_conv_variants(n, 32)[c_idx]),
+                        "ms": {str(k): v for k, v in c_ms.items()}}
+        tuned[str(n)] = {"fine": G.ac_fine_variants(n, G.AC_F32)[f_idx], "fine_ms_per_20_steps": f_ms,
+                         "conv": c_choice}
         h = G.Parareal(fp, net, u0, [p["slices"] for p in grp], [p["steps"] for p in grp])
         h.enable_graphs(not args.no_graphs)
         h.enable_timing(True)
@@ -250,7 +264,8 @@ def run_uneven(args):
         "iterations_mean": float(np.mean(its)), "problems": len(probs),
         "grid_classes": {str(n): sum(1 for p in probs if p["n"] == n) for n in classes},
         "fine_ms_per_solve_summed_over_streams": fine_ms, "steps": args.steps, "warmup": args.warmup,
-        "coarse_weights": "untrained N(0, 0.01^2)", "cuda_graphs": not args.no_graphs}), flush=True)
+        "coarse_weights": "untrained N(0, 0.01^2)", "cuda_graphs": not args.no_graphs, "autotuned": tuned}),
+        flush=True)
 
 
 def run_train(args):
@@ -468,6 +483,221 @@ def run_adjoint(args):
     print(json.dumps(out), flush=True)
 
 
+def run_plain64(args):
+    """The plain float64 configuration: classic Allen-Cahn on a 64^2 grid,
+    eps = 0.025, S = 2, dt = 1e-4, 8 slices x 100 steps, conv 1-16-16-16-1
+    tanh with N(0, 0.01^2) weights, iterated to a relative increment < 1e-10
+    or k = 8.  Times the GPU Parareal solve and the GPU sequential float64
+    fine solve (CUDA events, `--steps` repetitions after `--warmup`), and the
+    oracle's Algorithm 2 on the same problem on one host core and on all host
+    cores (its conv rows and independent fine solves split over threads).
+    Prints one JSON line (not the benchmark line)."""
+    import oracle as O
+    W = I.PLAIN_F64_64
+    O.build()
+    u0 = W.ics()
+    wt, bs = W.weights()
+    spec = O.CnnSpec(W.layers, W.channels, wt, bs, act=W.act)
+    p_o = O.params(W.n, W.eps, W.S, W.dt, W.variant)
+    t0 = time.perf_counter()
+    ref = O.parareal(p_o, spec, W.slices, W.steps, kmax=W.kmax, tol=W.tol, u0=u0[0])
+    oracle_1 = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    with O.threads(cores):
+        t0 = time.perf_counter()
+        O.parareal(p_o, spec, W.slices, W.steps, kmax=W.kmax, tol=W.tol, u0=u0[0])
+        oracle_n = time.perf_counter() - t0
+    import torch
+    import paper_2510_07672_gb300 as G
+    fp = G.FineParams(W.n, W.eps, W.S, W.dt, variant=W.variant, precision=G.AC_F64)
+    net = G.CoarseNet(W.layers, W.channels, wt, bs, act=W.act, precision=G.AC_F64)
+    u = torch.tensor(u0, device="cuda")
+    pr = G.Parareal(fp, net, u, W.slices, W.steps)
+    pr.enable_graphs(not args.no_graphs)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def solve():
+        pr.reset(u)
+        return pr.solve(tol=W.tol, kmax=W.kmax, allow_unconverged=True)
+
+    for _ in range(max(args.warmup, 1)):
+        its, l2 = solve()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        its, l2 = solve()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    para_ms = e0.elapsed_time(e1) / args.steps
+    err = float(np.abs(pr.trajectory()[0].cpu().numpy() - ref["U"]).max())
+    a, b = u.clone(), torch.empty_like(u)
+    for _ in range(W.slices):
+        G.ac_fine_propagate_slices(fp, W.steps, a, b)
+        a, b = b, a
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for _ in range(W.slices):
+            G.ac_fine_propagate_slices(fp, W.steps, a, b)
+            a, b = b, a
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({
+        "metric": METRIC, "workload": W.name,
+        "config": {"n": W.n, "eps": W.eps, "dt": W.dt, "slices": W.slices, "steps_per_slice": W.steps,
+                   "conv": "1-16-16-16-1 tanh float64", "tol": W.tol, "kmax": W.kmax},
+        "gpu_parareal_ms": para_ms, "gpu_sequential_ms": seq_ms, "iterations": its[0], "final_rel_l2": l2[0],
+        "oracle_iterations": ref["iters"], "max_abs_vs_oracle": err,
+        "oracle_parareal_s_1core": oracle_1, "oracle_parareal_s_all_cores": oracle_n, "host_cores": cores,
+        "steps": args.steps, "warmup": args.warmup}), flush=True)
+
+
+LARGE_WEIGHTS = os.path.join(ROOT, "paper_2510_07672_gb300", "weights", "large1024_c64l8_gelu.npz")
+
+
+def run_large(args):
+    """The large single problem: classic Allen-Cahn on a 1024^2 periodic grid,
+    eps = 0.004, S = 2, dt = 2e-5, 128 slices x 500 fine steps (T = 1.28), one
+    seeded U(-0.9, 0.9) initial field; float32 fine step (two-pass path
+    through L2/HBM), float64 increments, coarse net 1 -> 64 x 8 GELU bf16
+    (weights trained by train.py --workload large, or N(0, 0.01^2) with
+    --weights untrained).  Times the sequential float32 fine solve (128 slices
+    one after another, one field) and the Parareal solve to a relative L2
+    increment < 1e-6 or `--large-kmax` iterations, both with CUDA events on
+    the same GPU.  Prints one JSON line (not the benchmark line)."""
+    W = I.LARGE_F32_1024
+    n, s, c = W.n, W.slices, W.steps
+    # the oracle's sequential fine rate at 1024^2 on one host core, from 10
+    # float64 steps (before any GPU work in this process), extrapolated to
+    # the 64,000-step solve
+    import oracle as O
+    O.build()
+    p_o = O.params(n, W.eps, W.S, W.dt, W.variant)
+    u_host = W.ics()[0]
+    t0 = time.perf_counter()
+    O.fine_propagate(p_o, 10, u_host)
+    o_s = time.perf_counter() - t0
+    cpu = {"value": 10 * n * n / o_s, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+           "sample": f"10 float64 fine steps of the 1024^2 field on one core ({o_s:.1f} s); the sequential "
+                     f"64,000-step solve extrapolates to {o_s * s * c / 10:.0f} s"}
+    import torch
+    import paper_2510_07672_gb300 as G
+    fp = G.FineParams(n, W.eps, W.S, W.dt, variant=W.variant, precision=G.AC_F32)
+    wt, bs = W.weights()
+    wsrc = "untrained N(0, 0.01^2)"
+    wpath = LARGE_WEIGHTS if args.weights == "trained" else (None if args.weights == "untrained" else args.weights)
+    if wpath:
+        z = np.load(wpath)
+        wt, bs = z["w"], z["b"]
+        wsrc = (f"trained by paper_2510_07672_gb300/train.py --workload large ({int(z['iters'])} Adam steps, "
+                f"{int(z['unroll'])}-step unrolled MSE on {int(z['crop'])}^2 crops, h = 1/1024): "
+                f"{os.path.relpath(wpath, ROOT)}")
+    net = G.CoarseNet(W.layers, W.channels, wt.astype(np.float32), bs.astype(np.float32), act=W.act,
+                      precision=G.AC_F32)
+    u0 = torch.tensor(W.ics().astype(np.float32), device="cuda")
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    # sequential float32 fine solve: 128 slices of 500 steps, one field
+    a, b = u0.clone(), torch.empty_like(u0)
+    G.ac_fine_propagate_slices(fp, c, a, b)  # warm-up (workspace, tables)
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    for _ in range(s):
+        G.ac_fine_propagate_slices(fp, c, a, b)
+        a, b = b, a
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    seq_final = a.clone()
+
+    # one batched fine launch of all 128 slices (Parareal's fine phase at k = 1)
+    batch_in = u0.expand(s, n, n).contiguous()
+    batch_out = torch.empty_like(batch_in)
+    G.ac_fine_propagate_slices(fp, 2, batch_in, batch_out)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    G.ac_fine_propagate_slices(fp, c, batch_in, batch_out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1)
+
+    # one application of G to one 1024^2 field
+    g_out = torch.empty_like(u0)
+    for _ in range(3):
+        G.cnn_coarse_step(net, u0, g_out)
+    torch.cuda.synchronize()
+    reps = 20
+    e0.record(stream)
+    for _ in range(reps):  # each call ends with a status read (a sync of a few us)
+        G.cnn_coarse_step(net, u0, g_out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    g_ms = e0.elapsed_time(e1) / reps
+
+    # Parareal, iteration by iteration (each a CUDA graph), until the
+    # increment is below tol or k = --large-kmax; the clock runs from the
+    # k = 0 coarse sweep to the last increment
+    pr = G.Parareal(fp, net, u0, s, c)
+    pr.enable_timing(True)
+    pr.enable_graphs(not args.no_graphs)
+    pr.iterate()  # k = 0 (records its graph)
+    pr.reset(u0)
+    pr.reset_stats()
+    torch.cuda.synchronize()
+    incs, its_ms = [], []
+    e0.record(stream)
+    pr.iterate()  # k = 0
+    k = 0
+    while k < args.large_kmax:
+        t_it = time.perf_counter()
+        l2_k, _ = pr.iterate()
+        its_ms.append((time.perf_counter() - t_it) * 1e3)
+        k += 1
+        incs.append(l2_k[0])
+        if l2_k[0] < W.tol:
+            break
+    e1.record(stream)
+    torch.cuda.synchronize()
+    para_ms = e0.elapsed_time(e1)
+    its, l2 = [k], [incs[-1]]
+    st = pr.stats()
+    U = pr.trajectory()[0]
+    err_vs_seq = float(((U[-1].double() - seq_final[0].double()).norm() / seq_final[0].double().norm()).item())
+    peaks, src = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    cells_batch = s * c * n * n
+    conv_fl = conv_flops_per_cell(W.layers, W.channels) * n * n
+    pr.close()
+    print(json.dumps({
+        "metric": METRIC, "workload": W.name,
+        "config": {"n": n, "eps": W.eps, "S": W.S, "dt": W.dt, "slices": s, "steps_per_slice": c,
+                   "variant": "classic", "conv": "1-64x8-1 gelu bf16", "coarse_weights": wsrc, "tol": W.tol,
+                   "kmax": args.large_kmax, "cuda_graphs": not args.no_graphs},
+        "sequential_ms": seq_ms, "parareal_ms": para_ms, "speedup_vs_sequential": seq_ms / para_ms,
+        "iterations": its[0], "final_rel_l2": l2[0], "tol_reached": bool(l2[0] < W.tol),
+        "increments": incs, "iteration_wall_ms": its_ms,
+        "breakeven_iterations": "Parareal beats the sequential solve only if it stops by the k where "
+                                "k0 sweep + k x (fine phase + coarse sweep) < sequential_ms",
+        "rel_l2_final_field_vs_sequential": err_vs_seq,
+        "phase_ms": {"fine": st["fine_ms"], "coarse": st["coarse_ms"], "increment": st["increment_ms"]},
+        "sequential_us_per_step": seq_ms * 1e3 / (s * c),
+        "batched_fine": {"fields": s, "steps": c, "ms": batch_ms, "cell_steps_per_s": cells_batch / (batch_ms * 1e-3),
+                         "roofline": {"bound": "hbm", "achieved": 16.0 * cells_batch / (batch_ms * 1e-3) / 1e9,
+                                      "peak": hbm, "unit": "GB/s",
+                                      "frac": 16.0 * cells_batch / (batch_ms * 1e-3) / 1e9 / hbm,
+                                      "traffic_model": "16 B per cell-step (rows pass and columns pass, each "
+                                                       "one float32 read and write per cell)", "peak_source": src}},
+        "coarse_g": {"ms_per_application": g_ms, "tflops": conv_fl / (g_ms * 1e-3) / 1e12,
+                     "frac_of_bf16_peak": conv_fl / (g_ms * 1e-3) / 1e12 / bf16},
+        "cpu_baseline": cpu,
+        "steps": 1, "warmup": 1}), flush=True)
+
+
 # DRAM bytes (read + write) the fine kernel moved per field-slice in one ncu
 # capture of the 256^2 launch shape (512 fields x 20 steps: 134.3 MB read,
 # 87.7 MB written); a slice is read once and written once whatever its step
@@ -532,12 +762,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--weights", default="trained", help="'trained' (the committed G), 'untrained', or a .npz path")
-    ap.add_argument("--workload", default="mass256", choices=["mass256", "uneven", "train", "adjoint", "acnn", "fine3d"],
+    ap.add_argument("--workload", default="mass256",
+                    choices=["mass256", "uneven", "train", "adjoint", "acnn", "fine3d", "large", "plain64"],
                     help="mass256: the benchmark line; uneven: 64 classic problems of uneven size (batching); "
                          "train: coarse-net training iterations (C = 64, 8 layers); "
                          "adjoint: checkpointed energy gradient through 2000 steps; "
                          "acnn: the paper's ResBlock mACNN (Algorithm 1 training, G time, Parareal); "
-                         "fine3d: the fine step on the 128^3 periodic cube")
+                         "fine3d: the fine step on the 128^3 periodic cube; "
+                         "large: the 1024^2 single problem, Parareal vs the sequential fine solve; "
+                         "plain64: the 64^2 float64 problem, GPU and oracle")
+    ap.add_argument("--large-kmax", type=int, default=8)
     ap.add_argument("--acnn-epochs", type=int, default=20)
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--coarse-substeps", type=int, default=1,
@@ -565,6 +799,12 @@ def main():
         return
     if args.workload == "fine3d":
         run_fine3d(args)
+        return
+    if args.workload == "large":
+        run_large(args)
+        return
+    if args.workload == "plain64":
+        run_plain64(args)
         return
 
     # host-side oracle sample first (before any GPU work in this process)
@@ -706,6 +946,8 @@ def main():
                        "l2": "state larger than L2 (trajectories, stored G and F values: 0.54 GB)",
                        "parallelism": f"replicas x{world}", "cuda_graphs": not args.no_graphs},
             "iterations": its, "final_rel_l2": l2,
+            "tol_reached": bool(all(r < WL.tol and k < slices for k, r in zip(its, l2))),
+            "problems_stopped_at_k_eq_s": int(sum(1 for k in its if k >= slices)),
             "sequential_ms": seq_ms, "parareal_ms": ms,
             "speedup_vs_sequential": seq_ms / ms,
             "phase_ms_per_solve": {"fine": st["fine_ms"] / args.steps, "coarse": st["coarse_ms"] / args.steps,

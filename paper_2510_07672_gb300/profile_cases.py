@@ -1,7 +1,7 @@
 """Small single-kernel cases for profiling with ncu.
 
     python -m paper_2510_07672_gb300.profile_cases fine   # ac_fine_propagate_slices, 512 x 256^2, 20 steps
-    python -m paper_2510_07672_gb300.profile_cases conv   # cnn_coarse_step, 16 x 256^2, 1-32x6-1 gelu bf16
+    python -m paper_2510_07672_gb300.profile_cases conv   # cnn_coarse_step, 16 x 256^2, 1-32x6-1 gelu bf16, mass shift
     python -m paper_2510_07672_gb300.profile_cases big    # ac_fine_propagate_slices, 16 x 1024^2, 2 steps
     python -m paper_2510_07672_gb300.profile_cases acnn   # acnn_forward (fused), 512 x 256^2, C = 4, 2 blocks
     python -m paper_2510_07672_gb300.profile_cases fine3d # ac_fine3d_propagate, 16 x 128^3, 1 step (5 passes)
@@ -38,7 +38,7 @@ def main(case: str) -> None:
     elif case == "conv":
         wt, bs = W.weights()
         net = G.CoarseNet(W.layers, W.channels, wt.astype(np.float32), bs.astype(np.float32), act=W.act,
-                          precision=G.AC_F32)
+                          precision=G.AC_F32, mass_fix=W.mass_fix)
         u = torch.tensor(W.ics(), dtype=torch.float32, device="cuda")
         for _ in range(2):
             G.cnn_coarse_step(net, u)
