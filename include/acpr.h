@@ -240,7 +240,9 @@ int cnn_coarse_step(const cnn_desc* desc, int n, int batch, const void* u_in, vo
 
 /* Tile shapes of the persistent tensor-core conv kernel (n a multiple of
  * 128, channels 16, 32 or 64): M-tiles of 128 pixels per row segment, output
- * rows per work unit and depth of the input-row ring.  Every shape computes
+ * rows per work unit, depth of the input-row ring, and whether MMAs that share
+ * an input row read its A operand once through the tensor core's collector
+ * buffer (areuse).  Every shape computes
  * the same sums in the same order (results are identical); they differ in
  * speed.  cnn_conv_set_variant(n, C, -1) restores the automatic choice.
  * cnn_autotune times every shape on the caller's problem (u_in -> u_out,
@@ -249,7 +251,7 @@ int cnn_coarse_step(const cnn_desc* desc, int n, int batch, const void* u_in, vo
  * Process-wide host state, not thread-safe; a Parareal handle's captured
  * graphs keep the shape they were captured with. */
 int cnn_conv_variant_count(int n, int channels);
-int cnn_conv_variant_shape(int n, int channels, int index, int* mtiles, int* rows, int* ring);
+int cnn_conv_variant_shape(int n, int channels, int index, int* mtiles, int* rows, int* ring, int* areuse);
 int cnn_conv_set_variant(int n, int channels, int index);
 int cnn_conv_get_variant(int n, int channels);
 int cnn_autotune(const cnn_desc* desc, int n, int batch, const void* u_in, void* u_out, float* ms_out,

@@ -133,7 +133,7 @@ int hidden_layer_bf16(const cnn_desc* d, int l, int n, int batch, const __nv_bfl
 // Tile shapes of the persistent tensor-core kernel for (n, C) that a tuner
 // may choose (M-tiles per row segment, rows per unit, input-ring depth).
 int conv_variant_count(int n, int C);
-int conv_variant_describe(int n, int C, int index, int* mg, int* ty, int* ring);
+int conv_variant_describe(int n, int C, int index, int* mg, int* ty, int* ring, int* areuse);
 int conv_set_variant(int n, int C, int index);  // -1: automatic
 int conv_get_variant(int n, int C);
 

@@ -296,6 +296,7 @@ constexpr int kPMaxRing = 16;
 
 struct PShape {
     int MG = 0, CW = 0, TY = 0, RING = 0;
+    int areuse = 0;  // MMAs that share an input row read its A operand once (collector buffer)
     uint32_t slot_bytes = 0;
     size_t smem = 0;
 };
@@ -303,8 +304,9 @@ struct PShape {
 // Tile shape: mg = M-tiles per row segment (0: automatic), ring_mode = depth
 // of the input-row ring (0: one unit of prefetch, 2 TY + 2 rows; 1: no
 // prefetch, TY + 2; 2: as deep as shared memory allows, up to kPMaxRing).
-static PShape p_shape_with(int n, int C, int mg, int ring_mode) {
+static PShape p_shape_with(int n, int C, int mg, int ring_mode, int areuse = 0) {
     PShape s;
+    s.areuse = areuse;
     if (n < 128 || n % 128) return s;
     // C = 64 keeps one M-tile per row so that a ring slot stays small
     s.MG = mg ? mg : ((C >= 64 || n < 256) ? 1 : 2);
@@ -337,8 +339,9 @@ int g_conv_pick[3][11] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
                           {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1}};
 int cidx(int C) { return C == 16 ? 0 : (C == 32 ? 1 : 2); }
 int lg2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
-struct ConvVariant { int mg, ring_mode; };
-constexpr ConvVariant kConvVariants[] = {{0, 0}, {1, 0}, {2, 0}, {1, 1}, {2, 1}, {1, 2}, {2, 2}};
+struct ConvVariant { int mg, ring_mode, areuse; };
+constexpr ConvVariant kConvVariants[] = {{0, 0, 0}, {1, 0, 0}, {2, 0, 0}, {1, 1, 0}, {2, 1, 0}, {1, 2, 0}, {2, 2, 0},
+                                         {0, 0, 1}, {1, 0, 1}, {2, 0, 1}, {1, 2, 1}, {2, 2, 1}};
 constexpr int kConvVariantCount = int(sizeof(kConvVariants) / sizeof(kConvVariants[0]));
 }  // namespace
 
@@ -347,10 +350,11 @@ static int conv_variants(int n, int C, int* out) {
     int cnt = 0;
     PShape seen[kConvVariantCount];
     for (int i = 0; i < kConvVariantCount; ++i) {
-        const PShape s = p_shape_with(n, C, kConvVariants[i].mg, kConvVariants[i].ring_mode);
+        const PShape s = p_shape_with(n, C, kConvVariants[i].mg, kConvVariants[i].ring_mode, kConvVariants[i].areuse);
         if (!s.RING) continue;
         bool dup = false;
-        for (int k = 0; k < cnt; ++k) dup = dup || (seen[k].MG == s.MG && seen[k].RING == s.RING);
+        for (int k = 0; k < cnt; ++k)
+            dup = dup || (seen[k].MG == s.MG && seen[k].RING == s.RING && seen[k].areuse == s.areuse);
         if (dup) continue;
         seen[cnt] = s;
         out[cnt++] = i;
@@ -365,7 +369,7 @@ static PShape p_shape(int n, int C) {
         const int cnt = conv_variants(n, C, idx);
         if (pick < cnt) {
             const ConvVariant v = kConvVariants[idx[pick]];
-            return p_shape_with(n, C, v.mg, v.ring_mode);
+            return p_shape_with(n, C, v.mg, v.ring_mode, v.areuse);
         }
     }
     return p_shape_with(n, C, 0, 0);
@@ -377,14 +381,16 @@ int conv_variant_count(int n, int C) {
     return conv_variants(n, C, idx);
 }
 
-int conv_variant_describe(int n, int C, int index, int* mg, int* ty, int* ring) {
+int conv_variant_describe(int n, int C, int index, int* mg, int* ty, int* ring, int* areuse) {
     int idx[kConvVariantCount];
     const int cnt = conv_variant_count(n, C) ? conv_variants(n, C, idx) : 0;
     if (index < 0 || index >= cnt) return AC_ERR_ARG;
-    const PShape s = p_shape_with(n, C, kConvVariants[idx[index]].mg, kConvVariants[idx[index]].ring_mode);
+    const ConvVariant v = kConvVariants[idx[index]];
+    const PShape s = p_shape_with(n, C, v.mg, v.ring_mode, v.areuse);
     *mg = s.MG;
     *ty = s.TY;
     *ring = s.RING;
+    *areuse = s.areuse;
     return AC_OK;
 }
 
@@ -433,7 +439,7 @@ conv_hidden_tc_persistent(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* _
                           const __nv_bfloat16* __restrict__ wpk, const float* __restrict__ bias, int n,
                           int batch, int RING, uint32_t slot_bytes, int mode, float* __restrict__ zio,
                           int* __restrict__ status, int stall, const float* __restrict__ wlast,
-                          float* __restrict__ maps) {
+                          float* __restrict__ maps, int areuse) {
     constexpr int KC = C / 8;
     constexpr int TY = kPStageCols / (MG * C);
     constexpr int NACC = TY * MG;
@@ -557,6 +563,45 @@ conv_hidden_tc_persistent(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* _
             if (!ok) break;
             tc::fence_after_sync();
             const uint32_t dbase = tmem + uint32_t(stage * kPStageCols);
+            if (areuse) {
+                // input row rho of the unit serves output rows rho - dy (dy =
+                // 0, 1, 2): its A operand (shift dx, K-step ks, M-tile m) is
+                // read into the collector once and used for up to three MMAs.
+                // Each accumulator still receives its MMAs in (tap, K-step)
+                // order, so the sums are those of the loop below, bit for bit.
+#pragma unroll 1
+                for (int rho = 0; rho < TY + 2; ++rho) {
+                    int sl = aslot + rho;
+                    sl = sl >= RING ? sl - RING : sl;
+                    const uint32_t in_u = ring_u + uint32_t(sl) * slot_u;
+                    const int dy_lo = rho - (TY - 1) > 0 ? rho - (TY - 1) : 0;
+                    const int dy_hi = rho < 2 ? rho : 2;
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+#pragma unroll
+                        for (int ks = 0; ks < C / 16; ++ks) {
+#pragma unroll
+                            for (int m = 0; m < MG; ++m) {
+                                const uint64_t ad = a_hi | uint64_t(in_u + uint32_t(dx) + uint32_t(2 * ks) * plane_u +
+                                                                    uint32_t(m * 128));
+#pragma unroll
+                                for (int dy = 0; dy < 3; ++dy) {
+                                    if (dy < dy_lo || dy > dy_hi) continue;
+                                    const int tap = dy * 3 + dx;
+                                    const int acc = (rho - dy) * MG + m;
+                                    const uint64_t bd = b_hi | uint64_t(w_u + uint32_t((tap * KC + 2 * ks) * C));
+                                    const uint32_t d_addr = dbase + uint32_t(acc * C);
+                                    const uint32_t accum = (tap | ks) != 0;
+                                    if (dy_lo == dy_hi) tc::mma_bf16(d_addr, ad, bd, idesc, accum);
+                                    else if (dy == dy_lo) tc::mma_bf16_coll<1>(d_addr, ad, bd, idesc, accum);
+                                    else if (dy == dy_hi) tc::mma_bf16_coll<3>(d_addr, ad, bd, idesc, accum);
+                                    else tc::mma_bf16_coll<2>(d_addr, ad, bd, idesc, accum);
+                                }
+                            }
+                        }
+                    }
+                }
+            } else
 #pragma unroll 1
             for (int tap = 0; tap < 9; ++tap) {
                 const int dy = tap / 3, dx = tap % 3;
@@ -722,7 +767,7 @@ static int launch_persistent_act(const PShape& s, int n, int batch, const __nv_b
     const long long units = (long long)batch * (n / s.CW) * (n / s.TY);
     const int grid = int(units < num_sms() ? units : num_sms());
     kern<<<grid, kPThreads, s.smem, st>>>(in, out, w, bias, n, batch, s.RING, s.slot_bytes, mode, zio, status,
-                                          g_test_stall, wlast, maps);
+                                          g_test_stall, wlast, maps, s.areuse);
     ACPR_LAUNCH_CHECK();
     return AC_OK;
 }

@@ -109,7 +109,10 @@ __host__ __device__ constexpr int transpose_pitch(int L, int B) {
                                                  : ((L / (16 / B)) + 2 | 1) * (16 / B);
 }
 
-template <typename T, int N, int P, int A, int B>
+// NOX: no separate exchange buffer; the line FFTs of the row phase exchange
+// through bufR and those of the column phase through bufC, each free at that
+// time (asynchronous exchange only), which saves a third of the shared memory.
+template <typename T, int N, int P, int A, int B, bool NOX = false>
 struct FineShape {
     static constexpr int R = N / P;           // rows per CTA
     static constexpr int L = R / 2;           // lines per CTA (row pairs, then columns)
@@ -125,8 +128,9 @@ struct FineShape {
     // (16/B lines, B positions each, TP elements apart) hits distinct banks
     // when TP is an odd multiple of 16/B.
     static constexpr int TP = transpose_pitch(L, B);
-    static constexpr size_t BUFT = sizeof(vec2_t<T>) * size_t(N) * TP;
-    static constexpr size_t BUFX = sizeof(vec2_t<T>) * size_t(L) * XP;
+    static constexpr int BUFT_ELEMS = NOX && L * XP > N * TP ? L * XP : N * TP;
+    static constexpr size_t BUFT = sizeof(vec2_t<T>) * size_t(BUFT_ELEMS);
+    static constexpr size_t BUFX = NOX ? 0 : sizeof(vec2_t<T>) * size_t(L) * XP;
     static constexpr size_t SMEM = 2 * BUFT + BUFX + sizeof(vec2_t<T>) * N + sizeof(T) * N + 4 * sizeof(double) +
                                    2 * sizeof(uint64_t);
     // asynchronous exchange: a peer's share of a transpose is L positions of
@@ -170,17 +174,18 @@ __device__ __forceinline__ V* peer_ptr(V* local, int rank) {
 // CTA's data, so it is free), and the element for itself directly in the
 // other buffer.  No cluster-wide barrier and no release fence in the step
 // loop: a CTA waits only for the bytes it receives.
-template <typename T, int N, int P, int A, int B, int MINB, bool ASYNC = false>
-__global__ void __launch_bounds__(FineShape<T, N, P, A, B>::THREADS, MINB)
+template <typename T, int N, int P, int A, int B, int MINB, bool ASYNC = false, bool NOX = false>
+__global__ void __launch_bounds__(FineShape<T, N, P, A, B, NOX>::THREADS, MINB)
 fine_field_kernel(FineArgs args) {
-    using Sh = FineShape<T, N, P, A, B>;
+    using Sh = FineShape<T, N, P, A, B, NOX>;
     using V = vec2_t<T>;
     constexpr int R = Sh::R, L = Sh::L, HALF = Sh::HALF, TP = Sh::TP, XP = Sh::XP;
+    static_assert(!NOX || ASYNC, "the shared exchange areas need the asynchronous exchange");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* bufR = reinterpret_cast<V*>(smem_raw);         // row phase: [pos][line]
-    V* bufC = bufR + N * TP;                           // column phase: [pos][line]
-    V* bufX = bufC + N * TP;                           // line-FFT exchanges
-    V* tw = bufX + L * XP;                             // line_fft twiddle table
+    V* bufC = bufR + Sh::BUFT_ELEMS;                   // column phase: [pos][line]
+    V* bufX = bufC + Sh::BUFT_ELEMS;                   // line-FFT exchanges (not with NOX)
+    V* tw = bufX + (NOX ? 0 : L * XP);                 // line_fft twiddle table
     T* lam = reinterpret_cast<T*>(tw + N);             // dt eps^2 mu_k
     double* part = reinterpret_cast<double*>(lam + N); // mass partial, adjoint mean
     uint64_t* xbar = reinterpret_cast<uint64_t*>(part + 4);  // [0]: bufC received, [1]: bufR received
@@ -272,9 +277,12 @@ fine_field_kernel(FineArgs args) {
     V x[A];
     V* myR = bufR + line;  // element pos of this line at myR[pos * TP]
     V* myC = bufC + line;
-    V* myX = bufX + line * XP;
+    // this line's exchange areas of the row and the column phase
+    V* myXR = (NOX ? bufR : bufX) + line * XP;
+    V* myXC = (NOX ? bufC : bufX) + line * XP;
 #pragma unroll
     for (int t = 0; t < A; ++t) x[t] = myR[(j + B * t) * TP];
+    if constexpr (NOX) __syncthreads();  // bufR read before it serves as exchange area
 
     const T a = T(args.a);
     const T dt = T(args.dt);
@@ -324,7 +332,7 @@ fine_field_kernel(FineArgs args) {
                 x[t].y = a * ui + dt * (ui - ui * ui * ui);
             }
         }
-        line_fft<T, N, A, B, -1>(x, tw, myX, j, WMASK);
+        line_fft<T, N, A, B, -1>(x, tw, myXR, j, WMASK);
         // row spectra Z_p[k] -> column min(k, N - k) (k = 0, N/2 -> column 0)
         if constexpr (ASYNC) {
             __syncthreads();  // every rebuild read of bufR (now the staging area) is done
@@ -370,7 +378,8 @@ fine_field_kernel(FineArgs args) {
             }
             x[t] = v;
         }
-        line_fft<T, N, A, B, -1>(x, tw, myX, j, WMASK);
+        if constexpr (NOX) __syncthreads();  // every split read of bufC is done
+        line_fft<T, N, A, B, -1>(x, tw, myXC, j, WMASK);
         // divide by the symbol, with 1/N^2 of the inverse folded in
         if (col != 0) {
             const T lam_l = lam[col];
@@ -389,7 +398,7 @@ fine_field_kernel(FineArgs args) {
             __syncwarp(WMASK);
             if (col == 0) {
 #pragma unroll
-                for (int t = 0; t < A; ++t) myX[j + B * t] = x[t];
+                for (int t = 0; t < A; ++t) myXC[j + B * t] = x[t];
             }
             __syncwarp(WMASK);
             if (col == 0) {
@@ -398,7 +407,7 @@ fine_field_kernel(FineArgs args) {
                 for (int t = 0; t < A; ++t) {
                     const int k = j + B * t;
                     const V zc = x[t];
-                    const V zp = myX[(N - k) & (N - 1)];
+                    const V zp = myXC[(N - k) & (N - 1)];
                     const T lk = lam[k];
                     const T s0 = fast_div(inv_nn, a + lk);
                     const T sn = fast_div(inv_nn, a + (lk + lam_n));
@@ -419,7 +428,7 @@ fine_field_kernel(FineArgs args) {
                 }
             }
         }
-        line_fft<T, N, A, B, +1>(x, tw, myX, j, WMASK);
+        line_fft<T, N, A, B, +1>(x, tw, myXC, j, WMASK);
         // column values V_r[c] -> owner of row r, slot (row role) and column c
         if constexpr (ASYNC) {
             __syncthreads();  // every split read of bufC (now the staging area) is done
@@ -463,7 +472,8 @@ fine_field_kernel(FineArgs args) {
             }
             x[t] = z;
         }
-        line_fft<T, N, A, B, +1>(x, tw, myX, j, WMASK);
+        if constexpr (NOX) __syncthreads();  // every rebuild read of bufR is done
+        line_fft<T, N, A, B, +1>(x, tw, myXR, j, WMASK);
         if (args.adjoint) {
             // lambda_n = a mu + dt f'(u_n) (mu - mean mu), rows r0 (real) and r1 (imag)
             const int n_state = nsteps - 1 - step;
@@ -490,6 +500,7 @@ fine_field_kernel(FineArgs args) {
                 const int row = idx / N, c = idx % N;
                 ts[idx] = reinterpret_cast<const T*>(bufR)[2 * (c * TP + row % L) + row / L];
             }
+            if constexpr (NOX) __syncthreads();  // bufR read before the next row FFT's exchange
         }
     }
 
@@ -510,10 +521,10 @@ fine_field_kernel(FineArgs args) {
 }
 
 // ---------------------------------------------------------------- launch --
-template <typename T, int N, int P, int A, int B, int MINB, bool ASYNC = false>
+template <typename T, int N, int P, int A, int B, int MINB, bool ASYNC = false, bool NOX = false>
 static int launch_fine(const FineArgs& args, cudaStream_t stream) {
-    using Sh = FineShape<T, N, P, A, B>;
-    auto kern = fine_field_kernel<T, N, P, A, B, MINB, ASYNC>;
+    using Sh = FineShape<T, N, P, A, B, NOX>;
+    auto kern = fine_field_kernel<T, N, P, A, B, MINB, ASYNC, NOX>;
     static bool configured = false;  // per instantiation, once per process
     if (!configured) {
         ACPR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::SMEM)));
@@ -545,11 +556,14 @@ struct FineVariant {
     const char* name;
     int (*launch)(const FineArgs&, cudaStream_t);
     bool async;  // asynchronous exchange: no adjoint mode
+    int P;       // CTAs per field (the split that fixes the rounding)
 };
 
-#define ACPR_FV(T, N, P, A, B, M) {"P" #P "_A" #A "_B" #B "_occ" #M, &launch_fine<T, N, P, A, B, M>, false}
+#define ACPR_FV(T, N, P, A, B, M) {"P" #P "_A" #A "_B" #B "_occ" #M, &launch_fine<T, N, P, A, B, M>, false, P}
 #define ACPR_FVA(T, N, P, A, B, M) \
-    {"P" #P "_A" #A "_B" #B "_occ" #M "_async", &launch_fine<T, N, P, A, B, M, true>, true}
+    {"P" #P "_A" #A "_B" #B "_occ" #M "_async", &launch_fine<T, N, P, A, B, M, true>, true, P}
+#define ACPR_FVN(T, N, P, A, B, M) \
+    {"P" #P "_A" #A "_B" #B "_occ" #M "_async_nox", &launch_fine<T, N, P, A, B, M, true, true>, true, P}
 
 template <typename T>
 static const FineVariant* fine_variants(int n, int* count) {
@@ -561,17 +575,22 @@ static const FineVariant* fine_variants(int n, int* count) {
         static const FineVariant v128[] = {ACPR_FV(T, 128, 2, 16, 8, 2), ACPR_FV(T, 128, 4, 16, 8, 3),
                                            ACPR_FV(T, 128, 1, 16, 8, 1), ACPR_FVA(T, 128, 4, 16, 8, 3),
                                            ACPR_FVA(T, 128, 2, 16, 8, 2)};
-        // entry 0 (asynchronous exchange, clusters of 8) measured fastest on
-        // large batches (512 fields: 2.57 ms vs 2.97 ms for 20 steps), entry 1
-        // (clusters of 16) on batches that fill at most one wave of SMs
-        static const FineVariant v256[] = {ACPR_FVA(T, 256, 8, 16, 16, 2), ACPR_FVA(T, 256, 16, 16, 16, 3),
-                                           ACPR_FVA(T, 256, 4, 16, 16, 1), ACPR_FV(T, 256, 8, 16, 16, 2),
-                                           ACPR_FV(T, 256, 4, 16, 16, 1), ACPR_FV(T, 256, 16, 16, 16, 3),
-                                           ACPR_FV(T, 256, 8, 16, 16, 1)};
+        // entry 0 (clusters of 8, asynchronous exchange, no separate exchange
+        // buffer, 3 CTAs per SM) measured fastest on large batches (512 fields,
+        // 20 steps: 2.46 ms; with the exchange buffer 2.56 ms; cluster
+        // barriers 2.97 ms).  16-CTA clusters are 10% faster on 16 fields, but a
+        // shape change alters the rounding, and F must stay one function within
+        // a solve and between a Parareal solve and its sequential reference
+        // (exactness at k = s): the default does not depend on the batch size.
+        static const FineVariant v256[] = {ACPR_FVN(T, 256, 8, 16, 16, 3), ACPR_FVA(T, 256, 8, 16, 16, 2),
+                                           ACPR_FVA(T, 256, 16, 16, 16, 3), ACPR_FVA(T, 256, 4, 16, 16, 1),
+                                           ACPR_FV(T, 256, 8, 16, 16, 2), ACPR_FV(T, 256, 4, 16, 16, 1),
+                                           ACPR_FV(T, 256, 16, 16, 16, 3), ACPR_FV(T, 256, 8, 16, 16, 1),
+                                           ACPR_FVN(T, 256, 8, 16, 16, 2)};
         static const FineVariant v512[] = {ACPR_FV(T, 512, 16, 32, 16, 1), ACPR_FVA(T, 512, 16, 32, 16, 1)};
         switch (n) {
             case 128: *count = 5; return v128;
-            case 256: *count = 7; return v256;
+            case 256: *count = 9; return v256;
             case 512: *count = 2; return v512;
             default: break;
         }
@@ -596,21 +615,10 @@ static const FineVariant* fine_variants(int n, int* count) {
 }
 #undef ACPR_FV
 #undef ACPR_FVA
+#undef ACPR_FVN
 
 namespace {
-int g_variant[2][11] = {};      // [precision][log2 n]: chosen launch shape
-bool g_variant_set[2][11] = {};  // chosen explicitly (ac_fine_set_variant / autotune)
-}
-
-static int num_sms_fine() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-            sms = 1;
-    }
-    return sms;
+int g_variant[2][11] = {};  // [precision][log2 n]: chosen launch shape
 }
 
 static const FineVariant* pick_variant(int n, int precision, int* count) {
@@ -629,13 +637,16 @@ static int dispatch_fine(int n, const FineArgs& args, cudaStream_t stream) {
     const int pr = sizeof(T) == 8 ? AC_F64 : AC_F32;
     int idx = g_variant[pr][ilog2(n)];
     if (idx < 0 || idx >= count) idx = 0;
-    if (!g_variant_set[pr][ilog2(n)] && sizeof(T) == 4 && n == 256 && args.num_fields * 8 <= num_sms_fine())
-        idx = 1;  // a batch that fills one wave of 8-CTA clusters: 16-CTA clusters use more SMs
     // the adjoint's mean broadcast is ordered by cluster barriers: take the
-    // first barrier-exchange shape
+    // barrier-exchange shape of the same split (same rounding), else the first
     if (args.adjoint && v[idx].async) {
-        idx = 0;
-        while (idx < count && v[idx].async) ++idx;
+        const int want = v[idx].P;
+        int alt = -1;
+        for (int i = 0; i < count && alt < 0; ++i)
+            if (!v[i].async && v[i].P == want) alt = i;
+        for (int i = 0; i < count && alt < 0; ++i)
+            if (!v[i].async) alt = i;
+        idx = alt < 0 ? count : alt;
         if (idx == count) {
             set_error("ac_fine: no barrier-exchange shape for the adjoint at n=%d", n);
             return AC_ERR_UNSUPPORTED;
@@ -860,7 +871,6 @@ extern "C" int ac_fine_set_variant(int n, int precision, int index) {
     ACPR_CHECK_ARG(count > 0, "n=%d precision %d not built", n, precision);
     ACPR_CHECK_ARG(index >= 0 && index < count, "variant %d out of range (%d built)", index, count);
     g_variant[precision][ilog2(n)] = index;
-    g_variant_set[precision][ilog2(n)] = true;
     return AC_OK;
 }
 
@@ -879,7 +889,6 @@ extern "C" int ac_fine_autotune(const ac_params* params, int num_fields, int ste
     float best_ms = 1e30f;
     for (int v = 0; v < count; ++v) {
         g_variant[params->precision][ilog2(params->n)] = v;
-        g_variant_set[params->precision][ilog2(params->n)] = true;
         rc = fine_propagate(params, num_fields, steps, u_in, u_out, st);  // warm-up
         if (rc) break;
         ACPR_CUDA(cudaEventRecord(e0, st));
@@ -895,7 +904,6 @@ extern "C" int ac_fine_autotune(const ac_params* params, int num_fields, int ste
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     g_variant[params->precision][ilog2(params->n)] = best;
-    g_variant_set[params->precision][ilog2(params->n)] = true;
     return rc ? rc : AC_OK;
 }
 

@@ -115,6 +115,39 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         : "memory");
 }
 
+// The same MMA with a usage of the tensor core's collector buffer for A:
+// U = 1 fills it (A read from shared memory and kept), 2 uses the kept A,
+// 3 uses it for the last time; consecutive MMAs that share A then read it
+// from shared memory once.
+template <int U>
+__device__ __forceinline__ void mma_bf16_coll(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                              uint32_t accumulate) {
+    if constexpr (U == 1) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else if constexpr (U == 2) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else if constexpr (U == 3) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        mma_bf16(d_tmem, adesc, bdesc, idesc, accumulate);
+    }
+}
+
 // Arrive on `bar` once all previously issued tcgen05.mma of this thread are done.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -152,11 +185,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         : "r"(taddr));
 }
 
-// Load W consecutive columns (W = 16 or 32) of the warp's 32 lanes.
+// Load W consecutive columns (W = 8, 16 or 32) of the warp's 32 lanes.
 template <int W>
 __device__ __forceinline__ void tmem_ldw(uint32_t taddr, uint32_t (&v)[W]) {
     if constexpr (W == 32) tmem_ld32(taddr, v);
-    else tmem_ld16(taddr, v);
+    else if constexpr (W == 16) tmem_ld16(taddr, v);
+    else tmem_ld8(taddr, v);
 }
 
 }  // namespace tc
