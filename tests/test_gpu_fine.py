@@ -206,3 +206,21 @@ def test_propagate_1024_two_pass(variant):
         assert abs(got[0].mean() - u[0].astype(np.float64).mean()) < 1e-7
     zero = G.ac_fine_propagate_slices(fp, 0, dev(u, torch.float32)).cpu().numpy()
     assert np.array_equal(zero, u)
+
+
+def test_propagate_1024_with_caller_workspace():
+    """ac_fine_propagate_slices_ws: the 1024^2 path with the caller's
+    workspace gives the same bits as with the library's own, and a workspace
+    one byte too small is rejected before any launch."""
+    n, steps = 1024, 3
+    u = dev(np.stack([I.random_field(n, seed=70 + i) for i in range(2)]).astype(np.float32), torch.float32)
+    fp = G.FineParams(n, 0.004, 2.0, 2e-5, variant=G.AC_CLASSIC, precision=G.AC_F32)
+    ref = G.ac_fine_propagate_slices(fp, steps, u)
+    nbytes = G.ac_fine_workspace_bytes(n, 2, G.AC_F32)
+    assert nbytes > 0 and G.ac_fine_workspace_bytes(256, 2, G.AC_F32) == 0
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    out = torch.empty_like(u)
+    G.ac_fine_propagate_slices_ws(fp, steps, u, out, ws)
+    assert torch.equal(out, ref)
+    with pytest.raises(G.AcprError, match="AC_ERR_ARG"):
+        G.ac_fine_propagate_slices_ws(fp, steps, u, out, ws[: nbytes - 1])
