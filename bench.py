@@ -204,7 +204,7 @@ def run_uneven(args):
         c_choice = None
         if G.cnn_conv_variants(n, 32):
             c_ms, c_idx = G.cnn_autotune(net, u0)
-            c_choice = {"shape_mtiles_rows_ring_areuse": list(G.cnn_conv_variants(n, 32)[c_idx]),
+            c_choice = {"shape_ring_slots": list(G.cnn_conv_variants(n, 32)[c_idx]),
                         "ms": {str(k): v for k, v in c_ms.items()}}
         tuned[str(n)] = {"fine": G.ac_fine_variants(n, G.AC_F32)[f_idx], "fine_ms_per_20_steps": f_ms,
                          "conv": c_choice}

@@ -238,20 +238,18 @@ int cnn_pack_weights(const cnn_desc* desc, acpr_stream stream);
 int cnn_coarse_step(const cnn_desc* desc, int n, int batch, const void* u_in, void* u_out,
                     acpr_stream stream);
 
-/* Tile shapes of the persistent tensor-core conv kernel (n a multiple of
- * 128, channels 16, 32 or 64): M-tiles of 128 pixels per row segment, output
- * rows per work unit, depth of the input-row ring, and whether MMAs that share
- * an input row read its A operand once through the tensor core's collector
- * buffer (areuse).  Every shape computes
- * the same sums in the same order (results are identical); they differ in
- * speed.  cnn_conv_set_variant(n, C, -1) restores the automatic choice.
+/* Shapes of the persistent row-streaming tensor-core conv kernel (n a
+ * multiple of 128, channels 16, 32 or 64): depth of the ring of input rows in
+ * shared memory (`ring`) and number of TMEM accumulator slots of 3C columns
+ * (`slots`).  Every shape computes the same sums in the same order (results
+ * are identical); they differ in speed.  cnn_conv_set_variant(n, C, -1) restores the automatic choice.
  * cnn_autotune times every shape on the caller's problem (u_in -> u_out,
  * `batch` fields, three calls after a warm-up; ms per call into ms_out[i],
  * may be NULL), keeps the fastest for (n, C) and synchronises `stream`.
  * Process-wide host state, not thread-safe; a Parareal handle's captured
  * graphs keep the shape they were captured with. */
 int cnn_conv_variant_count(int n, int channels);
-int cnn_conv_variant_shape(int n, int channels, int index, int* mtiles, int* rows, int* ring, int* areuse);
+int cnn_conv_variant_shape(int n, int channels, int index, int* ring, int* slots);
 int cnn_conv_set_variant(int n, int channels, int index);
 int cnn_conv_get_variant(int n, int channels);
 int cnn_autotune(const cnn_desc* desc, int n, int batch, const void* u_in, void* u_out, float* ms_out,

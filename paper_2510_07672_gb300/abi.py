@@ -134,7 +134,7 @@ def load(build_if_missing: bool = True):
         L.ac_energy_gradient_ic.argtypes = [P(ac_params), I, I, S, S, S, C.c_size_t, S]
         L.ac_conv_status.argtypes = [S, S]
         L.cnn_conv_variant_count.argtypes = [I, I]
-        L.cnn_conv_variant_shape.argtypes = [I, I, I, P(I), P(I), P(I), P(I)]
+        L.cnn_conv_variant_shape.argtypes = [I, I, I, P(I), P(I)]
         L.cnn_conv_set_variant.argtypes = [I, I, I]
         L.cnn_conv_get_variant.argtypes = [I, I]
         L.cnn_autotune.argtypes = [P(cnn_desc), I, I, S, S, P(C.c_float), S]
@@ -782,14 +782,14 @@ def cnn_coarse_step(net: CoarseNet, u_in, u_out=None, stream=None):
 
 
 def cnn_conv_variants(n: int, channels: int):
-    """[(M-tiles per row segment, rows per unit, ring depth, A reuse)] of the
-    persistent tensor-core conv for (n, channels)."""
+    """[(input-ring depth, TMEM slots)] of the persistent row-streaming
+    tensor-core conv for (n, channels)."""
     L = load()
     out = []
     for i in range(L.cnn_conv_variant_count(int(n), int(channels))):
-        a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
-        _check(L.cnn_conv_variant_shape(int(n), int(channels), i, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
-        out.append((a.value, b.value, c.value, d.value))
+        a, b = C.c_int(), C.c_int()
+        _check(L.cnn_conv_variant_shape(int(n), int(channels), i, C.byref(a), C.byref(b)))
+        out.append((a.value, b.value))
     return out
 
 

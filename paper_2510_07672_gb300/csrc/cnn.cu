@@ -613,11 +613,10 @@ extern "C" int cnn_coarse_step(const cnn_desc* desc, int n, int batch, const voi
 
 extern "C" int cnn_conv_variant_count(int n, int channels) { return acpr::conv_variant_count(n, channels); }
 
-extern "C" int cnn_conv_variant_shape(int n, int channels, int index, int* mtiles, int* rows, int* ring,
-                                      int* areuse) {
+extern "C" int cnn_conv_variant_shape(int n, int channels, int index, int* ring, int* slots) {
     using namespace acpr;
-    ACPR_CHECK_ARG(mtiles && rows && ring && areuse, "null output");
-    const int rc = conv_variant_describe(n, channels, index, mtiles, rows, ring, areuse);
+    ACPR_CHECK_ARG(ring && slots, "null output");
+    const int rc = conv_variant_describe(n, channels, index, ring, slots);
     if (rc) set_error("cnn_conv_variant_shape: index %d out of range", index);
     return rc;
 }

@@ -31,6 +31,69 @@ __device__ __forceinline__ float phi_as(float x) {
     return x >= 0.0f ? 1.0f - q : q;
 }
 
+// Paired float32 arithmetic: two lanes in one 64-bit register, operated on by
+// the sm_100-family .f32x2 instructions (one issue for two results), each
+// lane rounded exactly as the scalar add / mul / fma.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2split(f32x2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// Hardware approximations: 1/x and 2^x (PTX rcp.approx, ex2.approx).
+__device__ __forceinline__ float rcp_hw(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_hw(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// GELU x Phi(x) of two lanes with the paired instructions: the same
+// Abramowitz & Stegun 7.1.26 form as phi_as, q = Phi(-|x|) = erfc(z)/2 with
+// the 1/2 folded into the coefficients (exact: a power of two) and
+// exp(-z^2) = 2^(-x^2 log2(e) / 2); then x Phi(x) = max(x, 0) - |x| q for
+// either sign of x.
+__device__ __forceinline__ f32x2 gelu2(f32x2 x) {
+    float x0, x1;
+    f2split(x, x0, x1);
+    const f32x2 nx = f2(-fabsf(x0), -fabsf(x1));
+    const f32x2 rx = f2(fmaxf(x0, 0.0f), fmaxf(x1, 0.0f));
+    const f32x2 z = f2_mul(nx, f2(-0.70710678118654752440f, -0.70710678118654752440f));
+    float d0, d1;
+    f2split(f2_fma(z, f2(0.3275911f, 0.3275911f), f2(1.0f, 1.0f)), d0, d1);
+    const f32x2 t = f2(rcp_hw(d0), rcp_hw(d1));
+    f32x2 p = f2_fma(t, f2(0.5307027145f, 0.5307027145f), f2(-0.7265760135f, -0.7265760135f));
+    p = f2_fma(t, p, f2(0.7107068705f, 0.7107068705f));
+    p = f2_fma(t, p, f2(-0.142248368f, -0.142248368f));
+    p = f2_fma(t, p, f2(0.127414796f, 0.127414796f));
+    float w0, w1;  // -x^2 log2(e) / 2
+    f2split(f2_mul(f2_mul(x, x), f2(-0.72134752044448170368f, -0.72134752044448170368f)), w0, w1);
+    const f32x2 q = f2_mul(f2_mul(p, t), f2(ex2_hw(w0), ex2_hw(w1)));  // Phi(-|x|)
+    return f2_fma(nx, q, rx);
+}
+
 // Activation after every conv but the last: tanh, or GELU x * Phi(x)
 // (float32: Phi by phi_as; float64: 0.5 (1 + erf(x / sqrt 2))).
 __device__ __forceinline__ float act_apply_gelu(float x) { return x * phi_as(x); }
@@ -50,6 +113,18 @@ template <int ACT>
 __device__ __forceinline__ float act_c(float x) {
     if constexpr (ACT == AC_ACT_TANH) return tanhf(x);
     else return act_apply_gelu(x);
+}
+
+// act_c of two lanes (GELU with the paired instructions).
+template <int ACT>
+__device__ __forceinline__ f32x2 act2(f32x2 x) {
+    if constexpr (ACT == AC_ACT_TANH) {
+        float a, b;
+        f2split(x, a, b);
+        return f2(tanhf(a), tanhf(b));
+    } else {
+        return gelu2(x);
+    }
 }
 
 int check_cnn(const cnn_desc* d);
@@ -130,10 +205,10 @@ int hidden_layer_bf16(const cnn_desc* d, int l, int n, int batch, const __nv_bfl
 // nine tap sums of W_last (bf16-rounded) with the layer's bf16 activations;
 // act_out gets the activations and zsave the pre-activations only when zsave
 // is not NULL (training).  AC_ERR_UNSUPPORTED for other shapes.
-// Tile shapes of the persistent tensor-core kernel for (n, C) that a tuner
-// may choose (M-tiles per row segment, rows per unit, input-ring depth).
+// Shapes of the persistent row-streaming kernel for (n, C) that a tuner may
+// choose (input-ring depth, TMEM slots).
 int conv_variant_count(int n, int C);
-int conv_variant_describe(int n, int C, int index, int* mg, int* ty, int* ring, int* areuse);
+int conv_variant_describe(int n, int C, int index, int* ring, int* slots);
 int conv_set_variant(int n, int C, int index);  // -1: automatic
 int conv_get_variant(int n, int C);
 

@@ -20,6 +20,8 @@
 // sets the caller's status word (the first int of the conv workspace), which
 // conv_check_status() reports as AC_ERR_TIMEOUT.
 // Fields with n >= 128 take the persistent, warp-specialised kernel below.
+#include <algorithm>
+
 #include "cnn.cuh"
 #include "tc_ptx.cuh"
 
@@ -262,117 +264,472 @@ conv_hidden_tc_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __res
     if (warp == 0) tc::tmem_dealloc(tmem, uint32_t(ncols));
 }
 
-// ------------------------------------------------------------ persistent --
-// Persistent, warp-specialised form of the same GEMM for n >= 128 (n a
-// multiple of 128), one CTA per SM.  Work unit = (field f, column block cb,
-// row block yb): TY output rows y0 = yb TY .. y0 + TY - 1, each cut into MG
-// M-tiles of 128 consecutive positions, columns [cb CW, cb CW + CW),
-// CW = 128 MG.  Units are ordered (f, cb, yb) and CTA c takes a contiguous
-// range of them, so consecutive units of a CTA mostly slide down TY rows and
-// need TY new input rows.
-//   warp 0 (lane 0), producer: input row segments (the CW columns of a row
-//     plus one wrapped pixel on each side, all C/8 chunk planes) into a ring
-//     of RING slots by cp.async.bulk, each completing on full[slot];
-//   warp 1 (lane 0), MMA issuer: for tap (dy, dx) the A operand of output row
-//     y0 + r, M-tile m, is slot(row y0 + r - 1 + dy) read from pixel
-//     m*128 + dx, so an M-tile never leaves its slot.  The TY * MG
-//     accumulators of a unit fill one of two TMEM stages of 256 columns.
-//     Descriptors are formed by integer adds on their start-address field, so
-//     issuing an MMA costs a few instructions.  tcgen05.commit marks the stage
-//     full and releases (empty[slot]) the input rows no later unit reads;
-//   warps 2..17, epilogue: tcgen05.ld of the stage, bias + activation (or the
-//     act' product), bf16 16-byte stores; then the stage is marked empty.
-// Loads of later rows, MMAs of the next unit and the epilogue of the current
-// one overlap.  Every output is the same sum in the same order (tap, then
-// K-step) as in the one-shot kernel, so both produce the same bits.  Every
-// wait is bounded and also stops once another role has given up (abort flag
-// in shared memory); before exit the CTA drains its in-flight copies and MMAs
-// and frees TMEM.
-constexpr int kPEpiWarps = 16;
-constexpr int kPThreads = 32 * (2 + kPEpiWarps);
-constexpr int kPStages = 2;
-constexpr int kPStageCols = 256;
-constexpr int kPMaxRing = 16;
+// Bounded wait on phase `parity` of `bar` by one role of a warp-specialised
+// kernel: gives up once another role has given up (abort flag in shared
+// memory) or after `limit` polls, then raises the abort flag and stores 3 in
+// the caller's status word.
+__device__ __forceinline__ bool p_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                       long long limit = kTcSpin) {
+    for (long long i = 0; i < limit; ++i) {
+        if (tc::mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        __nanosleep(32);
+    }
+    *abort_flag = 1;
+    atomicExch(status, 3);
+    return false;
+}
 
-struct PShape {
-    int MG = 0, CW = 0, TY = 0, RING = 0;
-    int areuse = 0;  // MMAs that share an input row read its A operand once (collector buffer)
-    uint32_t slot_bytes = 0;
+// ------------------------------------------------------- row streaming --
+// Persistent kernel that reads each input row once and folds the vertical
+// taps in TMEM.  Output row y of a 3x3 conv is
+//   out(y) = D(y-1)[dy=0] + D(y)[dy=1] + D(y+1)[dy=2],
+//   D(y')[dy](x, co) = sum_dx sum_ci in(y', x + dx - 1, ci) W(dy, dx, ci, co),
+// so one GEMM per input row y' (M = 128 positions, N = 3C = (dy, co),
+// K = 3 (dx) x C (ci)) gives the row's contribution to three output rows.
+// N = 3C keeps the tensor core busier per byte of A read from shared memory
+// than the tap-major form (N = C, each input row read nine times).
+// Work unit = one output row of one 128-column block (field f, block cb, row
+// y), ordered (f, cb, y); CTA c takes a contiguous range and streams the input
+// rows y-1, y, y+1 at the start of a block run and one new row (y+1) per unit
+// after that.
+//   warp 0 (lane 0), producer: each streamed input row (128 columns plus one
+//     wrapped pixel each side, all C/8 chunk planes) into a ring slot by
+//     cp.async.bulk, completing on full[slot];
+//   warp 1 (lane 0), MMA issuer: 3 x C/16 MMAs of 128 x 3C x 16 per streamed
+//     row into TMEM slot j % DS (DS slots of 3C columns, padded); tcgen05.commit
+//     releases the ring slot (empty) and marks the TMEM slot full (dfull);
+//   warps 2..17, epilogue: a warp reads its TMEM lane quarter and its C/32
+//     (at least one) 8-channel chunks of the three dy blocks, frees the TMEM
+//     slot (dempty) and keeps two partial output rows in registers:
+//       finish out(y'-1) = P + D(y')[2];  P = P' + D(y')[1];  P' = D(y')[0].
+//     Every output is ((D(y-1)[0] + D(y)[1]) + D(y+1)[2]) + bias with each
+//     D accumulated over (dx, K-step) in order, whatever the ring depth, TMEM
+//     slot count or CTA count: G is bitwise the same under every shape.
+// kFwdLast: the nine-tap projection of each pixel's activations is summed
+// per warp over its channels and then over the warps of a lane quarter in a
+// fixed order through shared memory.
+constexpr int kRMaxRing = 24;
+constexpr int kRMaxD = 5;
+
+struct RCtl {
+    uint64_t never;  // test hook: nothing ever arrives here
+    uint64_t full[kRMaxRing];
+    uint64_t empty[kRMaxRing];
+    uint64_t dfull[kRMaxD];
+    uint64_t dempty[kRMaxD];
+    uint64_t qbar[2][4];  // kFwdLast: the partial projections of a lane quarter are in shared memory
+    uint64_t fin;  // completion of every MMA the CTA issued
+    uint32_t tmem;
+    int abort;
+    alignas(16) float bias[64];
+    alignas(16) float wl[64 * 10];  // kFwdLast: bf16-rounded last-layer weights [channel][tap], tap 9 = 0
+};
+constexpr size_t kRCtlBytes = 4096;
+constexpr size_t kRScratchBytes = size_t(2) * 4 * 4 * 9 * 32 * sizeof(float);  // [2][quarter][warp][tap][lane]
+
+// TMEM columns of one slot: 3C rounded up to a power of two, so that every
+// slot starts on a multiple of its own width.
+__host__ __device__ constexpr int r_dcols(int C) { return C <= 16 ? 64 : (C <= 32 ? 128 : 256); }
+__host__ __device__ constexpr uint32_t r_slot_bytes(int C) { return uint32_t(C / 8) * 130u * 16u; }
+
+// Position in a ring of `size` entries: index and the parity of the pass
+// over the ring (the mbarrier phase it waits for), advanced without division.
+struct RingPos {
+    int idx = 0;
+    uint32_t phase = 0;
+    int size;
+    __device__ explicit RingPos(int sz) : size(sz) {}
+    __device__ void next() {
+        if (++idx == size) {
+            idx = 0;
+            phase ^= 1u;
+        }
+    }
+};
+
+// Output row (field f, column block cb, row y) of work unit u, advanced by
+// one unit at a time (one division per CTA, none in the loops).
+struct RowCursor {
+    int y, cb, NB, n;
+    long long f;
+    __device__ RowCursor(long long u, int n_, int nb) : NB(nb), n(n_) {
+        y = int(u % n_);
+        const long long t = u / n_;
+        cb = int(t % nb);
+        f = t / nb;
+    }
+    __device__ void next() {
+        if (++y == n) {
+            y = 0;
+            if (++cb == NB) {
+                cb = 0;
+                ++f;
+            }
+        }
+    }
+};
+
+// Epilogue geometry: CPW 8-channel chunks per warp, EPW warps per TMEM lane
+// quarter, THREADS = producer + MMA warps + 4 EPW epilogue warps.
+template <int C>
+struct RGeom {
+    static constexpr int KC = C / 8;
+    static constexpr int CPW = KC >= 4 ? KC / 4 : 1;
+    static constexpr int EPW = KC / CPW;
+    static constexpr int THREADS = 32 * (2 + 4 * EPW);
+};
+
+template <int C, int ACT>
+__global__ void __launch_bounds__(RGeom<C>::THREADS, 1)
+conv_rows_tc(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ out,
+             const __nv_bfloat16* __restrict__ wpk, const float* __restrict__ bias, int n, int batch, int RING,
+             int DS, int mode, float* __restrict__ zio, int* __restrict__ status, int stall,
+             const float* __restrict__ wlast, float* __restrict__ maps) {
+    constexpr int KC = C / 8;
+    constexpr int N3 = 3 * C;
+    constexpr int DCOLS = r_dcols(C);
+    constexpr int CPW = RGeom<C>::CPW;  // chunks per epilogue warp
+    constexpr int EPW = RGeom<C>::EPW;  // epilogue warps per lane quarter
+    constexpr uint32_t WBYTES = 9u * C * C * 2u;
+    constexpr uint32_t PLANE = 130u * 16u;
+    constexpr uint32_t SLOT = r_slot_bytes(C);
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* w_tile = smem;  // [dx][kc][dy][cout][8]: B of the (dx, K-step) MMA is one block
+    unsigned char* ring = smem + WBYTES;
+    RCtl* ctl = reinterpret_cast<RCtl*>(ring + size_t(RING) * SLOT);
+    float* scratch = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(ctl) + kRCtlBytes);
+    volatile int* abort_flag = &ctl->abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int NB = n / 128;
+    const size_t nn = size_t(n) * n;
+    const long long total = (long long)batch * NB * n;
+    const long long u0 = total * blockIdx.x / gridDim.x;
+    const long long u1 = total * (blockIdx.x + 1) / gridDim.x;
+
+    if (tid == 0) {
+        for (int i = 0; i < RING; ++i) {
+            tc::mbar_init(&ctl->full[i], 1);
+            tc::mbar_init(&ctl->empty[i], 1);
+        }
+        for (int i = 0; i < DS; ++i) {
+            tc::mbar_init(&ctl->dfull[i], 1);
+            tc::mbar_init(&ctl->dempty[i], 4 * EPW);
+        }
+        for (int i = 0; i < 8; ++i) tc::mbar_init(&ctl->qbar[i / 4][i % 4], EPW);
+        tc::mbar_init(&ctl->fin, 1);
+        tc::mbar_init(&ctl->never, 1);
+        ctl->abort = 0;
+        tc::fence_mbar_init();
+    }
+    static_assert(sizeof(RCtl) <= kRCtlBytes, "control block");
+    __syncthreads();
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer: starts at once; the other warps stage the weights meanwhile
+            long long j = 0;
+            RingPos rp(RING);
+            RowCursor cur(u0, n, NB);
+            bool ok = true;
+            for (long long u = u0; u < u1 && ok; ++u, cur.next()) {
+                const int y = cur.y;
+                const long long f = cur.f;
+                const bool start = (u == u0) || (y == 0);
+                const int x0 = cur.cb * 128;
+                const int xl = x0 == 0 ? n - 1 : x0 - 1;
+                const int xr = x0 + 128 == n ? 0 : x0 + 128;
+                for (int k = start ? 0 : 2; k < 3 && ok; ++k) {
+                    int yin = y - 1 + k;
+                    yin = yin < 0 ? yin + n : (yin >= n ? yin - n : yin);
+                    const int slot = rp.idx;
+                    if (j >= RING && !p_wait(&ctl->empty[slot], rp.phase ^ 1u, abort_flag, status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_arrive_expect_tx(&ctl->full[slot], SLOT);
+                    for (int kc = 0; kc < KC; ++kc) {
+                        const __nv_bfloat16* src = in + ((size_t(f) * KC + kc) * nn + size_t(yin) * n) * 8;
+                        unsigned char* dst = ring + size_t(slot) * SLOT + size_t(kc) * PLANE;
+                        tc::bulk_g2s(dst + 16, src + size_t(x0) * 8, 128u * 16u, &ctl->full[slot]);
+                        tc::bulk_g2s(dst, src + size_t(xl) * 8, 16u, &ctl->full[slot]);
+                        tc::bulk_g2s(dst + 129 * 16, src + size_t(xr) * 8, 16u, &ctl->full[slot]);
+                    }
+                    ++j;
+                    rp.next();
+                }
+            }
+            // drain: every issued copy lands before the CTA may exit
+            for (long long x = j > RING ? j - RING : 0; x < j; ++x)
+                tc::mbar_wait_bounded(&ctl->full[x % RING], uint32_t((x / RING) & 1), kTcSpin);
+        }
+    } else {
+        // ---- weights (permuted to [dx][kc][dy][cout][8]), bias, last-layer taps
+        const uint4* wsrc = reinterpret_cast<const uint4*>(wpk);
+        uint4* wdst = reinterpret_cast<uint4*>(w_tile);
+        for (int e = tid - 32; e < 9 * KC * C; e += blockDim.x - 32) {
+            const int co = e % C, kc = (e / C) % KC, tap = e / (C * KC);
+            wdst[((tap % 3) * KC + kc) * N3 + (tap / 3) * C + co] = wsrc[e];
+        }
+        tc::fence_proxy_async_smem();
+        if (tid - 32 < C) ctl->bias[tid - 32] = (mode != kDgrad) ? bias[tid - 32] : 0.f;
+        if (mode == kFwdLast)
+            for (int e = tid - 32; e < 10 * C; e += blockDim.x - 32) {
+                const int tap = e % 10, c = e / 10;
+                ctl->wl[e] = tap < 9 ? bf16r(wlast[c * 9 + tap]) : 0.f;
+            }
+        if (warp == 1) tc::tmem_alloc(&ctl->tmem, 512u);
+        tc::fence_before_sync();
+        tc::bar_sync(1, blockDim.x - 32);
+        tc::fence_after_sync();
+        const uint32_t tmem = ctl->tmem;
+
+        if (warp == 1) {
+            if (lane == 0) {
+                // ---- MMA issuer
+                bool ok = true;
+                // test hook: a wait that cannot succeed, so the bounded-wait path runs
+                if (stall > 0) ok = p_wait(&ctl->never, 0, abort_flag, status, stall);
+                const uint32_t idesc = tc::idesc_bf16_f32(128, N3);
+                const uint64_t a_hi = tc::smem_desc(0, PLANE, 128);
+                const uint64_t b_hi = tc::smem_desc(0, N3 * 16, 128);
+                // start-address fields count 16-byte units; one pixel (8 channels) is one unit
+                const uint32_t ring_u = tc::smem_u32(ring) >> 4, w_u = tc::smem_u32(w_tile) >> 4;
+                long long j = 0;
+                RingPos rp(RING), dp(DS);
+                int y = int(u0 % n);
+                for (long long u = u0; u < u1 && ok; ++u, y = (y + 1 == n ? 0 : y + 1)) {
+                    const bool start = (u == u0) || (y == 0);
+                    for (int k = start ? 0 : 2; k < 3; ++k, ++j, rp.next(), dp.next()) {
+                        const int slot = rp.idx;
+                        const int ds = dp.idx;
+                        if (j >= DS && !(ok = p_wait(&ctl->dempty[ds], dp.phase ^ 1u, abort_flag, status))) break;
+                        if (!(ok = p_wait(&ctl->full[slot], rp.phase, abort_flag, status))) break;
+                        tc::fence_after_sync();
+                        const uint32_t in_u = ring_u + uint32_t(slot) * (SLOT >> 4);
+                        const uint32_t d_addr = tmem + uint32_t(ds * DCOLS);
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+#pragma unroll
+                            for (int ks = 0; ks < C / 16; ++ks) {
+                                const uint64_t ad = a_hi | uint64_t(in_u + uint32_t(dx) + uint32_t(2 * ks) * (PLANE >> 4));
+                                const uint64_t bd = b_hi | uint64_t(w_u + uint32_t((dx * KC + 2 * ks) * N3));
+                                tc::mma_bf16(d_addr, ad, bd, idesc, (dx | ks) != 0);
+                            }
+                        }
+                        tc::mma_commit(&ctl->empty[slot]);
+                        tc::mma_commit(&ctl->dfull[ds]);
+                    }
+                }
+                // every MMA issued so far completes before TMEM is freed
+                tc::mma_commit(&ctl->fin);
+                tc::mbar_wait_bounded(&ctl->fin, 0, kTcSpin);
+            }
+        } else if ((warp - 2) / 4 < EPW) {
+            // ---- epilogue
+            const int q = warp & 3;         // TMEM lane quarter: pixels 32 q .. 32 q + 31
+            const int g = (warp - 2) >> 2;  // chunk group: chunks g CPW .. g CPW + CPW - 1
+            const f32x2* bias2 = reinterpret_cast<const f32x2*>(ctl->bias);
+            f32x2 P[CPW][4], Pn[CPW][4];  // partial sums of output rows y and y + 1, channel pairs
+#pragma unroll
+            for (int c = 0; c < CPW; ++c)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) P[c][e] = Pn[c][e] = f2(0.f, 0.f);
+            RingPos dp(DS);
+            RowCursor cur(u0, n, NB);
+            int rows_done = 0;
+            bool ok = true;
+            for (long long u = u0; u < u1 && ok; ++u, cur.next()) {
+                const int y = cur.y;
+                const long long f = cur.f;
+                const bool start = (u == u0) || (y == 0);
+                const size_t pix = size_t(y) * n + size_t(cur.cb * 128 + q * 32 + lane);
+                for (int k = start ? 0 : 2; k < 3; ++k, dp.next()) {
+                    const int ds = dp.idx;
+                    if (!(ok = p_wait(&ctl->dfull[ds], dp.phase, abort_flag, status))) break;
+                    tc::fence_after_sync();
+                    const uint32_t trow = tmem + (uint32_t(q * 32) << 16) + uint32_t(ds * DCOLS);
+                    f32x2 pt2[5];  // kFwdLast: the nine-tap projection, tap pairs
+#pragma unroll
+                    for (int m = 0; m < 5; ++m) pt2[m] = f2(0.f, 0.f);
+#pragma unroll
+                    for (int c = 0; c < CPW; ++c) {
+                        const int kc = g * CPW + c;
+                        uint32_t v[3][8];
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy) tc::tmem_ld8(trow + uint32_t(dy * C + kc * 8), v[dy]);
+                        tc::tmem_wait_ld();
+                        if (c == CPW - 1) {
+                            // the slot is in registers: the MMA issuer may refill it
+                            tc::fence_before_sync();
+                            __syncwarp();
+                            if (lane == 0) tc::mbar_arrive(&ctl->dempty[ds]);
+                        }
+                        f32x2 d[3][4];
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                d[dy][e] = f2(__uint_as_float(v[dy][2 * e]), __uint_as_float(v[dy][2 * e + 1]));
+                        if (k == 2) {
+                            // output row y is complete: P + D(y+1)[dy=2]
+                            const size_t off = ((size_t(f) * KC + kc) * nn + pix) * 8;
+                            f32x2 acc[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) acc[e] = f2_add(P[c][e], d[2][e]);
+                            uint32_t packed[4];
+                            if (mode != kDgrad) {
+                                f32x2 z[4];
+                                float a8[8];
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    z[e] = f2_add(acc[e], bias2[kc * 4 + e]);
+                                    float a0, a1;
+                                    f2split(act2<ACT>(z[e]), a0, a1);
+                                    const __nv_bfloat162 hh = __floats2bfloat162_rn(a0, a1);
+                                    packed[e] = *reinterpret_cast<const uint32_t*>(&hh);
+                                    a8[2 * e] = __low2float(hh);
+                                    a8[2 * e + 1] = __high2float(hh);
+                                }
+                                if (zio) {
+                                    f32x2* z2 = reinterpret_cast<f32x2*>(zio + off);
+#pragma unroll
+                                    for (int e = 0; e < 4; ++e) z2[e] = z[e];
+                                }
+                                if (mode == kFwdLast) {
+                                    // channels in order, taps in pairs: each tap's sum is the
+                                    // same fma chain as one tap at a time
+#pragma unroll
+                                    for (int i = 0; i < 8; ++i) {
+                                        const f32x2* w2 = reinterpret_cast<const f32x2*>(ctl->wl + (kc * 8 + i) * 10);
+                                        const f32x2 ai = f2(a8[i], a8[i]);
+#pragma unroll
+                                        for (int m = 0; m < 5; ++m) pt2[m] = f2_fma(w2[m], ai, pt2[m]);
+                                    }
+                                }
+                            } else {
+                                const float4 za = reinterpret_cast<const float4*>(zio + off)[0];
+                                const float4 zb = reinterpret_cast<const float4*>(zio + off)[1];
+                                const float zz[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    float a0, a1;
+                                    f2split(acc[e], a0, a1);
+                                    const __nv_bfloat162 hh = __floats2bfloat162_rn(a0 * act_grad_c<ACT>(zz[2 * e]),
+                                                                                    a1 * act_grad_c<ACT>(zz[2 * e + 1]));
+                                    packed[e] = *reinterpret_cast<const uint32_t*>(&hh);
+                                }
+                            }
+                            // kFwdLast stores the activations only for training (zio)
+                            if (mode != kFwdLast || zio)
+                                *reinterpret_cast<uint4*>(out + off) =
+                                    make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                        }
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            P[c][e] = f2_add(Pn[c][e], d[1][e]);
+                            Pn[c][e] = d[0][e];
+                        }
+                    }
+                    if (k == 2 && mode == kFwdLast) {
+                        // the quarter's EPW partial projections, summed in warp order
+                        const int par = rows_done & 1;
+                        float* sc = scratch + size_t(par * 4 + q) * (4 * 9 * 32);
+#pragma unroll
+#pragma unroll
+                        for (int m = 0; m < 5; ++m) {
+                            float t0, t1;
+                            f2split(pt2[m], t0, t1);
+                            sc[(g * 9 + 2 * m) * 32 + lane] = t0;
+                            if (m < 4) sc[(g * 9 + 2 * m + 1) * 32 + lane] = t1;
+                        }
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&ctl->qbar[par][q]);
+                        if (!(ok = p_wait(&ctl->qbar[par][q], uint32_t((rows_done >> 1) & 1), abort_flag,
+                                          status)))
+                            break;
+                        for (int tp = g; tp < 9; tp += EPW) {
+                            float s_ = sc[tp * 32 + lane];
+#pragma unroll
+                            for (int w = 1; w < EPW; ++w) s_ = __fadd_rn(s_, sc[(w * 9 + tp) * 32 + lane]);
+                            maps[(size_t(f) * 9 + tp) * nn + pix] = s_;
+                        }
+                    }
+                    if (k == 2) ++rows_done;
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(ctl->tmem, 512u);
+}
+
+struct RShape {
+    int RING = 0, DS = 0;
     size_t smem = 0;
 };
 
-// Tile shape: mg = M-tiles per row segment (0: automatic), ring_mode = depth
-// of the input-row ring (0: one unit of prefetch, 2 TY + 2 rows; 1: no
-// prefetch, TY + 2; 2: as deep as shared memory allows, up to kPMaxRing).
-static PShape p_shape_with(int n, int C, int mg, int ring_mode, int areuse = 0) {
-    PShape s;
-    s.areuse = areuse;
-    if (n < 128 || n % 128) return s;
-    // C = 64 keeps one M-tile per row so that a ring slot stays small
-    s.MG = mg ? mg : ((C >= 64 || n < 256) ? 1 : 2);
-    if (s.MG < 1 || s.MG > 2 || (s.MG == 2 && (C >= 64 || n < 256))) return PShape{};
-    s.CW = 128 * s.MG;
-    s.TY = kPStageCols / (s.MG * C);
-    if (s.TY < 1 || n % s.TY) return PShape{};
-    s.slot_bytes = uint32_t(C / 8) * uint32_t(s.CW + 2) * 16u;
-    const size_t wbytes = size_t(9) * C * C * 2;
-    const size_t ctrl = 4096;  // PCtl
-    const size_t avail = size_t(227) * 1024 - wbytes - ctrl;
-    int ring = int(avail / s.slot_bytes);
-    if (ring > kPMaxRing) ring = kPMaxRing;
-    if (ring_mode == 0 && ring > 2 * s.TY + 2) ring = 2 * s.TY + 2;  // one unit of prefetch
-    if (ring_mode == 1 && ring > s.TY + 2) ring = s.TY + 2;
-    if (ring < s.TY + 2) return PShape{};
+// ring_mode: 0 as deep as shared memory allows (up to kRMaxRing slots),
+// 1 at most 12, 2 at most 6; ds: TMEM slots (0: as many as fit, up to kRMaxD).
+static RShape r_shape_with(int n, int C, int ring_mode, int ds, bool last) {
+    RShape s;
+    if (n < 128 || n % 128 || !(C == 16 || C == 32 || C == 64)) return s;
+    const int dmax = std::min(kRMaxD, 512 / r_dcols(C));
+    s.DS = ds ? ds : dmax;
+    if (s.DS < 2 || s.DS > dmax) return RShape{};
+    const size_t fixed = size_t(9) * C * C * 2 + kRCtlBytes + (last ? kRScratchBytes : 0);
+    int ring = int((size_t(227) * 1024 - fixed) / r_slot_bytes(C));
+    ring = std::min(ring, kRMaxRing);
+    if (ring_mode == 1) ring = std::min(ring, 12);
+    if (ring_mode == 2) ring = std::min(ring, 6);
+    if (ring < 2) return RShape{};
     s.RING = ring;
-    s.smem = wbytes + size_t(ring) * s.slot_bytes + ctrl;
-    // more than half an SM's shared memory: at most one such CTA per SM, so
-    // the CTAs' TMEM stages (all 512 columns) never contend
+    s.smem = fixed + size_t(ring) * r_slot_bytes(C);
+    // one CTA per SM: it owns all 512 TMEM columns
     if (s.smem < size_t(116) * 1024) s.smem = size_t(116) * 1024;
     return s;
 }
 
-// Tile shapes a tuner may pick, per (channels, log2 n): index into
-// conv_variants() (-1: automatic).
+// Shape of the row-streaming kernel per (channels, log2 n): index into
+// conv_variants() (-1: automatic, the first).  A shape is a ring depth mode
+// and a TMEM slot count; every shape gives the same bits.
 namespace {
 int g_conv_pick[3][11] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
                           {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
                           {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1}};
 int cidx(int C) { return C == 16 ? 0 : (C == 32 ? 1 : 2); }
 int lg2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
-struct ConvVariant { int mg, ring_mode, areuse; };
-constexpr ConvVariant kConvVariants[] = {{0, 0, 0}, {1, 0, 0}, {2, 0, 0}, {1, 1, 0}, {2, 1, 0}, {1, 2, 0}, {2, 2, 0},
-                                         {0, 0, 1}, {1, 0, 1}, {2, 0, 1}, {1, 2, 1}, {2, 2, 1}};
+struct ConvVariant { int ring_mode, ds; };
+constexpr ConvVariant kConvVariants[] = {{0, 0}, {1, 0}, {2, 0}, {0, 2}, {0, 3}, {1, 2}};
 constexpr int kConvVariantCount = int(sizeof(kConvVariants) / sizeof(kConvVariants[0]));
 }  // namespace
 
 // The valid, distinct shapes for (n, C), in kConvVariants order.
 static int conv_variants(int n, int C, int* out) {
     int cnt = 0;
-    PShape seen[kConvVariantCount];
+    RShape seen[kConvVariantCount];
     for (int i = 0; i < kConvVariantCount; ++i) {
-        const PShape s = p_shape_with(n, C, kConvVariants[i].mg, kConvVariants[i].ring_mode, kConvVariants[i].areuse);
-        if (!s.RING) continue;
+        const RShape r = r_shape_with(n, C, kConvVariants[i].ring_mode, kConvVariants[i].ds, false);
+        if (!r.RING) continue;
         bool dup = false;
-        for (int k = 0; k < cnt; ++k)
-            dup = dup || (seen[k].MG == s.MG && seen[k].RING == s.RING && seen[k].areuse == s.areuse);
+        for (int k = 0; k < cnt; ++k) dup = dup || (seen[k].RING == r.RING && seen[k].DS == r.DS);
         if (dup) continue;
-        seen[cnt] = s;
+        seen[cnt] = r;
         out[cnt++] = i;
     }
     return cnt;
 }
 
-static PShape p_shape(int n, int C) {
+// The shape a hidden layer of (n, C) runs with (RING 0: the one-shot kernel);
+// `last` leaves room for the fused last layer's reduction scratch.
+static RShape conv_plan(int n, int C, bool last) {
     const int pick = (C == 16 || C == 32 || C == 64) && n >= 1 && n <= 1024 ? g_conv_pick[cidx(C)][lg2(n)] : -1;
-    if (pick >= 0) {
-        int idx[kConvVariantCount];
-        const int cnt = conv_variants(n, C, idx);
-        if (pick < cnt) {
-            const ConvVariant v = kConvVariants[idx[pick]];
-            return p_shape_with(n, C, v.mg, v.ring_mode, v.areuse);
-        }
-    }
-    return p_shape_with(n, C, 0, 0);
+    int idx[kConvVariantCount];
+    const int cnt = conv_variants(n, C, idx);
+    if (cnt == 0) return RShape{};
+    const ConvVariant v = kConvVariants[idx[pick >= 0 && pick < cnt ? pick : 0]];
+    return r_shape_with(n, C, v.ring_mode, v.ds, last);
 }
 
 int conv_variant_count(int n, int C) {
@@ -381,16 +738,13 @@ int conv_variant_count(int n, int C) {
     return conv_variants(n, C, idx);
 }
 
-int conv_variant_describe(int n, int C, int index, int* mg, int* ty, int* ring, int* areuse) {
+int conv_variant_describe(int n, int C, int index, int* ring, int* slots) {
     int idx[kConvVariantCount];
     const int cnt = conv_variant_count(n, C) ? conv_variants(n, C, idx) : 0;
     if (index < 0 || index >= cnt) return AC_ERR_ARG;
-    const ConvVariant v = kConvVariants[idx[index]];
-    const PShape s = p_shape_with(n, C, v.mg, v.ring_mode, v.areuse);
-    *mg = s.MG;
-    *ty = s.TY;
-    *ring = s.RING;
-    *areuse = s.areuse;
+    const RShape r = r_shape_with(n, C, kConvVariants[idx[index]].ring_mode, kConvVariants[idx[index]].ds, false);
+    *ring = r.RING;
+    *slots = r.DS;
     return AC_OK;
 }
 
@@ -407,342 +761,6 @@ int conv_get_variant(int n, int C) {
     return g_conv_pick[cidx(C)][lg2(n)];
 }
 
-struct PCtl {
-    uint64_t never;  // test hook: nothing ever arrives here
-    uint64_t full[kPMaxRing];
-    uint64_t empty[kPMaxRing];
-    uint64_t accf[kPStages];
-    uint64_t acce[kPStages];
-    uint64_t wbar;  // the weight copy
-    uint64_t fin;   // completion of every MMA the CTA issued
-    uint32_t tmem;
-    int abort;
-    alignas(16) float bias[64];
-    alignas(16) float wl[64 * 9];  // kFwdLast: bf16-rounded last-layer weights [kc][tap][8]
-};
-
-__device__ __forceinline__ bool p_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
-                                       long long limit = kTcSpin) {
-    for (long long i = 0; i < limit; ++i) {
-        if (tc::mbar_try_wait(bar, parity)) return true;
-        if (*abort_flag) return false;
-        __nanosleep(32);
-    }
-    *abort_flag = 1;
-    atomicExch(status, 3);
-    return false;
-}
-
-template <int C, int MG, int ACT>
-__global__ void __launch_bounds__(kPThreads, 1)
-conv_hidden_tc_persistent(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ out,
-                          const __nv_bfloat16* __restrict__ wpk, const float* __restrict__ bias, int n,
-                          int batch, int RING, uint32_t slot_bytes, int mode, float* __restrict__ zio,
-                          int* __restrict__ status, int stall, const float* __restrict__ wlast,
-                          float* __restrict__ maps, int areuse) {
-    constexpr int KC = C / 8;
-    constexpr int TY = kPStageCols / (MG * C);
-    constexpr int NACC = TY * MG;
-    constexpr int CW = 128 * MG;
-    constexpr uint32_t WBYTES = 9u * C * C * 2u;
-    extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char* w_tile = smem;
-    unsigned char* ring = smem + WBYTES;
-    PCtl* ctl = reinterpret_cast<PCtl*>(ring + size_t(RING) * slot_bytes);
-    volatile int* abort_flag = &ctl->abort;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int NB = n / CW;
-    const int NYB = n / TY;
-    const uint32_t plane_b = uint32_t(CW + 2) * 16u;
-    const size_t nn = size_t(n) * n;
-    const long long total = (long long)batch * NB * NYB;
-    const long long u0 = total * blockIdx.x / gridDim.x;
-    const long long u1 = total * (blockIdx.x + 1) / gridDim.x;
-
-    if (tid == 0) {
-        for (int i = 0; i < RING; ++i) {
-            tc::mbar_init(&ctl->full[i], 1);
-            tc::mbar_init(&ctl->empty[i], 1);
-        }
-        for (int i = 0; i < kPStages; ++i) {
-            tc::mbar_init(&ctl->accf[i], 1);
-            tc::mbar_init(&ctl->acce[i], kPEpiWarps);
-        }
-        tc::mbar_init(&ctl->wbar, 1);
-        tc::mbar_init(&ctl->fin, 1);
-        tc::mbar_init(&ctl->never, 1);
-        ctl->abort = 0;
-        tc::fence_mbar_init();
-    }
-    static_assert(sizeof(PCtl) <= 4096, "control block");
-    if (tid < C) ctl->bias[tid] = (mode != kDgrad) ? bias[tid] : 0.f;
-    if (mode == kFwdLast)
-        for (int e = tid; e < 9 * C; e += blockDim.x) {
-            // wl[kc][tap][i] = bf16(W_last[0][kc 8 + i][tap])
-            const int i = e % 8, tap = (e / 8) % 9, kc = e / 72;
-            ctl->wl[e] = bf16r(wlast[(kc * 8 + i) * 9 + tap]);
-        }
-    __syncthreads();
-    if (warp == 1) tc::tmem_alloc(&ctl->tmem, uint32_t(kPStages * kPStageCols));
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    const uint32_t tmem = ctl->tmem;
-
-    if (warp == 0 && lane == 0) {
-        // ---- producer
-        tc::mbar_arrive_expect_tx(&ctl->wbar, WBYTES);
-        tc::bulk_g2s(w_tile, wpk, WBYTES, &ctl->wbar);
-        long long s = 0;
-        bool ok = true;
-        for (long long u = u0; u < u1 && ok; ++u) {
-            const int yb = int(u % NYB);
-            const long long t = u / NYB;
-            const int cb = int(t % NB);
-            const long long f = t / NB;
-            const int y0 = yb * TY;
-            const bool start = (u == u0) || (yb == 0);
-            // input rows y0 - 1 .. y0 + TY (segment start) or y0 + 1 .. y0 + TY
-            for (int r = start ? -1 : 1; r <= TY && ok; ++r) {
-                int yin = y0 + r;
-                yin = yin < 0 ? yin + n : (yin >= n ? yin - n : yin);
-                const int slot = int(s % RING);
-                const long long k = s / RING;
-                if (k >= 1 && !p_wait(&ctl->empty[slot], uint32_t((k - 1) & 1), abort_flag, status)) {
-                    ok = false;
-                    break;
-                }
-                tc::mbar_arrive_expect_tx(&ctl->full[slot], uint32_t(KC) * plane_b);
-                const int x0 = cb * CW;
-                const int xl = x0 == 0 ? n - 1 : x0 - 1;
-                const int xr = x0 + CW == n ? 0 : x0 + CW;
-                for (int kc = 0; kc < KC; ++kc) {
-                    const __nv_bfloat16* src = in + ((size_t(f) * KC + kc) * nn + size_t(yin) * n) * 8;
-                    unsigned char* dst = ring + size_t(slot) * slot_bytes + size_t(kc) * plane_b;
-                    tc::bulk_g2s(dst + 16, src + size_t(x0) * 8, uint32_t(CW) * 16u, &ctl->full[slot]);
-                    tc::bulk_g2s(dst, src + size_t(xl) * 8, 16u, &ctl->full[slot]);
-                    tc::bulk_g2s(dst + size_t(CW + 1) * 16, src + size_t(xr) * 8, 16u, &ctl->full[slot]);
-                }
-                ++s;
-            }
-        }
-        // drain: every issued copy lands before the CTA may exit
-        const long long first = s > RING ? s - RING : 0;
-        for (long long x = first; x < s; ++x)
-            tc::mbar_wait_bounded(&ctl->full[x % RING], uint32_t((x / RING) & 1), kTcSpin);
-        tc::mbar_wait_bounded(&ctl->wbar, 0, kTcSpin);
-    } else if (warp == 1 && lane == 0) {
-        // ---- MMA issuer
-        bool ok = p_wait(&ctl->wbar, 0, abort_flag, status);
-        // test hook: a wait that cannot succeed, so the bounded-wait path runs
-        if (ok && stall > 0) ok = p_wait(&ctl->never, 0, abort_flag, status, stall);
-        const uint32_t idesc = tc::idesc_bf16_f32(128, C);
-        const uint64_t a_hi = tc::smem_desc(0, plane_b, 128);
-        const uint64_t b_hi = tc::smem_desc(0, C * 16, 128);
-        // start-address fields count 16-byte units; one pixel (8 channels) is one unit
-        const uint32_t ring_u = tc::smem_u32(ring) >> 4, w_u = tc::smem_u32(w_tile) >> 4;
-        const uint32_t slot_u = slot_bytes >> 4, plane_u = plane_b >> 4;
-        int a = 0, snext = 0;  // load index of the unit's first input row (a CTA's loads are few)
-        int i = 0;
-        for (long long u = u0; u < u1 && ok; ++u, ++i) {
-            const int yb = int(u % NYB);
-            const bool start = (u == u0) || (yb == 0);
-            if (start) {
-                a = snext;
-                snext += TY + 2;
-            } else {
-                a += TY;
-                snext += TY;
-            }
-            const int stage = i & 1;
-            const int kk = i >> 1;
-            if (kk >= 1 && !p_wait(&ctl->acce[stage], uint32_t((kk - 1) & 1), abort_flag, status)) break;
-            const int aslot = a % RING;
-            for (int d = 0; d < TY + 2 && ok; ++d)
-                ok = p_wait(&ctl->full[(a + d) % RING], uint32_t(((a + d) / RING) & 1), abort_flag, status);
-            if (!ok) break;
-            tc::fence_after_sync();
-            const uint32_t dbase = tmem + uint32_t(stage * kPStageCols);
-            if (areuse) {
-                // input row rho of the unit serves output rows rho - dy (dy =
-                // 0, 1, 2): its A operand (shift dx, K-step ks, M-tile m) is
-                // read into the collector once and used for up to three MMAs.
-                // Each accumulator still receives its MMAs in (tap, K-step)
-                // order, so the sums are those of the loop below, bit for bit.
-#pragma unroll 1
-                for (int rho = 0; rho < TY + 2; ++rho) {
-                    int sl = aslot + rho;
-                    sl = sl >= RING ? sl - RING : sl;
-                    const uint32_t in_u = ring_u + uint32_t(sl) * slot_u;
-                    const int dy_lo = rho - (TY - 1) > 0 ? rho - (TY - 1) : 0;
-                    const int dy_hi = rho < 2 ? rho : 2;
-#pragma unroll
-                    for (int dx = 0; dx < 3; ++dx) {
-#pragma unroll
-                        for (int ks = 0; ks < C / 16; ++ks) {
-#pragma unroll
-                            for (int m = 0; m < MG; ++m) {
-                                const uint64_t ad = a_hi | uint64_t(in_u + uint32_t(dx) + uint32_t(2 * ks) * plane_u +
-                                                                    uint32_t(m * 128));
-#pragma unroll
-                                for (int dy = 0; dy < 3; ++dy) {
-                                    if (dy < dy_lo || dy > dy_hi) continue;
-                                    const int tap = dy * 3 + dx;
-                                    const int acc = (rho - dy) * MG + m;
-                                    const uint64_t bd = b_hi | uint64_t(w_u + uint32_t((tap * KC + 2 * ks) * C));
-                                    const uint32_t d_addr = dbase + uint32_t(acc * C);
-                                    const uint32_t accum = (tap | ks) != 0;
-                                    if (dy_lo == dy_hi) tc::mma_bf16(d_addr, ad, bd, idesc, accum);
-                                    else if (dy == dy_lo) tc::mma_bf16_coll<1>(d_addr, ad, bd, idesc, accum);
-                                    else if (dy == dy_hi) tc::mma_bf16_coll<3>(d_addr, ad, bd, idesc, accum);
-                                    else tc::mma_bf16_coll<2>(d_addr, ad, bd, idesc, accum);
-                                }
-                            }
-                        }
-                    }
-                }
-            } else
-#pragma unroll 1
-            for (int tap = 0; tap < 9; ++tap) {
-                const int dy = tap / 3, dx = tap % 3;
-                // start of each output row's input row for this tap
-                uint32_t row_u[TY];
-#pragma unroll
-                for (int r = 0; r < TY; ++r) {
-                    int sl = aslot + r + dy;
-                    sl = sl >= RING ? sl - RING : sl;
-                    row_u[r] = ring_u + uint32_t(sl) * slot_u + uint32_t(dx);
-                }
-#pragma unroll
-                for (int ks = 0; ks < C / 16; ++ks) {
-                    const uint64_t bd = b_hi | uint64_t(w_u + uint32_t((tap * KC + 2 * ks) * C));
-#pragma unroll
-                    for (int acc = 0; acc < NACC; ++acc) {
-                        const int r = acc / MG, m = acc % MG;
-                        const uint64_t ad =
-                            a_hi | uint64_t(row_u[r] + uint32_t(2 * ks) * plane_u + uint32_t(m * 128));
-                        tc::mma_bf16(dbase + uint32_t(acc * C), ad, bd, idesc, (tap | ks) != 0);
-                    }
-                }
-            }
-            tc::mma_commit(&ctl->accf[stage]);
-            const bool cont = (u + 1 < u1) && (yb != NYB - 1);
-            const int nrel = cont ? TY : TY + 2;
-            for (int d = 0; d < nrel; ++d) tc::mma_commit(&ctl->empty[(a + d) % RING]);
-        }
-        // every MMA issued so far completes before TMEM is freed
-        tc::mma_commit(&ctl->fin);
-        tc::mbar_wait_bounded(&ctl->fin, 0, kTcSpin);
-    } else if (warp >= 2) {
-        // ---- epilogue: kPEpiWarps warps in kPEpiWarps / 4 groups; a warp
-        // reads TMEM lanes 32 (warp % 4) .. + 31 (one pixel per lane of an
-        // M-tile) and owns its group's accumulators acc = grp, grp + NG, ...:
-        // all C channels of its pixel come in W-column TMEM loads (one wait
-        // per W channels), then bias + activation (or the act' product),
-        // bf16, 16-byte stores per 8-channel chunk.  kFwdLast also projects
-        // the pixel's activations onto the last layer's nine taps.
-        constexpr int NG = kPEpiWarps / 4;
-        constexpr int W = 16;
-        const int grp = (warp - 2) >> 2;
-        const int q = warp & 3;
-        const float4* bias4 = reinterpret_cast<const float4*>(ctl->bias);
-        int i = 0;
-        for (long long u = u0; u < u1; ++u, ++i) {
-            const int yb = int(u % NYB);
-            const long long t = u / NYB;
-            const int cb = int(t % NB);
-            const long long f = t / NB;
-            const int stage = i & 1;
-            if (!p_wait(&ctl->accf[stage], uint32_t((i >> 1) & 1), abort_flag, status)) break;
-            tc::fence_after_sync();
-            const size_t pix0 = size_t(yb * TY) * n + size_t(cb * CW + q * 32 + lane);
-            const uint32_t trow = tmem + (uint32_t(q * 32) << 16) + uint32_t(stage * kPStageCols);
-            for (int acc = grp; acc < NACC; acc += NG) {
-                const int r = acc / MG, m = acc % MG;
-                const size_t pix = pix0 + size_t(r) * n + size_t(m) * 128;
-                float pt[9];
-#pragma unroll
-                for (int tp = 0; tp < 9; ++tp) pt[tp] = 0.f;
-#pragma unroll 1
-                for (int kc0 = 0; kc0 < KC; kc0 += W / 8) {
-                    uint32_t v[W];
-                    tc::tmem_ldw<W>(trow + uint32_t(acc * C + kc0 * 8), v);
-                    tc::tmem_wait_ld();
-#pragma unroll
-                    for (int h = 0; h < W / 8; ++h) {
-                        const int kc = kc0 + h;
-                        const size_t off = ((size_t(f) * KC + kc) * nn + pix) * 8;
-                        uint32_t packed[4];
-                        if (mode != kDgrad) {
-                            const float4 b0 = bias4[kc * 2], b1 = bias4[kc * 2 + 1];
-                            __align__(16) float z8[8] = {
-                                __uint_as_float(v[h * 8 + 0]) + b0.x, __uint_as_float(v[h * 8 + 1]) + b0.y,
-                                __uint_as_float(v[h * 8 + 2]) + b0.z, __uint_as_float(v[h * 8 + 3]) + b0.w,
-                                __uint_as_float(v[h * 8 + 4]) + b1.x, __uint_as_float(v[h * 8 + 5]) + b1.y,
-                                __uint_as_float(v[h * 8 + 6]) + b1.z, __uint_as_float(v[h * 8 + 7]) + b1.w};
-                            float a8[8];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const __nv_bfloat162 hh = __floats2bfloat162_rn(act_c<ACT>(z8[2 * e]),
-                                                                                act_c<ACT>(z8[2 * e + 1]));
-                                packed[e] = *reinterpret_cast<const uint32_t*>(&hh);
-                                a8[2 * e] = __low2float(hh);
-                                a8[2 * e + 1] = __high2float(hh);
-                            }
-                            if (zio) {
-                                reinterpret_cast<float4*>(zio + off)[0] = *reinterpret_cast<const float4*>(z8);
-                                reinterpret_cast<float4*>(zio + off)[1] = *reinterpret_cast<const float4*>(z8 + 4);
-                            }
-                            if (mode == kFwdLast) {
-                                const float4* wl4 = reinterpret_cast<const float4*>(ctl->wl + kc * 72);
-#pragma unroll
-                                for (int tp = 0; tp < 9; ++tp) {
-                                    const float4 w0 = wl4[tp * 2], w1 = wl4[tp * 2 + 1];
-                                    float s_ = pt[tp];
-                                    s_ = fmaf(w0.x, a8[0], s_);
-                                    s_ = fmaf(w0.y, a8[1], s_);
-                                    s_ = fmaf(w0.z, a8[2], s_);
-                                    s_ = fmaf(w0.w, a8[3], s_);
-                                    s_ = fmaf(w1.x, a8[4], s_);
-                                    s_ = fmaf(w1.y, a8[5], s_);
-                                    s_ = fmaf(w1.z, a8[6], s_);
-                                    s_ = fmaf(w1.w, a8[7], s_);
-                                    pt[tp] = s_;
-                                }
-                            }
-                        } else {
-                            const float4 za = reinterpret_cast<const float4*>(zio + off)[0];
-                            const float4 zb = reinterpret_cast<const float4*>(zio + off)[1];
-                            const float zz[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const __nv_bfloat162 hh = __floats2bfloat162_rn(
-                                    __uint_as_float(v[h * 8 + 2 * e]) * act_grad_c<ACT>(zz[2 * e]),
-                                    __uint_as_float(v[h * 8 + 2 * e + 1]) * act_grad_c<ACT>(zz[2 * e + 1]));
-                                packed[e] = *reinterpret_cast<const uint32_t*>(&hh);
-                            }
-                        }
-                        // kFwdLast stores the activations only for training (zio)
-                        if (mode != kFwdLast || zio)
-                            *reinterpret_cast<uint4*>(out + off) =
-                                make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                    }
-                }
-                if (mode == kFwdLast) {
-#pragma unroll
-                    for (int tp = 0; tp < 9; ++tp) maps[(size_t(f) * 9 + tp) * nn + pix] = pt[tp];
-                }
-            }
-            tc::fence_before_sync();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&ctl->acce[stage]);
-        }
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    if (warp == 1) tc::tmem_dealloc(tmem, uint32_t(kPStages * kPStageCols));
-}
-
 static int num_sms() {
     static int sms = 0;
     if (!sms) {
@@ -754,45 +772,31 @@ static int num_sms() {
     return sms;
 }
 
-template <int C, int MG, int ACT>
-static int launch_persistent_act(const PShape& s, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
-                                 const __nv_bfloat16* w, const float* bias, int mode, float* zio, int* status,
-                                 cudaStream_t st, const float* wlast, float* maps) {
-    auto kern = conv_hidden_tc_persistent<C, MG, ACT>;
+template <int C, int ACT>
+static int launch_rows_act(const RShape& s, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
+                           const __nv_bfloat16* w, const float* bias, int mode, float* zio, int* status,
+                           cudaStream_t st, const float* wlast, float* maps) {
+    auto kern = conv_rows_tc<C, ACT>;
     static bool configured = false;
     if (!configured) {
         ACPR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(227 * 1024)));
         configured = true;
     }
-    const long long units = (long long)batch * (n / s.CW) * (n / s.TY);
+    const long long units = (long long)batch * (n / 128) * n;
     const int grid = int(units < num_sms() ? units : num_sms());
-    kern<<<grid, kPThreads, s.smem, st>>>(in, out, w, bias, n, batch, s.RING, s.slot_bytes, mode, zio, status,
-                                          g_test_stall, wlast, maps, s.areuse);
+    kern<<<grid, RGeom<C>::THREADS, s.smem, st>>>(in, out, w, bias, n, batch, s.RING, s.DS, mode, zio, status, g_test_stall,
+                                          wlast, maps);
     ACPR_LAUNCH_CHECK();
     return AC_OK;
 }
 
-template <int C, int MG>
-static int launch_persistent_mg(const PShape& s, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
-                                const __nv_bfloat16* w, const float* bias, int act, int mode, float* zio,
-                                int* status, cudaStream_t st, const float* wlast = nullptr, float* maps = nullptr) {
-    if (act == AC_ACT_TANH)
-        return launch_persistent_act<C, MG, AC_ACT_TANH>(s, n, batch, in, out, w, bias, mode, zio, status, st, wlast,
-                                                         maps);
-    return launch_persistent_act<C, MG, AC_ACT_GELU>(s, n, batch, in, out, w, bias, mode, zio, status, st, wlast,
-                                                     maps);
-}
-
 template <int C>
-static int launch_persistent(const PShape& s, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
-                             const __nv_bfloat16* w, const float* bias, int act, int mode, float* zio,
-                             int* status, cudaStream_t st, const float* wlast = nullptr, float* maps = nullptr) {
-    if (s.MG == 1)
-        return launch_persistent_mg<C, 1>(s, n, batch, in, out, w, bias, act, mode, zio, status, st, wlast, maps);
-    if constexpr (C < 64)
-        return launch_persistent_mg<C, 2>(s, n, batch, in, out, w, bias, act, mode, zio, status, st, wlast, maps);
-    set_error("conv: no persistent kernel for C=%d, MG=%d", C, s.MG);
-    return AC_ERR_UNSUPPORTED;
+static int launch_rows(const RShape& r, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
+                       const __nv_bfloat16* w, const float* bias, int act, int mode, float* zio, int* status,
+                       cudaStream_t st, const float* wlast = nullptr, float* maps = nullptr) {
+    if (act == AC_ACT_TANH)
+        return launch_rows_act<C, AC_ACT_TANH>(r, n, batch, in, out, w, bias, mode, zio, status, st, wlast, maps);
+    return launch_rows_act<C, AC_ACT_GELU>(r, n, batch, in, out, w, bias, mode, zio, status, st, wlast, maps);
 }
 
 template <int C>
@@ -803,8 +807,8 @@ static int launch_hidden(int n, int batch, const __nv_bfloat16* in, __nv_bfloat1
         set_error("tensor-core conv: no status word");
         return AC_ERR_ARG;
     }
-    const PShape ps = p_shape(n, C);
-    if (ps.RING) return launch_persistent<C>(ps, n, batch, in, out, w, bias, act, mode, zio, status, st);
+    const RShape plan = conv_plan(n, C, false);
+    if (plan.RING) return launch_rows<C>(plan, n, batch, in, out, w, bias, act, mode, zio, status, st);
     const TcShape s = pick_shape(n, C);
     if (s.TY == 0) return AC_ERR_UNSUPPORTED;
     auto kern = act == AC_ACT_TANH ? conv_hidden_tc_kernel<C, AC_ACT_TANH> : conv_hidden_tc_kernel<C, AC_ACT_GELU>;
@@ -833,7 +837,7 @@ int hidden_layer_bf16(const cnn_desc* d, int l, int n, int batch, const __nv_bfl
     }
 }
 
-bool hidden_last_fused_supported(int n, int C) { return C >= 32 && C <= 64 && p_shape(n, C).RING > 0; }
+bool hidden_last_fused_supported(int n, int C) { return C >= 32 && C <= 64 && conv_plan(n, C, true).RING > 0; }
 
 int hidden_last_fused(const cnn_desc* d, int l, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* act_out,
                       const float* bias, const float* w_last, float* maps, int* status, cudaStream_t st,
@@ -846,12 +850,10 @@ int hidden_last_fused(const cnn_desc* d, int l, int n, int batch, const __nv_bfl
         return AC_ERR_ARG;
     }
     const __nv_bfloat16* w = static_cast<const __nv_bfloat16*>(d->packed) + size_t(l - 1) * 9 * C * C;
-    const PShape ps = p_shape(n, C);
+    const RShape plan = conv_plan(n, C, true);
     if (C == 32)
-        return launch_persistent<32>(ps, n, batch, in, act_out, w, bias, d->act, kFwdLast, zsave, status, st, w_last,
-                                     maps);
-    return launch_persistent<64>(ps, n, batch, in, act_out, w, bias, d->act, kFwdLast, zsave, status, st, w_last,
-                                 maps);
+        return launch_rows<32>(plan, n, batch, in, act_out, w, bias, d->act, kFwdLast, zsave, status, st, w_last, maps);
+    return launch_rows<64>(plan, n, batch, in, act_out, w, bias, d->act, kFwdLast, zsave, status, st, w_last, maps);
 }
 
 int hidden_dgrad_bf16(int C, int act, int n, int batch, const __nv_bfloat16* dz_next, __nv_bfloat16* dz_out,

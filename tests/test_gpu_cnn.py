@@ -86,10 +86,11 @@ def test_cnn_bf16_partition_independent():
 
 @pytest.mark.parametrize("n,L,C", [(128, 4, 32), (128, 3, 64), (512, 4, 16), (256, 3, 64), (256, 4, 32)])
 def test_cnn_bf16_persistent_shapes(n, L, C):
-    """Every persistent-kernel shape (one or two M-tiles per row, 2 to 8 rows
-    per work unit, one or two column blocks) against the oracle's
-    bf16-emulating mode, with weights large enough (sigma 0.05) that the
-    stack's output depends on its input."""
+    """The persistent row-streaming kernel for every channel count (TMEM slots
+    of 64, 128 and 256 columns), one, two or four 128-column blocks, with and
+    without the fused last layer, against the oracle's bf16-emulating mode,
+    with weights large enough (sigma 0.05) that the stack's output depends on
+    its input."""
     w, b = I.cnn_weights(L, C, seed=6, sigma=0.05)
     u = np.stack([I.random_field(n, seed=s) for s in range(2)]).astype(np.float32)
     w32, b32 = w.astype(np.float32), b.astype(np.float32)
@@ -128,6 +129,36 @@ def test_gelu_activation_error_bound():
     assert np.all(exact_hit | (err <= ulp * 1.01))
     # one-step flips are rare (about 1% of this ramp, measured)
     assert np.mean(exact_hit) > 0.98
+
+
+def test_gelu_activation_error_bound_hidden_layer():
+    """The paired-instruction GELU of the hidden tensor-core layer (the same
+    Abramowitz & Stegun 7.1.26 form, written as max(x, 0) - |x| Phi(-|x|)):
+    a 1 -> 32 -> 32 -> 1 stack at 128^2 whose first layer copies bf16(u) into
+    channel 0, whose hidden layer copies channel 0 (centre tap) and whose
+    fused last layer reads channel 0 back gives
+    out = bf16(GELU(bf16(GELU(bf16(u))))).  Each stage must be the correctly
+    rounded bf16 of the exact GELU or, where the exact value lies within the
+    approximation's error of a rounding midpoint, a neighbouring bf16 value."""
+    from math import erf, sqrt
+    n, L, C = 128, 3, 32
+    w = np.zeros(C * 9 + C * C * 9 + C * 9)
+    w[4] = 1.0                              # first layer, out channel 0, centre tap
+    w[C * 9 + 4] = 1.0                      # hidden layer, out 0 <- in 0, centre tap
+    w[C * 9 + C * C * 9 + 4] = 1.0          # last layer, in channel 0, centre tap
+    b = np.zeros(C + C + 1)
+    net = G.CoarseNet(L, C, w.astype(np.float32), b.astype(np.float32), act=1, precision=G.AC_F32, residual=0)
+    u = np.linspace(-7.0, 5.0, n * n).reshape(1, n, n).astype(np.float32)
+    got = G.cnn_coarse_step(net, torch.tensor(u, device="cuda")).cpu().numpy().astype(np.float64)
+    gelu = np.vectorize(lambda x: 0.5 * x * (1.0 + erf(x / sqrt(2.0))))
+    bf = lambda x: torch.tensor(x).to(torch.bfloat16).double().numpy()
+    ref = bf(gelu(bf(gelu(bf(u)))))
+    ulp = np.maximum(np.abs(ref), 1e-30) * 2.0 ** -7
+    err = np.abs(got - ref)
+    exact_hit = err <= 1e-7 + 1e-6 * np.abs(ref)
+    # a flip in the first stage moves the second by about one ulp as well
+    assert np.all(exact_hit | (err <= ulp * 1.2))
+    assert np.mean(exact_hit) > 0.96
 
 
 def test_cnn_bf16_mass_shift_trained_256():
@@ -184,10 +215,10 @@ def test_bounded_wait_timeout_is_reported_and_cleared():
 
 @pytest.mark.parametrize("n,C", [(256, 32), (128, 64)])
 def test_conv_tile_shapes_identical_and_autotune(n, C):
-    """Every tile shape of the persistent tensor-core kernel (M-tiles per row,
-    rows per unit, ring depth) forms each output with the same sums in the
-    same order, so G is bitwise the same under every shape; cnn_autotune
-    times them all and keeps the fastest."""
+    """Every shape of the persistent row-streaming tensor-core kernel (input
+    ring depth, TMEM slots) forms each output with the same sums in the same
+    order, so G is bitwise the same under every shape; cnn_autotune times them
+    all and keeps the fastest."""
     L = 6
     w, b = I.cnn_weights(L, C, seed=9, sigma=0.05)
     net = G.CoarseNet(L, C, w.astype(np.float32), b.astype(np.float32), act=1, precision=G.AC_F32, mass_fix=1)
