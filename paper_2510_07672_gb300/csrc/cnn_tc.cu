@@ -302,8 +302,8 @@ __device__ __forceinline__ bool p_wait(uint64_t* bar, uint32_t parity, volatile 
 //   warps 2..17, epilogue: a warp reads its TMEM lane quarter and its C/32
 //     (at least one) 8-channel chunks of the three dy blocks, frees the TMEM
 //     slot (dempty) and keeps two partial output rows in registers:
-//       finish out(y'-1) = P + D(y')[2];  P = P' + D(y')[1];  P' = D(y')[0].
-//     Every output is ((D(y-1)[0] + D(y)[1]) + D(y+1)[2]) + bias with each
+//       finish out(y'-1) = P + D(y')[2];  P = P' + D(y')[1];  P' = D(y')[0] + b.
+//     Every output is ((D(y-1)[0] + b) + D(y)[1]) + D(y+1)[2] with each
 //     D accumulated over (dx, K-step) in order, whatever the ring depth, TMEM
 //     slot count or CTA count: G is bitwise the same under every shape.
 // kFwdLast: the nine-tap projection of each pixel's activations is summed
@@ -380,11 +380,11 @@ struct RGeom {
     static constexpr int THREADS = 32 * (2 + 4 * EPW);
 };
 
-template <int C, int ACT>
+template <int C, int ACT, int mode>
 __global__ void __launch_bounds__(RGeom<C>::THREADS, 1)
 conv_rows_tc(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ out,
              const __nv_bfloat16* __restrict__ wpk, const float* __restrict__ bias, int n, int batch, int RING,
-             int DS, int mode, float* __restrict__ zio, int* __restrict__ status, int stall,
+             int DS, float* __restrict__ zio, int* __restrict__ status, int stall,
              const float* __restrict__ wlast, float* __restrict__ maps) {
     constexpr int KC = C / 8;
     constexpr int N3 = 3 * C;
@@ -436,9 +436,14 @@ conv_rows_tc(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ o
                 const int y = cur.y;
                 const long long f = cur.f;
                 const bool start = (u == u0) || (y == 0);
+                // one copy per chunk plane from the first to the last pixel that
+                // lies in the row (guard pixels included where they are
+                // interior), one 16-byte copy per wrapped guard pixel
                 const int x0 = cur.cb * 128;
-                const int xl = x0 == 0 ? n - 1 : x0 - 1;
-                const int xr = x0 + 128 == n ? 0 : x0 + 128;
+                const bool wl = x0 == 0, wr = x0 + 128 == n;
+                const int bx = wl ? x0 : x0 - 1;                                  // first pixel copied
+                const uint32_t bbytes = uint32_t(130 - int(wl) - int(wr)) * 16u;  // body bytes
+                const uint32_t boff = wl ? 16u : 0u;                              // its offset in the plane
                 for (int k = start ? 0 : 2; k < 3 && ok; ++k) {
                     int yin = y - 1 + k;
                     yin = yin < 0 ? yin + n : (yin >= n ? yin - n : yin);
@@ -451,9 +456,9 @@ conv_rows_tc(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ o
                     for (int kc = 0; kc < KC; ++kc) {
                         const __nv_bfloat16* src = in + ((size_t(f) * KC + kc) * nn + size_t(yin) * n) * 8;
                         unsigned char* dst = ring + size_t(slot) * SLOT + size_t(kc) * PLANE;
-                        tc::bulk_g2s(dst + 16, src + size_t(x0) * 8, 128u * 16u, &ctl->full[slot]);
-                        tc::bulk_g2s(dst, src + size_t(xl) * 8, 16u, &ctl->full[slot]);
-                        tc::bulk_g2s(dst + 129 * 16, src + size_t(xr) * 8, 16u, &ctl->full[slot]);
+                        tc::bulk_g2s(dst + boff, src + size_t(bx) * 8, bbytes, &ctl->full[slot]);
+                        if (wl) tc::bulk_g2s(dst, src + size_t(n - 1) * 8, 16u, &ctl->full[slot]);
+                        if (wr) tc::bulk_g2s(dst + 129 * 16, src, 16u, &ctl->full[slot]);
                     }
                     ++j;
                     rp.next();
@@ -473,7 +478,7 @@ conv_rows_tc(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ o
         }
         tc::fence_proxy_async_smem();
         if (tid - 32 < C) ctl->bias[tid - 32] = (mode != kDgrad) ? bias[tid - 32] : 0.f;
-        if (mode == kFwdLast)
+        if constexpr (mode == kFwdLast)
             for (int e = tid - 32; e < 10 * C; e += blockDim.x - 32) {
                 const int tap = e % 10, c = e / 10;
                 ctl->wl[e] = tap < 9 ? bf16r(wlast[c * 9 + tap]) : 0.f;
@@ -572,31 +577,31 @@ conv_rows_tc(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ o
                             for (int e = 0; e < 4; ++e)
                                 d[dy][e] = f2(__uint_as_float(v[dy][2 * e]), __uint_as_float(v[dy][2 * e + 1]));
                         if (k == 2) {
-                            // output row y is complete: P + D(y+1)[dy=2]
+                            // output row y is complete: ((D(y-1)[0] + b) + D(y)[1]) + D(y+1)[2]
                             const size_t off = ((size_t(f) * KC + kc) * nn + pix) * 8;
-                            f32x2 acc[4];
+                            f32x2 z[4];
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) acc[e] = f2_add(P[c][e], d[2][e]);
+                            for (int e = 0; e < 4; ++e) z[e] = f2_add(P[c][e], d[2][e]);
                             uint32_t packed[4];
-                            if (mode != kDgrad) {
-                                f32x2 z[4];
+                            if constexpr (mode != kDgrad) {
                                 float a8[8];
 #pragma unroll
                                 for (int e = 0; e < 4; ++e) {
-                                    z[e] = f2_add(acc[e], bias2[kc * 4 + e]);
                                     float a0, a1;
                                     f2split(act2<ACT>(z[e]), a0, a1);
                                     const __nv_bfloat162 hh = __floats2bfloat162_rn(a0, a1);
                                     packed[e] = *reinterpret_cast<const uint32_t*>(&hh);
-                                    a8[2 * e] = __low2float(hh);
-                                    a8[2 * e + 1] = __high2float(hh);
+                                    if constexpr (mode == kFwdLast) {
+                                        a8[2 * e] = __low2float(hh);
+                                        a8[2 * e + 1] = __high2float(hh);
+                                    }
                                 }
                                 if (zio) {
                                     f32x2* z2 = reinterpret_cast<f32x2*>(zio + off);
 #pragma unroll
                                     for (int e = 0; e < 4; ++e) z2[e] = z[e];
                                 }
-                                if (mode == kFwdLast) {
+                                if constexpr (mode == kFwdLast) {
                                     // channels in order, taps in pairs: each tap's sum is the
                                     // same fma chain as one tap at a time
 #pragma unroll
@@ -614,7 +619,7 @@ conv_rows_tc(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ o
 #pragma unroll
                                 for (int e = 0; e < 4; ++e) {
                                     float a0, a1;
-                                    f2split(acc[e], a0, a1);
+                                    f2split(z[e], a0, a1);
                                     const __nv_bfloat162 hh = __floats2bfloat162_rn(a0 * act_grad_c<ACT>(zz[2 * e]),
                                                                                     a1 * act_grad_c<ACT>(zz[2 * e + 1]));
                                     packed[e] = *reinterpret_cast<const uint32_t*>(&hh);
@@ -628,14 +633,14 @@ conv_rows_tc(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ o
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             P[c][e] = f2_add(Pn[c][e], d[1][e]);
-                            Pn[c][e] = d[0][e];
+                            if constexpr (mode == kDgrad) Pn[c][e] = d[0][e];
+                            else Pn[c][e] = f2_add(d[0][e], bias2[kc * 4 + e]);  // the bias enters first
                         }
                     }
-                    if (k == 2 && mode == kFwdLast) {
+                    if (mode == kFwdLast && k == 2) {
                         // the quarter's EPW partial projections, summed in warp order
                         const int par = rows_done & 1;
                         float* sc = scratch + size_t(par * 4 + q) * (4 * 9 * 32);
-#pragma unroll
 #pragma unroll
                         for (int m = 0; m < 5; ++m) {
                             float t0, t1;
@@ -772,11 +777,11 @@ static int num_sms() {
     return sms;
 }
 
-template <int C, int ACT>
-static int launch_rows_act(const RShape& s, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
-                           const __nv_bfloat16* w, const float* bias, int mode, float* zio, int* status,
-                           cudaStream_t st, const float* wlast, float* maps) {
-    auto kern = conv_rows_tc<C, ACT>;
+template <int C, int ACT, int MODE>
+static int launch_rows_mode(const RShape& s, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
+                            const __nv_bfloat16* w, const float* bias, float* zio, int* status, cudaStream_t st,
+                            const float* wlast, float* maps) {
+    auto kern = conv_rows_tc<C, ACT, MODE>;
     static bool configured = false;
     if (!configured) {
         ACPR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(227 * 1024)));
@@ -784,10 +789,22 @@ static int launch_rows_act(const RShape& s, int n, int batch, const __nv_bfloat1
     }
     const long long units = (long long)batch * (n / 128) * n;
     const int grid = int(units < num_sms() ? units : num_sms());
-    kern<<<grid, RGeom<C>::THREADS, s.smem, st>>>(in, out, w, bias, n, batch, s.RING, s.DS, mode, zio, status, g_test_stall,
-                                          wlast, maps);
+    kern<<<grid, RGeom<C>::THREADS, s.smem, st>>>(in, out, w, bias, n, batch, s.RING, s.DS, zio, status,
+                                                  g_test_stall, wlast, maps);
     ACPR_LAUNCH_CHECK();
     return AC_OK;
+}
+
+template <int C, int ACT>
+static int launch_rows_act(const RShape& s, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* out,
+                           const __nv_bfloat16* w, const float* bias, int mode, float* zio, int* status,
+                           cudaStream_t st, const float* wlast, float* maps) {
+    if (mode == kDgrad)
+        return launch_rows_mode<C, ACT, kDgrad>(s, n, batch, in, out, w, bias, zio, status, st, wlast, maps);
+    if constexpr (C >= 32)
+        if (mode == kFwdLast)
+            return launch_rows_mode<C, ACT, kFwdLast>(s, n, batch, in, out, w, bias, zio, status, st, wlast, maps);
+    return launch_rows_mode<C, ACT, kFwd>(s, n, batch, in, out, w, bias, zio, status, st, wlast, maps);
 }
 
 template <int C>
