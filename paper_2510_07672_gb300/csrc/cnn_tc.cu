@@ -293,9 +293,10 @@ __device__ __forceinline__ bool p_wait(uint64_t* bar, uint32_t parity, volatile 
 // y), ordered (f, cb, y); CTA c takes a contiguous range and streams the input
 // rows y-1, y, y+1 at the start of a block run and one new row (y+1) per unit
 // after that.
-//   warp 0 (lane 0), producer: each streamed input row (128 columns plus one
-//     wrapped pixel each side, all C/8 chunk planes) into a ring slot by
-//     cp.async.bulk, completing on full[slot];
+//   warp 0, producer: each streamed input row (128 columns plus one pixel
+//     each side, wrapped at the field's edge, all C/8 chunk planes) into a
+//     ring slot: one bulk copy per plane, wrapped pixels by cp.async, all
+//     completing on full[slot];
 //   warp 1 (lane 0), MMA issuer: 3 x C/16 MMAs of 128 x 3C x 16 per streamed
 //     row into TMEM slot j % DS (DS slots of 3C columns, padded); tcgen05.commit
 //     releases the ring slot (empty) and marks the TMEM slot full (dfull);
@@ -311,6 +312,16 @@ __device__ __forceinline__ bool p_wait(uint64_t* bar, uint32_t parity, volatile 
 // fixed order through shared memory.
 constexpr int kRMaxRing = 24;
 constexpr int kRMaxD = 5;
+
+// 16-byte global -> shared copy on the load/store path (cp.async), and an
+// arrival on `bar` once all of this thread's earlier cp.async copies landed.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 struct RCtl {
     uint64_t never;  // test hook: nothing ever arrives here
@@ -409,7 +420,7 @@ conv_rows_tc(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ o
 
     if (tid == 0) {
         for (int i = 0; i < RING; ++i) {
-            tc::mbar_init(&ctl->full[i], 1);
+            tc::mbar_init(&ctl->full[i], 1 + 32);  // producer's byte count + 32 lanes' cp.async
             tc::mbar_init(&ctl->empty[i], 1);
         }
         for (int i = 0; i < DS; ++i) {
@@ -426,48 +437,61 @@ conv_rows_tc(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ o
     __syncthreads();
 
     if (warp == 0) {
-        if (lane == 0) {
-            // ---- producer: starts at once; the other warps stage the weights meanwhile
-            long long j = 0;
-            RingPos rp(RING);
-            RowCursor cur(u0, n, NB);
-            bool ok = true;
-            for (long long u = u0; u < u1 && ok; ++u, cur.next()) {
-                const int y = cur.y;
-                const long long f = cur.f;
-                const bool start = (u == u0) || (y == 0);
-                // one copy per chunk plane from the first to the last pixel that
-                // lies in the row (guard pixels included where they are
-                // interior), one 16-byte copy per wrapped guard pixel
-                const int x0 = cur.cb * 128;
-                const bool wl = x0 == 0, wr = x0 + 128 == n;
-                const int bx = wl ? x0 : x0 - 1;                                  // first pixel copied
-                const uint32_t bbytes = uint32_t(130 - int(wl) - int(wr)) * 16u;  // body bytes
-                const uint32_t boff = wl ? 16u : 0u;                              // its offset in the plane
-                for (int k = start ? 0 : 2; k < 3 && ok; ++k) {
-                    int yin = y - 1 + k;
-                    yin = yin < 0 ? yin + n : (yin >= n ? yin - n : yin);
-                    const int slot = rp.idx;
-                    if (j >= RING && !p_wait(&ctl->empty[slot], rp.phase ^ 1u, abort_flag, status)) {
-                        ok = false;
-                        break;
-                    }
-                    tc::mbar_arrive_expect_tx(&ctl->full[slot], SLOT);
-                    for (int kc = 0; kc < KC; ++kc) {
-                        const __nv_bfloat16* src = in + ((size_t(f) * KC + kc) * nn + size_t(yin) * n) * 8;
-                        unsigned char* dst = ring + size_t(slot) * SLOT + size_t(kc) * PLANE;
-                        tc::bulk_g2s(dst + boff, src + size_t(bx) * 8, bbytes, &ctl->full[slot]);
-                        if (wl) tc::bulk_g2s(dst, src + size_t(n - 1) * 8, 16u, &ctl->full[slot]);
-                        if (wr) tc::bulk_g2s(dst + 129 * 16, src, 16u, &ctl->full[slot]);
-                    }
-                    ++j;
-                    rp.next();
+        // ---- producer warp: starts at once; the other warps stage the weights
+        // meanwhile.  Per streamed row and chunk plane lane 0 issues one bulk
+        // copy from the first to the last pixel that lies in the row (guard
+        // pixels included where they are interior); a wrapped guard pixel is a
+        // 16-byte cp.async by lane kc (a 16-byte bulk copy costs the copy
+        // engine about as much as a 2 KB one).  Every lane then arrives on
+        // full[slot] once its cp.async copies have landed.
+        long long j = 0;
+        RingPos rp(RING);
+        RowCursor cur(u0, n, NB);
+        bool ok = true;
+        for (long long u = u0; u < u1 && ok; ++u, cur.next()) {
+            const int y = cur.y;
+            const long long f = cur.f;
+            const bool start = (u == u0) || (y == 0);
+            const int x0 = cur.cb * 128;
+            const bool wl = x0 == 0, wr = x0 + 128 == n;
+            const int bx = wl ? x0 : x0 - 1;                                  // first pixel of the bulk copy
+            const uint32_t bbytes = uint32_t(130 - int(wl) - int(wr)) * 16u;  // its bytes
+            const uint32_t boff = wl ? 16u : 0u;                              // its offset in the plane
+            for (int k = start ? 0 : 2; k < 3; ++k) {
+                int yin = y - 1 + k;
+                yin = yin < 0 ? yin + n : (yin >= n ? yin - n : yin);
+                const int slot = rp.idx;
+                bool free_slot = true;
+                if (lane == 0 && j >= RING) free_slot = p_wait(&ctl->empty[slot], rp.phase ^ 1u, abort_flag, status);
+                if (!__shfl_sync(0xffffffffu, free_slot, 0)) {
+                    ok = false;
+                    break;
                 }
+                unsigned char* dst = ring + size_t(slot) * SLOT;
+                const __nv_bfloat16* src = in + (size_t(f) * KC * nn + size_t(yin) * n) * 8;
+                if (lane == 0) {
+                    tc::mbar_arrive_expect_tx(&ctl->full[slot], uint32_t(KC) * bbytes);
+                    for (int kc = 0; kc < KC; ++kc)
+                        tc::bulk_g2s(dst + size_t(kc) * PLANE + boff, src + (size_t(kc) * nn + size_t(bx)) * 8, bbytes,
+                                     &ctl->full[slot]);
+                }
+                if (lane < KC) {
+                    unsigned char* d = dst + size_t(lane) * PLANE;
+                    const __nv_bfloat16* r = src + size_t(lane) * nn * 8;
+                    if (wl) cp_async16(d, r + size_t(n - 1) * 8);
+                    if (wr) cp_async16(d + 129 * 16, r);
+                }
+                cp_async_arrive(&ctl->full[slot]);
+                ++j;
+                rp.next();
             }
-            // drain: every issued copy lands before the CTA may exit
+        }
+        // drain: every issued copy lands before the CTA may exit
+        if (lane == 0)
             for (long long x = j > RING ? j - RING : 0; x < j; ++x)
                 tc::mbar_wait_bounded(&ctl->full[x % RING], uint32_t((x / RING) & 1), kTcSpin);
-        }
+        cp_async_wait_all();
+        __syncwarp();
     } else {
         // ---- weights (permuted to [dx][kc][dy][cout][8]), bias, last-layer taps
         const uint4* wsrc = reinterpret_cast<const uint4*>(wpk);
@@ -510,6 +534,9 @@ conv_rows_tc(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ o
                         const int ds = dp.idx;
                         if (j >= DS && !(ok = p_wait(&ctl->dempty[ds], dp.phase ^ 1u, abort_flag, status))) break;
                         if (!(ok = p_wait(&ctl->full[slot], rp.phase, abort_flag, status))) break;
+                        // the guard pixels came by cp.async (generic proxy); the MMAs read
+                        // the slot through the async proxy
+                        tc::fence_proxy_async_smem();
                         tc::fence_after_sync();
                         const uint32_t in_u = ring_u + uint32_t(slot) * (SLOT >> 4);
                         const uint32_t d_addr = tmem + uint32_t(ds * DCOLS);
