@@ -297,12 +297,13 @@ __device__ __forceinline__ bool p_wait(uint64_t* bar, uint32_t parity, volatile 
 //     each side, wrapped at the field's edge, all C/8 chunk planes) into a
 //     ring slot: one bulk copy per plane, wrapped pixels by cp.async, all
 //     completing on full[slot];
-//   warp 1 (lane 0), MMA issuer: 3 x C/16 MMAs of 128 x 3C x 16 per streamed
-//     row into TMEM slot j % DS (DS slots of 3C columns, padded); tcgen05.commit
-//     releases the ring slot (empty) and marks the TMEM slot full (dfull);
-//   warps 2..17, epilogue: a warp reads its TMEM lane quarter and its C/32
-//     (at least one) 8-channel chunks of the three dy blocks, frees the TMEM
-//     slot (dempty) and keeps two partial output rows in registers:
+//   warps 1 and 2 (lane 0), MMA issuers of the even and odd rows: 3 x C/16
+//     MMAs of 128 x 3C x 16 per streamed row into TMEM slot j % DS (DS slots
+//     of 3C columns, padded); tcgen05.commit releases the ring slot (empty)
+//     and marks the TMEM slot full (dfull);
+//   warps 3 .. 2 + 4 EPW, epilogue: a warp reads its TMEM lane quarter and
+//     its C/32 (at least one) 8-channel chunks of the three dy blocks, frees
+//     the TMEM slot (dempty) and keeps two partial output rows in registers:
 //       finish out(y'-1) = P + D(y')[2];  P = P' + D(y')[1];  P' = D(y')[0] + b.
 //     Every output is ((D(y-1)[0] + b) + D(y)[1]) + D(y+1)[2] with each
 //     D accumulated over (dx, K-step) in order, whatever the ring depth, TMEM
@@ -382,13 +383,13 @@ struct RowCursor {
 };
 
 // Epilogue geometry: CPW 8-channel chunks per warp, EPW warps per TMEM lane
-// quarter, THREADS = producer + MMA warps + 4 EPW epilogue warps.
+// quarter, THREADS = producer warp + two MMA warps + 4 EPW epilogue warps.
 template <int C>
 struct RGeom {
     static constexpr int KC = C / 8;
     static constexpr int CPW = KC >= 4 ? KC / 4 : 1;
     static constexpr int EPW = KC / CPW;
-    static constexpr int THREADS = 32 * (2 + 4 * EPW);
+    static constexpr int THREADS = 32 * (3 + 4 * EPW);
 };
 
 template <int C, int ACT, int mode>
@@ -428,7 +429,7 @@ conv_rows_tc(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ o
             tc::mbar_init(&ctl->dempty[i], 4 * EPW);
         }
         for (int i = 0; i < 8; ++i) tc::mbar_init(&ctl->qbar[i / 4][i % 4], EPW);
-        tc::mbar_init(&ctl->fin, 1);
+        tc::mbar_init(&ctl->fin, 2);
         tc::mbar_init(&ctl->never, 1);
         ctl->abort = 0;
         tc::fence_mbar_init();
@@ -513,9 +514,12 @@ conv_rows_tc(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ o
         tc::fence_after_sync();
         const uint32_t tmem = ctl->tmem;
 
-        if (warp == 1) {
+        if (warp == 1 || warp == 2) {
             if (lane == 0) {
-                // ---- MMA issuer
+                // ---- MMA issuers: warp 1 takes the even stream positions, warp 2
+                // the odd ones, so that one issuer's waits and address
+                // arithmetic overlap the other's MMAs
+                const long long mine = warp - 1;
                 bool ok = true;
                 // test hook: a wait that cannot succeed, so the bounded-wait path runs
                 if (stall > 0) ok = p_wait(&ctl->never, 0, abort_flag, status, stall);
@@ -530,6 +534,7 @@ conv_rows_tc(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ o
                 for (long long u = u0; u < u1 && ok; ++u, y = (y + 1 == n ? 0 : y + 1)) {
                     const bool start = (u == u0) || (y == 0);
                     for (int k = start ? 0 : 2; k < 3; ++k, ++j, rp.next(), dp.next()) {
+                        if ((j & 1) != mine) continue;
                         const int slot = rp.idx;
                         const int ds = dp.idx;
                         if (j >= DS && !(ok = p_wait(&ctl->dempty[ds], dp.phase ^ 1u, abort_flag, status))) break;
@@ -553,14 +558,14 @@ conv_rows_tc(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ o
                         tc::mma_commit(&ctl->dfull[ds]);
                     }
                 }
-                // every MMA issued so far completes before TMEM is freed
+                // every MMA issued so far (by both issuers) completes before TMEM is freed
                 tc::mma_commit(&ctl->fin);
                 tc::mbar_wait_bounded(&ctl->fin, 0, kTcSpin);
             }
-        } else if ((warp - 2) / 4 < EPW) {
+        } else if (warp >= 3) {
             // ---- epilogue
             const int q = warp & 3;         // TMEM lane quarter: pixels 32 q .. 32 q + 31
-            const int g = (warp - 2) >> 2;  // chunk group: chunks g CPW .. g CPW + CPW - 1
+            const int g = (warp - 3) >> 2;  // chunk group: chunks g CPW .. g CPW + CPW - 1
             const f32x2* bias2 = reinterpret_cast<const f32x2*>(ctl->bias);
             f32x2 P[CPW][4], Pn[CPW][4];  // partial sums of output rows y and y + 1, channel pairs
 #pragma unroll
