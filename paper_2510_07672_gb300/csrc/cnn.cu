@@ -103,23 +103,25 @@ __global__ void conv_first_bf16_kernel(const float* __restrict__ u, __nv_bfloat1
 #pragma unroll
         for (int e = 0; e < kFirstPx + 2; ++e)
             v[a][e] = bf16r(f[(long long)wrap(y + a - 1, n) * n + wrap(x + e - 1, n)]);
+    static_assert(kFirstPx == 2, "the two pixels of a thread are the lanes of the paired instructions");
+    f32x2 vp[3][3];  // the window of the pair: vp[dy][dx] = (v[dy][dx], v[dy][dx + 1])
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int e = 0; e < 3; ++e) vp[a][e] = f2(v[a][e], v[a][e + 1]);
 #pragma unroll
     for (int kc = 0; kc < C / 8; ++kc) {
         __align__(16) __nv_bfloat16 o8[kFirstPx][8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int o = kc * 8 + i;
-            float s[kFirstPx];
+            f32x2 s2 = f2(0.f, 0.f);
 #pragma unroll
-            for (int px = 0; px < kFirstPx; ++px) s[px] = 0.f;
-#pragma unroll
-            for (int t = 0; t < 9; ++t) {
-                const float wt = ws[o * 9 + t];
-#pragma unroll
-                for (int px = 0; px < kFirstPx; ++px) s[px] = fmaf(wt, v[t / 3][px + t % 3], s[px]);
-            }
-#pragma unroll
-            for (int px = 0; px < kFirstPx; ++px) o8[px][i] = __float2bfloat16_rn(act_c<ACT>(s[px] + bs[o]));
+            for (int t = 0; t < 9; ++t) s2 = f2_fma(f2(ws[o * 9 + t], ws[o * 9 + t]), vp[t / 3][t % 3], s2);
+            float a0, a1;
+            f2split(act2<ACT>(f2_add(s2, f2(bs[o], bs[o]))), a0, a1);
+            o8[0][i] = __float2bfloat16_rn(a0);
+            o8[1][i] = __float2bfloat16_rn(a1);
         }
 #pragma unroll
         for (int px = 0; px < kFirstPx; ++px)

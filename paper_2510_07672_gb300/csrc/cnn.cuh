@@ -94,9 +94,23 @@ __device__ __forceinline__ f32x2 gelu2(f32x2 x) {
     return f2_fma(nx, q, rx);
 }
 
+// One lane of gelu2 with the same roundings (scalar kernels and the paired
+// ones give the same bits for the same input).
+__device__ __forceinline__ float gelu1(float x) {
+    const float nx = -fabsf(x);
+    const float z = __fmul_rn(nx, -0.70710678118654752440f);
+    const float t = rcp_hw(__fmaf_rn(z, 0.3275911f, 1.0f));
+    float p = __fmaf_rn(t, 0.5307027145f, -0.7265760135f);
+    p = __fmaf_rn(t, p, 0.7107068705f);
+    p = __fmaf_rn(t, p, -0.142248368f);
+    p = __fmaf_rn(t, p, 0.127414796f);
+    const float q = __fmul_rn(__fmul_rn(p, t), ex2_hw(__fmul_rn(__fmul_rn(x, x), -0.72134752044448170368f)));
+    return __fmaf_rn(nx, q, fmaxf(x, 0.0f));
+}
+
 // Activation after every conv but the last: tanh, or GELU x * Phi(x)
-// (float32: Phi by phi_as; float64: 0.5 (1 + erf(x / sqrt 2))).
-__device__ __forceinline__ float act_apply_gelu(float x) { return x * phi_as(x); }
+// (float32: gelu1 / gelu2; float64: 0.5 (1 + erf(x / sqrt 2))).
+__device__ __forceinline__ float act_apply_gelu(float x) { return gelu1(x); }
 __device__ __forceinline__ double act_apply_gelu(double x) {
     return 0.5 * x * (1.0 + erf(x * 0.70710678118654752440));
 }
