@@ -336,6 +336,13 @@ int cnn_backward(const cnn_desc* desc, int n, int batch, const float* u_in, cons
                  float* grad_in, float* grad_w, float* grad_b, int accumulate, void* train_ws,
                  acpr_stream stream);
 
+/* Weight gradients of the hidden C -> C layers of cnn_backward: on the tensor
+ * cores (default; C = 64 and n a multiple of 128, bf16 products summed in
+ * float32 in TMEM, per-chunk partials reduced in a fixed order) when `on` is
+ * nonzero, on the CUDA cores otherwise (both deterministic; they differ by the
+ * order of the float32 sums).  Process-wide host state, not thread-safe. */
+int cnn_train_set_wgrad_tc(int on);
+
 /* One Adam update of `count` float32 parameters (device arrays w, grad and the
  * moment estimates m, v), step number t >= 1 (bias correction 1 - beta^t). */
 int cnn_adam_step(float* w, const float* grad, float* m, float* v, long long count, double lr,

@@ -14,7 +14,7 @@ from .abi import (  # noqa: F401
     ac_fine_workspace_bytes, ac_fine_propagate_slices_ws,
     ac_fine_variants, ac_fine_set_variant, ac_fine_get_variant, ac_fine_autotune, ac_fine_propagate_work,
     ac_fine_trajectory, ac_fine_adjoint, ac_energy, ac_energy_grad, ac_energy_gradient_ic,
-    cnn_packed_bytes, cnn_work_bytes, cnn_pack_weights, cnn_coarse_step, ac_conv_status, ac_test_conv_stall,
+    cnn_packed_bytes, cnn_work_bytes, cnn_pack_weights, cnn_coarse_step, ac_conv_status, ac_test_conv_stall, cnn_train_set_wgrad_tc,
     cnn_conv_variants, cnn_conv_set_variant, cnn_autotune,
     parareal_residual, parareal_residual_noalloc, ac_launch_count, parareal_solve_many, Parareal, CoarseNet, FineParams,
     TrainableCoarseNet, mse_loss_grad, coarse_step_function, fine_solve_function, fine_solve,

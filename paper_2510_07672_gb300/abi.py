@@ -63,7 +63,7 @@ EXPORTS = ["ac_last_error", "ac_fine_supported", "ac_fine_step", "ac_fine_propag
            "ac_fine_autotune", "ac_fine_propagate_work", "ac_fine_workspace_bytes", "ac_fine_propagate_slices_ws", "ac_fine_trajectory", "ac_fine_adjoint", "ac_energy", "ac_energy_grad",
            "ac_energy_gradient_workspace", "ac_energy_gradient_ic",
            "ac_conv_status", "ac_test_conv_stall", "cnn_conv_variant_count", "cnn_conv_variant_shape",
-           "cnn_conv_set_variant", "cnn_conv_get_variant", "cnn_autotune", "cnn_train_bytes", "cnn_forward_train", "cnn_backward", "cnn_adam_step", "mse_loss_grad",
+           "cnn_conv_set_variant", "cnn_conv_get_variant", "cnn_autotune", "cnn_train_bytes", "cnn_forward_train", "cnn_backward", "cnn_train_set_wgrad_tc", "cnn_adam_step", "mse_loss_grad",
            "acnn_param_count", "acnn_create", "acnn_destroy", "acnn_work_bytes", "acnn_forward", "acnn_train_bytes",
            "acnn_forward_train", "acnn_backward", "loss_acn_work_bytes", "loss_acn", "acnn_adam_step",
            "acnn_train_alg1", "acnn_train_alg1_bytes", "ac_parareal_set_coarse_acnn",
@@ -144,6 +144,7 @@ def load(build_if_missing: bool = True):
         L.cnn_forward_train.argtypes = [P(cnn_desc), I, I, S, S, S, S]
         L.cnn_backward.argtypes = [P(cnn_desc), I, I, S, S, S, S, S, I, S, S]
         L.cnn_adam_step.argtypes = [S, S, S, S, C.c_longlong, D, D, D, D, I, S]
+        L.cnn_train_set_wgrad_tc.argtypes = [I]
         L.mse_loss_grad.argtypes = [S, S, C.c_longlong, D, S, I, S, S, I, S]
         L.ac_parareal_destroy.argtypes = [S]
         L.ac_parareal_destroy.restype = None
@@ -823,6 +824,12 @@ def ac_test_conv_stall(polls: int):
     """Test hook: polls > 0 makes the persistent tensor-core conv kernels wait,
     for that many polls, on an mbarrier nothing arrives on (0 turns it off)."""
     _check(load().ac_test_conv_stall(int(polls)))
+
+
+def cnn_train_set_wgrad_tc(on: bool):
+    """Hidden-layer weight gradients of cnn_backward on the tensor cores (True,
+    default; C = 64, n a multiple of 128) or on the CUDA cores (False)."""
+    _check(load().cnn_train_set_wgrad_tc(int(bool(on))))
 
 
 def parareal_solve_many(handles, streams, tol, kmax, allow_unconverged=False):

@@ -226,6 +226,16 @@ int conv_variant_describe(int n, int C, int index, int* ring, int* slots);
 int conv_set_variant(int n, int C, int index);  // -1: automatic
 int conv_get_variant(int n, int C);
 
+// Weight gradient of a hidden C -> C layer on the tensor cores (C = 64, n a
+// multiple of 128): writes the weight partials part[chunk][tap][co][ci] and
+// the bias partials part[chunk][0][C*C + co] of `chunks` pixel chunks, for
+// the fixed-order reduction of the CUDA-core path.  set_wgrad_tc(false)
+// selects the CUDA-core path everywhere (tests).
+void set_wgrad_tc(bool on);
+bool wgrad_tc_supported(int C, int n);
+int wgrad_tc_partials(int n, int batch, const __nv_bfloat16* a, const __nv_bfloat16* dz, float* part, int chunks,
+                      int* status, cudaStream_t st);
+
 bool hidden_last_fused_supported(int n, int C);
 int hidden_last_fused(const cnn_desc* d, int l, int n, int batch, const __nv_bfloat16* in, __nv_bfloat16* act_out,
                       const float* bias, const float* w_last, float* maps, int* status, cudaStream_t st,

@@ -23,13 +23,13 @@
 #include <algorithm>
 
 #include "cnn.cuh"
+#include "tc_pipe.cuh"
 #include "tc_ptx.cuh"
 
 namespace acpr {
 
 namespace {
 constexpr int kTcThreads = 256;
-constexpr long long kTcSpin = 4000000;  // ~0.2 s of polls with 32 ns sleeps
 // Test hook (ac_test_conv_stall): > 0 makes the next persistent conv launches'
 // MMA issuer wait, with this poll limit, on an mbarrier nothing arrives on.
 int g_test_stall = 0;
@@ -264,22 +264,6 @@ conv_hidden_tc_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __res
     if (warp == 0) tc::tmem_dealloc(tmem, uint32_t(ncols));
 }
 
-// Bounded wait on phase `parity` of `bar` by one role of a warp-specialised
-// kernel: gives up once another role has given up (abort flag in shared
-// memory) or after `limit` polls, then raises the abort flag and stores 3 in
-// the caller's status word.
-__device__ __forceinline__ bool p_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
-                                       long long limit = kTcSpin) {
-    for (long long i = 0; i < limit; ++i) {
-        if (tc::mbar_try_wait(bar, parity)) return true;
-        if (*abort_flag) return false;
-        __nanosleep(32);
-    }
-    *abort_flag = 1;
-    atomicExch(status, 3);
-    return false;
-}
-
 // ------------------------------------------------------- row streaming --
 // Persistent kernel that reads each input row once and folds the vertical
 // taps in TMEM.  Output row y of a 3x3 conv is
@@ -314,16 +298,6 @@ __device__ __forceinline__ bool p_wait(uint64_t* bar, uint32_t parity, volatile 
 constexpr int kRMaxRing = 24;
 constexpr int kRMaxD = 5;
 
-// 16-byte global -> shared copy on the load/store path (cp.async), and an
-// arrival on `bar` once all of this thread's earlier cp.async copies landed.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 struct RCtl {
     uint64_t never;  // test hook: nothing ever arrives here
     uint64_t full[kRMaxRing];
@@ -344,43 +318,6 @@ constexpr size_t kRScratchBytes = size_t(2) * 4 * 4 * 9 * 32 * sizeof(float);  /
 // slot starts on a multiple of its own width.
 __host__ __device__ constexpr int r_dcols(int C) { return C <= 16 ? 64 : (C <= 32 ? 128 : 256); }
 __host__ __device__ constexpr uint32_t r_slot_bytes(int C) { return uint32_t(C / 8) * 130u * 16u; }
-
-// Position in a ring of `size` entries: index and the parity of the pass
-// over the ring (the mbarrier phase it waits for), advanced without division.
-struct RingPos {
-    int idx = 0;
-    uint32_t phase = 0;
-    int size;
-    __device__ explicit RingPos(int sz) : size(sz) {}
-    __device__ void next() {
-        if (++idx == size) {
-            idx = 0;
-            phase ^= 1u;
-        }
-    }
-};
-
-// Output row (field f, column block cb, row y) of work unit u, advanced by
-// one unit at a time (one division per CTA, none in the loops).
-struct RowCursor {
-    int y, cb, NB, n;
-    long long f;
-    __device__ RowCursor(long long u, int n_, int nb) : NB(nb), n(n_) {
-        y = int(u % n_);
-        const long long t = u / n_;
-        cb = int(t % nb);
-        f = t / nb;
-    }
-    __device__ void next() {
-        if (++y == n) {
-            y = 0;
-            if (++cb == NB) {
-                cb = 0;
-                ++f;
-            }
-        }
-    }
-};
 
 // Epilogue geometry: CPW 8-channel chunks per warp, EPW warps per TMEM lane
 // quarter, THREADS = producer warp + two MMA warps + 4 EPW epilogue warps.

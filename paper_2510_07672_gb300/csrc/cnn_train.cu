@@ -424,7 +424,16 @@ static int backward(const cnn_desc* d, int n, int batch, const float* u, const f
     int cur = 0;
     // hidden layers L-2 .. 1: dz[cur] holds dz_l
     for (int l = L - 2; l >= 1; --l) {
-        rc = wgrad<C, C>(A(l), dz[cur], part, gw + woffs[l], gb + boffs[l], batch, n, C, accumulate, st);
+        if (wgrad_tc_supported(C, n)) {
+            rc = wgrad_tc_partials(n, batch, A(l), dz[cur], part, kChunks, conv_status(ws), st);
+            if (rc) return rc;
+            const int tot = C * C * 9 + C;
+            wgrad_reduce_kernel<<<(tot + 255) / 256, 256, 0, st>>>(part, gw + woffs[l], gb + boffs[l], C, C, C,
+                                                                   accumulate);
+            ACPR_LAUNCH_CHECK();
+        } else {
+            rc = wgrad<C, C>(A(l), dz[cur], part, gw + woffs[l], gb + boffs[l], batch, n, C, accumulate, st);
+        }
         if (rc) return rc;
         __nv_bfloat16* wl = wt + size_t(l - 1) * 9 * C * C;
         rc = pack_hidden_t(C, W + woffs[l], wl, st);

@@ -25,7 +25,7 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("n,L,C,act,mass_fix", [(32, 4, 16, 1, 0), (16, 3, 32, 0, 0), (64, 5, 32, 1, 0),
-                                                (32, 4, 16, 1, 1)])
+                                                (32, 4, 16, 1, 1), (128, 4, 64, 1, 1)])
 def test_backward_matches_oracle(n, L, C, act, mass_fix):
     w, b = I.cnn_weights(L, C, seed=7, sigma=0.25)
     w, b = w.astype(np.float32), b.astype(np.float32)
@@ -147,3 +147,42 @@ def test_training_reduces_one_slice_error():
     e1 = err()
     assert losses[-1] < 0.5 * losses[0]
     assert e1 < 0.5 * e0, (e0, e1)
+
+
+def test_weight_gradient_tensor_cores_match_cuda_cores():
+    """The hidden layers' weight gradient on the tensor cores (C = 64, n a
+    multiple of 128: per-tap 64 x 64 x 16 MMAs over 16-pixel groups, float32
+    sums in TMEM, per-chunk partials) equals the CUDA-core one up to the order
+    of the float32 sums, is bitwise repeatable, and leaves every other
+    gradient unchanged."""
+    n, L, C, batch = 256, 4, 64, 3
+    w, b = I.cnn_weights(L, C, seed=11, sigma=0.05)
+    u = np.stack([I.random_field(n, seed=s) for s in range(batch)]).astype(np.float32)
+    g = np.random.default_rng(2).standard_normal((batch, n, n)).astype(np.float32)
+    U, Gt = torch.tensor(u, device="cuda"), torch.tensor(g, device="cuda")
+    res = {}
+    try:
+        for tc in (True, False, True):
+            G.cnn_train_set_wgrad_tc(tc)
+            net = G.TrainableCoarseNet(L, C, w.astype(np.float32), b.astype(np.float32), act=1, mass_fix=0)
+            ws = net.new_workspace(n, batch)
+            net.forward_train(U, ws)
+            du = torch.empty_like(U)
+            net.backward(U, Gt, ws, grad_in=du)
+            key = "tc" if tc else "cc"
+            if key in res:
+                assert torch.equal(res[key][0], net.gw) and torch.equal(res[key][1], net.gb)
+            res[key] = (net.gw.clone(), net.gb.clone(), du.clone())
+    finally:
+        G.cnn_train_set_wgrad_tc(True)
+    gw_tc, gb_tc, du_tc = res["tc"]
+    gw_cc, gb_cc, du_cc = res["cc"]
+    assert torch.equal(du_tc, du_cc)  # the input gradient does not involve the weight gradient
+    # first and last layers stay on the CUDA cores: identical
+    first = 9 * C
+    last = C * 9
+    assert torch.equal(gw_tc[:first], gw_cc[:first]) and torch.equal(gw_tc[-last:], gw_cc[-last:])
+    rel = ((gw_tc - gw_cc).norm() / gw_cc.norm()).item()
+    assert rel < 1e-4, rel
+    relb = ((gb_tc - gb_cc).norm() / gb_cc.norm()).item()
+    assert relb < 1e-4, relb
