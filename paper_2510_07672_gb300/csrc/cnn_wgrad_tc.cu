@@ -17,8 +17,10 @@
 // contiguous ranges; each range is run by two CTAs, one for taps 0..4 and one
 // for taps 5..8 (5 or 4 accumulators of 64 columns), so every CTA keeps its
 // accumulators in TMEM over its whole range and writes one partial per tap at
-// the end.  The partials are summed in a fixed order by the same reduction as
-// the CUDA-core weight gradient, so the result is deterministic.
+// the end.  The CTA of taps 0..4 also forms the bias gradient sum_p dz(p, co)
+// as one more 64 x 16 x 16 MMA per pixel group against a B of ones.  The
+// partials are summed in a fixed order by the same reduction as the CUDA-core
+// weight gradient, so the result is deterministic.
 //   warp 0, producer: the input rows y - 1, y, y + 1 of a run start and then
 //     row y + 1 per unit (128 columns plus one pixel each side, wrapped at the
 //     field's edge: bulk copy per chunk plane, wrapped pixel by cp.async) into
@@ -44,7 +46,9 @@ constexpr uint32_t kWDPlane = 128u * 16u;        // dz row: 128 pixels
 constexpr uint32_t kWDSlot = kWKC * kWDPlane;
 constexpr int kWRA = 7;                          // activation-row ring
 constexpr int kWRD = 4;                          // dz-row ring
-constexpr size_t kWCtlOff = size_t(kWRA) * kWASlot + size_t(kWRD) * kWDSlot;
+constexpr size_t kWOnesOff = size_t(kWRA) * kWASlot + size_t(kWRD) * kWDSlot;
+constexpr uint32_t kWOnesPlane = 16u * 16u;      // B = ones for the bias: N = 16, K = 16, MN-major
+constexpr size_t kWCtlOff = kWOnesOff + 2 * kWOnesPlane;
 constexpr size_t kWSmem = kWCtlOff + 256;
 
 struct WCtl {
@@ -90,6 +94,11 @@ wgrad_tc_kernel(const __nv_bfloat16* __restrict__ a, const __nv_bfloat16* __rest
         tc::mbar_init(&ctl->fin, 1);
         ctl->abort = 0;
         tc::fence_mbar_init();
+    }
+    if (group == 0) {
+        uint32_t* ones = reinterpret_cast<uint32_t*>(smem + kWOnesOff);
+        for (int i = tid; i < int(2 * kWOnesPlane / 4); i += blockDim.x) ones[i] = 0x3F803F80u;  // bf16 1.0 pairs
+        tc::fence_proxy_async_smem();
     }
     if (warp == 1) tc::tmem_alloc(&ctl->tmem, 512u);
     tc::fence_before_sync();
@@ -170,6 +179,8 @@ wgrad_tc_kernel(const __nv_bfloat16* __restrict__ a, const __nv_bfloat16* __rest
             // ---- MMA issuer
             // bf16 A and B, f32 D, both operands MN-major (transposed), M = 64, N = 64
             constexpr uint32_t idesc = tc::idesc_bf16_f32(64, 64) | (1u << 15) | (1u << 16);
+            constexpr uint32_t idesc_b = tc::idesc_bf16_f32(64, 16) | (1u << 15) | (1u << 16);
+            const uint64_t ones_d = tc::smem_desc(tc::smem_u32(smem + kWOnesOff), 128, kWOnesPlane);
             const uint64_t a_hi = tc::smem_desc(0, 128, kWDPlane);  // A = dz rows
             const uint64_t b_hi = tc::smem_desc(0, 128, kWAPlane);  // B = activation rows
             const uint32_t aring_u = tc::smem_u32(aring) >> 4, dring_u = tc::smem_u32(dring) >> 4;
@@ -211,6 +222,8 @@ wgrad_tc_kernel(const __nv_bfloat16* __restrict__ a, const __nv_bfloat16* __rest
                         const uint64_t bd = b_hi | uint64_t(r_u + uint32_t(kg * 16 + dx));
                         tc::mma_bf16(tmem + uint32_t(t * kWC), ad, bd, idesc, (first && kg == 0) ? 0u : 1u);
                     }
+                    if (group == 0)  // bias: every column of this accumulator is sum_p dz(p, co)
+                        tc::mma_bf16(tmem + uint32_t(5 * kWC), ad, ones_d, idesc_b, (first && kg == 0) ? 0u : 1u);
                 }
                 first = false;
                 tc::mma_commit(&ctl->dempty[rd.idx]);
@@ -252,6 +265,12 @@ wgrad_tc_kernel(const __nv_bfloat16* __restrict__ a, const __nv_bfloat16* __rest
                     }
                 }
             }
+            if (group == 0) {
+                uint32_t v[8];
+                tc::tmem_ld8(tmem + (uint32_t(q * 32) << 16) + uint32_t(5 * kWC), v);
+                tc::tmem_wait_ld();
+                if (lane < 16) part[(size_t(ch) * 9) * (kWC * kWC + kWC) + kWC * kWC + co] = __uint_as_float(v[0]);
+            }
         }
     }
     tc::fence_before_sync();
@@ -261,43 +280,6 @@ wgrad_tc_kernel(const __nv_bfloat16* __restrict__ a, const __nv_bfloat16* __rest
         if (lane == 0) tc::mbar_wait_bounded(&ctl->fin, 0, kTcSpin);
         __syncwarp();
         tc::tmem_dealloc(tmem, 512u);
-    }
-}
-
-// Bias-gradient partials in the same slots as the CUDA-core weight gradient's:
-// part[chunk][tap 0][C*C + o] = sum over the chunk's pixels of dz(p, o).
-__global__ void bgrad_partials_kernel(const __nv_bfloat16* __restrict__ dz, float* __restrict__ part, int n,
-                                      int batch, int chunks) {
-    const int ch = blockIdx.x;
-    const size_t nn = size_t(n) * n;
-    const long long total = (long long)nn * batch;
-    const long long p0 = total * ch / chunks, p1 = total * (ch + 1) / chunks;
-    const int kc = threadIdx.x & 7, w = threadIdx.x >> 3;  // 32 pixel streams x 8 chunk planes
-    const int lg2nn = 2 * (__ffs(n) - 1);                    // n is a power of two
-    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (long long p = p0 + w; p < p1; p += 32) {
-        const long long f = p >> lg2nn, q = p & (long long)(nn - 1);
-        const uint4 raw = *reinterpret_cast<const uint4*>(dz + ((size_t(f) * kWKC + kc) * nn + size_t(q)) * 8);
-        const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&raw);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) s[i] += __bfloat162float(v8[i]);
-    }
-    // fixed-order sum over the 32 streams: a tree over the warp's 4 streams, then the 8 warps
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        float v = s[i];
-        v += __shfl_down_sync(0xffffffffu, v, 16);
-        v += __shfl_down_sync(0xffffffffu, v, 8);
-        s[i] = v;
-    }
-    __shared__ float wsum[8][kWC];
-    if ((threadIdx.x & 31) < 8)
-        for (int i = 0; i < 8; ++i) wsum[threadIdx.x >> 5][kc * 8 + i] = s[i];
-    __syncthreads();
-    if (threadIdx.x < kWC) {
-        float t = 0.f;
-        for (int wi = 0; wi < 8; ++wi) t += wsum[wi][threadIdx.x];
-        part[(size_t(ch) * 9) * (kWC * kWC + kWC) + kWC * kWC + threadIdx.x] = t;
     }
 }
 
@@ -315,8 +297,6 @@ int wgrad_tc_partials(int n, int batch, const __nv_bfloat16* a, const __nv_bfloa
         configured = true;
     }
     wgrad_tc_kernel<<<2 * chunks, kWThreads, kWSmem, st>>>(a, dz, part, n, batch, chunks, status);
-    ACPR_LAUNCH_CHECK();
-    bgrad_partials_kernel<<<chunks, 256, 0, st>>>(dz, part, n, batch, chunks);
     ACPR_LAUNCH_CHECK();
     return AC_OK;
 }
