@@ -289,6 +289,103 @@ wgrad_kernel(const void* __restrict__ a_src, const void* __restrict__ dz_src, fl
     }
     if (tap == 0 && threadIdx.x < COUT) out[C * C + threadIdx.x] = bacc;
 }
+// The same partials for the first (CIN = 1) and last (COUT = 1) layers, where
+// one side has K = C channels and the other one: a thread walks its own pixels
+// of the (tap, chunk) block with all K channel sums in registers (the K-side
+// operand comes as 16-byte chunk vectors), then the block sums its threads in
+// a fixed order (a shuffle tree per warp, then the warps in order).
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kWgThreads)
+wgrad_thin_kernel(const void* __restrict__ a_src, const void* __restrict__ dz_src, float* __restrict__ part,
+                  int batch, int n, int C) {
+    static_assert(CIN == 1 || COUT == 1, "one side of the layer has one channel");
+    constexpr int K = CIN > COUT ? CIN : COUT;
+    constexpr int KC = K / 8;
+    constexpr int NW = kWgThreads / 32;
+    __shared__ float red[NW][K + 1];
+    const int tap = blockIdx.x % 9;
+    const int chunk = blockIdx.x / 9;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const int lg = __ffs(n) - 1;  // n is a power of two
+    const long long nn = (long long)n * n;
+    const long long total = nn * batch;
+    const long long per_chunk = (total + kChunks - 1) / kChunks;
+    const long long p0 = chunk * per_chunk;
+    const long long p1 = p0 + per_chunk < total ? p0 + per_chunk : total;
+    const bool bias = tap == 0;
+    float acc[K], bacc[CIN == 1 ? K : 1];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < (CIN == 1 ? K : 1); ++k) bacc[k] = 0.f;
+    for (long long p = p0 + threadIdx.x; p < p1; p += kWgThreads) {
+        const int b = int(p >> (2 * lg));
+        const long long pl = p & (nn - 1);
+        const int y = wrapi((int(p >> lg) & (n - 1)) + dy, n), x = wrapi((int(p) & (n - 1)) + dx, n);
+        const long long q = (long long)y * n + x;
+        if constexpr (CIN == 1) {
+            // first layer: a = the float32 field (bf16-rounded), dz = C bf16 channels at p
+            const float av = bf16r(static_cast<const float*>(a_src)[(long long)b * nn + q]);
+            const __nv_bfloat16* dz = static_cast<const __nv_bfloat16*>(dz_src);
+#pragma unroll
+            for (int kc = 0; kc < KC; ++kc) {
+                const uint4 raw = *reinterpret_cast<const uint4*>(dz + (((long long)b * KC + kc) * nn + pl) * 8);
+                const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&raw);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float dv = __bfloat162float(v8[i]);
+                    acc[kc * 8 + i] = fmaf(dv, av, acc[kc * 8 + i]);
+                    if (bias) bacc[kc * 8 + i] += dv;
+                }
+            }
+        } else {
+            // last layer: dz = the float32 output gradient (bf16-rounded), a = C bf16 channels at q
+            const float dv = bf16r(static_cast<const float*>(dz_src)[(long long)b * nn + pl]);
+            const __nv_bfloat16* a = static_cast<const __nv_bfloat16*>(a_src);
+#pragma unroll
+            for (int kc = 0; kc < KC; ++kc) {
+                const uint4 raw = *reinterpret_cast<const uint4*>(a + (((long long)b * KC + kc) * nn + q) * 8);
+                const __nv_bfloat16* v8 = reinterpret_cast<const __nv_bfloat16*>(&raw);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc[kc * 8 + i] = fmaf(dv, __bfloat162float(v8[i]), acc[kc * 8 + i]);
+            }
+            if (bias) bacc[0] += dv;
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* out = part + ((long long)chunk * 9 + tap) * (C * C + C);
+    // weight partials: index o * CIN + c is k on both sides (the other index is 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        float t = 0.f;
+        for (int w = 0; w < NW; ++w) t += red[w][threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+    if (bias) {
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < COUT; ++k) {
+            float v = bacc[CIN == 1 ? k : 0];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < COUT) {
+            float t = 0.f;
+            for (int w = 0; w < NW; ++w) t += red[w][threadIdx.x];
+            out[C * C + threadIdx.x] = t;
+        }
+    }
+}
+
 // Fixed-order sum of the chunk partials into the float32 gradients
 // (W[o][c][tap] layout of the masters; overwrite or accumulate).
 __global__ void wgrad_reduce_kernel(const float* __restrict__ part, float* __restrict__ gw, float* __restrict__ gb,
@@ -322,7 +419,10 @@ static int check_train(const cnn_desc* d) {
 template <int CIN, int COUT>
 static int wgrad(const void* a, const void* dz, float* part, float* gw, float* gb, int batch, int n, int C,
                  int accumulate, cudaStream_t st) {
-    wgrad_kernel<CIN, COUT><<<kChunks * 9, kWgThreads, 0, st>>>(a, dz, part, batch, n, C);
+    if constexpr (CIN == 1 || COUT == 1)
+        wgrad_thin_kernel<CIN, COUT><<<kChunks * 9, kWgThreads, 0, st>>>(a, dz, part, batch, n, C);
+    else
+        wgrad_kernel<CIN, COUT><<<kChunks * 9, kWgThreads, 0, st>>>(a, dz, part, batch, n, C);
     ACPR_LAUNCH_CHECK();
     const int total = COUT * CIN * 9 + COUT;
     wgrad_reduce_kernel<<<(total + 255) / 256, 256, 0, st>>>(part, gw, gb, CIN, COUT, C, accumulate);
