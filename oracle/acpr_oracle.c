@@ -31,9 +31,9 @@
  *
  * Parity status: every function here is pinned by the not-gpu tests (naive DFT,
  * dense linear solve, closed forms, invariants, finite differences, brute force,
- * library routines) except the straight-through backward of the bf16-emulating
- * conv mode: parity unpinned there beyond the float64 mode it reduces to when
- * rounding is off.
+ * library routines).  The straight-through backward of the bf16-emulating conv
+ * mode is pinned as the exact gradient (central differences) of the stack with
+ * each rounding frozen into a constant offset at the evaluation point.
  */
 #include <complex.h>
 #include <math.h>

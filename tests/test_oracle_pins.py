@@ -409,6 +409,84 @@ def test_conv_backward_finite_differences(act, mass_fix):
     assert abs(fd - np.vdot(gb, db)) < 1e-7 * max(1, abs(fd))
 
 
+def _stack_frozen_rounding(u, w, b, layers, C, act, mass_fix, r_u, r_w, r_a):
+    """The conv stack with every bf16 rounding replaced by the addition of a
+    constant offset (r_u to the input, r_w to the weights, r_a[l] to the
+    activations of hidden layer l); scipy correlate2d(wrap) convolutions."""
+    dims = I.cnn_layer_dims(layers, C)
+    a = [u + r_u]
+    wr = w + r_w
+    wo = bo = 0
+    for l, (ci, co) in enumerate(dims):
+        W = wr[wo:wo + ci * co * 9].reshape(co, ci, 3, 3)
+        out = []
+        for o in range(co):
+            z = np.full_like(u, b[bo + o])
+            for c in range(ci):
+                z = z + scipy.signal.correlate2d(a[c], W[o, c], mode="same", boundary="wrap")
+            out.append(z)
+        wo += ci * co * 9
+        bo += co
+        if l < layers - 1:
+            out = [(np.tanh(z) if act == 0 else _gelu(z)) + r_a[l][o] for o, z in enumerate(out)]
+        a = out
+    res = u + a[0]
+    if mass_fix:
+        res = res + (u.mean() - res.mean())
+    return res
+
+
+@pytest.mark.parametrize("act,mass_fix", [(0, 0), (1, 0), (1, 1)])
+def test_bf16_backward_is_the_gradient_with_frozen_rounding(act, mass_fix):
+    """The straight-through backward of the bf16 mode (reading 5) is the exact
+    gradient of the stack in which each bf16 rounding is frozen into a
+    constant offset taken at the evaluation point: that stack equals the bf16
+    forward there, and it is smooth, so central differences of it in random
+    directions of u, W and b must match the backward's inner products."""
+    n, L, C = 6, 3, 3
+    w, b = I.cnn_weights(L, C, seed=15, sigma=0.4)
+    w = w.astype(np.float32).astype(np.float64)
+    b = b.astype(np.float32).astype(np.float64)
+    u = I.random_field(n, seed=16).astype(np.float32).astype(np.float64)
+    gout = rng(17).standard_normal((n, n))
+    spec = O.CnnSpec(L, C, w, b, act=act, mass_fix=mass_fix, bf16=1)
+    # the rounding offsets at the evaluation point, from an independent forward
+    r_u = _bf16_bits(u) - u
+    r_w = _bf16_bits(w) - w
+    dims = I.cnn_layer_dims(L, C)
+    a = [u + r_u]
+    wr = w + r_w
+    r_a = []
+    wo = bo = 0
+    for l, (ci, co) in enumerate(dims[:-1]):
+        W = wr[wo:wo + ci * co * 9].reshape(co, ci, 3, 3)
+        acts = []
+        for o in range(co):
+            z = np.full_like(u, b[bo + o])
+            for c in range(ci):
+                z = z + scipy.signal.correlate2d(a[c], W[o, c], mode="same", boundary="wrap")
+            acts.append(np.tanh(z) if act == 0 else _gelu(z))
+        r_a.append([_bf16_bits(v) - v for v in acts])
+        a = [v + r for v, r in zip(acts, r_a[-1])]
+        wo += ci * co * 9
+        bo += co
+    frozen = lambda uu, ww, bb: _stack_frozen_rounding(uu, ww, bb, L, C, act, mass_fix, r_u, r_w, r_a)
+    # at the evaluation point the frozen stack is the bf16 forward
+    assert np.abs(frozen(u, w, b) - O.cnn_forward(spec, u)).max() < 1e-13
+    gin, gw, gb = O.cnn_backward(spec, u, gout)
+    hh = 1e-6
+    J = lambda uu, ww, bb: np.vdot(gout, frozen(uu, ww, bb))
+    d = rng(18).standard_normal((n, n))
+    fd = (J(u + hh * d, w, b) - J(u - hh * d, w, b)) / (2 * hh)
+    assert abs(fd - np.vdot(gin, d)) < 1e-7 * max(1, abs(fd))
+    dw = rng(19).standard_normal(w.shape)
+    fd = (J(u, w + hh * dw, b) - J(u, w - hh * dw, b)) / (2 * hh)
+    assert abs(fd - np.vdot(gw, dw)) < 1e-7 * max(1, abs(fd))
+    db = rng(20).standard_normal(b.shape)
+    fd = (J(u, w, b + hh * db) - J(u, w, b - hh * db)) / (2 * hh)
+    assert abs(fd - np.vdot(gb, db)) < 1e-7 * max(1, abs(fd))
+
+
 # -------------------------------------------------------------- Parareal
 def _small_problem(variant=0):
     n, s, c = 16, 6, 5
