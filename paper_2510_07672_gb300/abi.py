@@ -799,7 +799,7 @@ def cnn_conv_set_variant(n: int, channels: int, index: int):
 
 
 def cnn_autotune(net, u_in, u_out=None, stream=None):
-    """Time every conv tile shape on this problem, keep the fastest; returns
+    """Time every shape of the persistent conv kernel on this problem, keep the fastest; returns
     {shape: ms per call} and the chosen index."""
     n = u_in.shape[-1]
     batch = u_in.numel() // (n * n)
