@@ -964,8 +964,16 @@ def main():
             "conv_tflops": conv_tflops,
             "roofline": {"bound": "alu", "kernel": "fine_field_kernel", "achieved": fine_tflops,
                          "peak": peak, "unit": "TFLOP/s", "frac": fine_tflops / peak,
-                         "traffic": fine_traffic_per_launch(st, WL, steps),
+                         # the counters were taken on the asynchronous-exchange launch shape (2 CTAs
+                         # per SM); the default shape has changed since (no exchange buffer, 3 CTAs per
+                         # SM) and was not captured again
+                         "traffic": None,
+                         "traffic_earlier_shape": fine_traffic_per_launch(st, WL, steps),
                          "traffic_unit": "bytes per launch (ncu DRAM bytes per field-slice x field-slices per launch)",
+                         "traffic_note": "null: the DRAM counters (433.6 KB per field-slice, 512 KB algorithmic) "
+                                         "are of the asynchronous-exchange launch shape, not of the current "
+                                         "default (no exchange buffer, 3 CTAs per SM); traffic_earlier_shape "
+                                         "scales them to this run's launches",
                          "peak_source": f"FP32 lanes x 2 x sm_max_mhz {sm_mhz:.0f} from {src} peaks",
                          "flops_per_cell_step": fpc},
             "cpu_baseline": cpu,
