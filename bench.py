@@ -196,7 +196,7 @@ def run_uneven(args):
         u0 = torch.tensor(np.stack([I.random_field(n, seed=p["seed"]) for p in grp]), dtype=torch.float32,
                           device="cuda")
         # the tuners pick the fine launch shape (on a batch of the size a fine
-        # phase launches) and the conv tile (on the problems' fields) before
+        # phase launches) and the conv kernel shape (on the problems' fields) before
         # the handle exists, so no solve changes shape midway
         reps = max(1, 256 // len(grp))
         fb = u0.repeat(reps, 1, 1).contiguous()
