@@ -158,3 +158,34 @@ def test_acnn_handle_lifetime_with_a_parareal_handle(monkeypatch):
     assert fake.attached == [100, 101]       # re-attached to the new handle
     net._free_handles()
     assert sorted(fake.destroyed) == [100, 101]
+
+
+def test_conv_shape_queries_on_the_host():
+    """The persistent conv kernel's shape table (ring depth, TMEM slots) is
+    host logic: every (n, C) with n a multiple of 128 has at least one shape,
+    the shapes are distinct, the ring holds at most 24 rows, the slots of
+    3C columns (rounded up to a power of two) fit the 512 TMEM columns, and
+    selecting, reading back and resetting a shape works without a GPU; the
+    weight-gradient switch is host state too."""
+    L = G.load()
+    for C_ in (16, 32, 64):
+        width = 64 if C_ <= 16 else (128 if C_ <= 32 else 256)
+        for n in (128, 256, 512, 1024):
+            shapes = G.cnn_conv_variants(n, C_)
+            assert shapes, (n, C_)
+            assert len(set(shapes)) == len(shapes)
+            for ring, slots in shapes:
+                assert 2 <= ring <= 24 and 2 <= slots and slots * width <= 512, (n, C_, ring, slots)
+        assert G.cnn_conv_variants(64, C_) == []  # below 128 the one-shot kernel runs
+    assert L.cnn_conv_variant_count(256, 24) == 0
+    n_sh = len(G.cnn_conv_variants(256, 32))
+    G.cnn_conv_set_variant(256, 32, n_sh - 1)
+    assert L.cnn_conv_get_variant(256, 32) == n_sh - 1
+    G.cnn_conv_set_variant(256, 32, -1)
+    assert L.cnn_conv_get_variant(256, 32) == -1
+    with pytest.raises(G.AcprError):
+        G.cnn_conv_set_variant(256, 32, n_sh)
+    r, s = C.c_int(), C.c_int()
+    assert L.cnn_conv_variant_shape(256, 32, n_sh, C.byref(r), C.byref(s)) != 0
+    G.cnn_train_set_wgrad_tc(False)
+    G.cnn_train_set_wgrad_tc(True)
